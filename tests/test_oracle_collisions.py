@@ -1,0 +1,133 @@
+"""Pins of the oracle's collision detection and resolution (Sect. 5, Eq. 2,
+Eq. 3, Sect. 6.2): brute force, a geometry with a known answer, the
+conservation statement of Sect. 6.2 and the head-on closed form."""
+import os
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _dense(seed, n=400, L=30.0, zsig=1.0):
+    g = np.random.default_rng(seed)
+    x, y = g.uniform(-L / 2, L / 2, (2, n))
+    z = g.normal(0, zsig, n)
+    r = g.uniform(0.6, 1.2, n)
+    return x, y, z, r
+
+
+@pytest.mark.parametrize("boundary,seed", [(0, 1), (1, 2), (2, 3), (2, 4)])
+def test_tree_search_equals_brute_force(orc, boundary, seed):
+    """Sect. 5.2: the Eq. 3 descent finds exactly the overlaps that testing
+    every pair and every image (Sect. 5.1) finds."""
+    L = 30.0
+    x, y, z, r = _dense(seed, L=L)
+    ids = np.random.default_rng(seed).permutation(len(x)).astype(np.int64)
+    p = orc.Params(omega=0.02, L=(L, L, L), nghost=(1, 1, 0), boundary=boundary)
+    t = 123.4
+    kb = orc.collide_brute(p, t, x, y, z, r, ids)
+    kt = orc.collide_tree(p, t, x, y, z, r, ids)
+    assert len(kb) > 50
+    assert kb.tolist() == kt.tolist()
+    a, b, c = orc.decode_pairs(kb)
+    assert np.all(a < b)
+    if boundary != 0:
+        assert np.any(c != orc.CENTRAL_CODE)
+
+
+def test_overlap_across_the_shear_boundary(orc):
+    """Two particles that touch only through the sheared image at +Lx."""
+    L, O, t = 20.0, 0.05, 7.0
+    p = orc.Params(omega=O, L=(L, L, L), nghost=(1, 1, 0), boundary=2)
+    s = np.fmod(1.5 * O * L * t, L)
+    y0 = -3.0
+    x = np.array([L / 2 - 0.5, -L / 2 + 0.5])
+    y = np.array([y0, y0 + s])
+    z = np.zeros(2)
+    r = np.ones(2)
+    keys = orc.collide_brute(p, t, x, y, z, r, np.array([0, 1]))
+    code = (1 + 7) | ((0 + 7) << 4) | ((0 + 7) << 8)
+    assert keys.tolist() == [(0 << 36) | (1 << 12) | code]
+    # from the other side the same pair is the image at -Lx of particle 0
+    keys2 = orc.collide_brute(p, t, x, y, z, r, np.array([1, 0]))
+    code2 = (-1 + 7) | ((0 + 7) << 4) | ((0 + 7) << 8)
+    assert keys2.tolist() == [(0 << 36) | (1 << 12) | code2]
+
+
+def _golden_e2():
+    rows = {}
+    with open(os.path.join(HERE, "golden", "e2_conservation.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                rows[k] = v
+    return rows
+
+
+@pytest.mark.parametrize("detector", [1, 2])
+def test_elastic_collisions_conserve_energy_and_momentum(orc, detector):
+    """Sect. 6.2: non-rotating periodic box, no gravity, eps = 1: momentum and
+    energy are conserved to machine precision."""
+    assert _golden_e2() == {"momentum": "machine_precision", "energy": "machine_precision"}
+    g = np.random.default_rng(11)
+    n, L = 300, 16.0
+    x, y, z = g.uniform(-L / 2, L / 2, (3, n))
+    vx, vy, vz = g.normal(0, 0.5, (3, n))
+    m = g.uniform(0.5, 2.0, n)
+    r = np.full(n, 0.5)
+    p = orc.Params(L=(L, L, L), nghost=(1, 1, 1), boundary=1, z_periodic=1, eps=1.0, dt=0.02,
+                   gravity=0, collisions=detector, integrator=0)
+    st = orc.State(p, x, y, z, vx, vy, vz, m, r)
+    E0, P0 = st.energy()
+    npairs = 0
+    for _ in range(40):
+        st.step(1)
+        npairs += len(st.last_pairs)
+    E1, P1 = st.energy()
+    assert npairs > 100
+    assert abs(E1 - E0) <= 1e-13 * abs(E0)
+    scale = np.sum(m * np.sqrt(vx ** 2 + vy ** 2 + vz ** 2))
+    assert np.all(np.abs(P1 - P0) <= 1e-14 * scale)
+
+
+def test_head_on_collision(orc):
+    """Eq. 2 for a head-on pair: the relative normal velocity becomes
+    -eps times its old value and the momentum is unchanged."""
+    p = orc.Params(L=(10.0,) * 3, eps=0.5)
+    x = np.array([0.0, 1.9]); y = np.array([0.0, 0.0]); z = np.zeros(2)
+    vx = np.array([1.0, -0.5]); vy = np.array([0.3, 0.3]); vz = np.zeros(2)
+    m = np.array([2.0, 3.0])
+    keys = orc.collide_brute(p, 0.0, x, y, z, np.ones(2), np.array([0, 1]))
+    assert len(keys) == 1
+    nvx, nvy, nvz = orc.resolve(p, 0.0, x, y, z, vx, vy, vz, m, np.array([0, 1]), keys)
+    assert nvx[1] - nvx[0] == pytest.approx(-0.5 * (vx[1] - vx[0]), rel=1e-15)
+    assert m @ nvx == pytest.approx(m @ vx, rel=1e-15)
+    np.testing.assert_array_equal(nvy, vy)
+
+
+def test_receding_pair_is_not_resolved(orc):
+    """Sect. 5.1: a pair is resolved only if the particles approach."""
+    p = orc.Params(L=(10.0,) * 3, eps=0.5)
+    x = np.array([0.0, 1.9]); y = np.zeros(2); z = np.zeros(2)
+    vx = np.array([-1.0, 0.5]); vy = np.zeros(2); vz = np.zeros(2)
+    keys = orc.collide_brute(p, 0.0, x, y, z, np.ones(2), np.array([0, 1]))
+    nv = orc.resolve(p, 0.0, x, y, z, vx, vy, vz, np.ones(2), np.array([0, 1]), keys)
+    np.testing.assert_array_equal(nv[0], vx)
+
+
+def test_sheet_step_runs_and_collides(orc):
+    """A full DKD step of the small shearing sheet (tree gravity, tree
+    collisions, SEI) keeps particles in the box and finds collisions."""
+    from paper_1110_4876_gb300 import inputs as I
+    P = I.sheet(100.0, 2400, 1)
+    p = orc.Params(G=I.G_SI, omega=I.OMEGA, L=(100.0,) * 3, nghost=(1, 1, 0), boundary=2,
+                   integrator=1, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    st = orc.State(p, *P.arrays())
+    tot = 0
+    for _ in range(3):
+        st.step(1)
+        tot += len(st.last_pairs)
+    assert st.n == 2400
+    assert np.all(np.abs(st.x) <= 50) and np.all(np.abs(st.y) <= 50)
+    assert tot > 0
