@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the tree gravity + tree collision step on GB300.
+
+Workload: the 1,000,000-particle shearing sheet (box 2050 x 2050 m, R = 1 m,
+rho = 400 kg/m^3, z ~ N(0, 1 m), shear flow plus dispersion 2 Omega x 1 m),
+1 ghost ring in x and y, open z, SEI, Barnes-Hut theta = 0.5 with quadrupoles,
+FP32 cell-relative walk, hard-sphere collisions with eps = 0.5.  A step is one
+full DKD step (drift, tree build, gravity walk, kick, drift, collision tree,
+collision search, pair sort, resolution).  Metric: particle-steps/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own independent sheet on its own GPU
+(replicas; weak scaling) and rank 0 prints one JSON line.  --impl reference
+times the FP64 CPU oracle (the only reference this method has) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (tree gravity+collisions, N=1M) at fixed force error vs direct sum"
+UNIT = "particle-steps/s"
+N_SHEET = 1_000_000
+L_SHEET = 2050.0
+SEED = 5
+SMS = 152
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 flops per interaction (FMA = 2, add/mul = 1, rsqrt = 0)
+FLOP_CELL, FLOP_LEAF, FLOP_MAC = 60, 20, 10
+
+
+def workload_name(walk: str) -> str:
+    return (f"shearing sheet N={N_SHEET:,} box {L_SHEET:g}x{L_SHEET:g} m, 1 ghost ring, SEI, "
+            f"theta=0.5 quadrupole, {walk} walk, collisions eps=0.5")
+
+
+def sheet_config(rb, walk):
+    from paper_1110_4876_gb300 import inputs as I
+
+    return dict(G=I.G_SI, omega=I.OMEGA, box=(L_SHEET,) * 3, nghost=(1, 1, 0),
+                boundary=rb.RB_BC_SHEAR, integrator=rb.RB_INT_SEI, theta=0.5, eps=0.5,
+                dt=I.DT_SHEET, gravity=1, collisions=1,
+                walk=rb.RB_WALK_FP32 if walk == "fp32" else rb.RB_WALK_FP64)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    rb.load()
+    stream = torch.cuda.Stream()
+    cfg = sheet_config(rb, args.walk)
+    P = I.sheet(L_SHEET, N_SHEET, SEED + rank)
+    sim = rb.Sim(stream=stream.cuda_stream, **cfg)
+    sim.set_particles(P)
+    rb.rb_set_profiling(sim.h, True)
+    sim.step(args.warmup)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput (inputs already in HBM) ----
+    walk_ms, walk_flops, stage_sum = [], [], {}
+    launches = 0
+    pairs = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.step(1)
+            st = sim.stats()
+            walk_ms.append(st["ms_stage"]["gravity_walk"])
+            walk_flops.append(FLOP_CELL * st["cell_interactions"] + FLOP_LEAF * st["leaf_interactions"]
+                              + FLOP_MAC * st["mac_tests"])
+            for k, v in st["ms_stage"].items():
+                stage_sum[k] = stage_sum.get(k, 0.0) + v
+            launches += st["kernels_per_step"]
+            pairs.append(st["pairs_found"])
+        e1.record(stream)
+        barrier()
+    t_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    clocks = clk.summary()
+    value = world * N_SHEET * args.steps / (t_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    ke = max(1, min(args.steps, 3))
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in P.arrays()]
+    sim_e = rb.Sim(stream=stream.cuda_stream, **cfg)
+    sim_e.set_particles(tuple(host))
+    sim_e.step(1)  # capture the step graphs outside the timed region
+    state = tuple(host)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        sim_e.set_particles(state)
+        sim_e.step(1)
+        d = sim_e.particles()
+        state = (d["x"], d["y"], d["z"], d["vx"], d["vy"], d["vz"], d["m"], d["r"])
+    barrier()
+    te = time.perf_counter() - t0
+    e2e = {"value": world * N_SHEET * ke / te, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * 8 * N_SHEET, "d2h_bytes_per_step": (8 * 8 + 4 + 4) * N_SHEET,
+           "steps": ke}
+    del sim_e
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    wms = statistics.mean(walk_ms)
+    achieved = statistics.mean(walk_flops) / (wms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_walk32 (gravity walk)", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": walk_traffic(), "peak_source":
+                    f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
+                    "(MEASURED_PEAKS.json sm_max_mhz)",
+                "flops_per_launch": statistics.mean(walk_flops), "ms_per_launch": wms}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.walk == "fp32" else "f64",
+        "data": "synthetic (seeded shearing-sheet generator; no dataset or weights)",
+        "config": {"workload": workload_name(args.walk), "particles_per_gpu": N_SHEET,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "precision": "walk FP32 on hi/lo cell-relative offsets; positions, kick/drift, "
+                                "moments, collisions FP64" if args.walk == "fp32" else "all FP64",
+                   "l2": "no flush: working set (2 x 72 MB particle sets + ~0.4 GB tree) > 129 MB L2",
+                   "pairs_per_step": statistics.mean(pairs)},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
+    }
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"], line["force_error"] = cpu_baseline(sim, cfg, P, args)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def walk_traffic():
+    """DRAM bytes per gravity-walk launch from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "gravity_walk_sheet1m.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_launch:"):
+                    return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def oracle_sample(P, samples: int, seed: int = 0):
+    """Time the oracle's step on the full workload with the gravity walk run
+    on a sample of targets; returns (seconds per particle-step, details)."""
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
+
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L_SHEET,) * 3, nghost=(1, 1, 0), boundary=2,
+                      integrator=1, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    n = P.n
+    t = time.perf_counter()
+    s = oracle.drift(p, P.x, P.y, P.z, P.vx, P.vy, P.vz)
+    t_drift = time.perf_counter() - t
+    t = time.perf_counter()
+    tree = oracle.Tree(s[0], s[1], s[2], P.m, L_SHEET)
+    t_build = time.perf_counter() - t
+    sel = np.random.default_rng(seed).choice(n, samples, replace=False)
+    t = time.perf_counter()
+    tree.gravity(p, oracle.time_at(p, 1), targets=sel)
+    t_walk = time.perf_counter() - t
+    del tree
+    t = time.perf_counter()
+    keys = oracle.collide_tree(p, oracle.time_at(p, 2), s[0], s[1], s[2], P.r, np.arange(n))
+    t_coll = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.resolve(p, oracle.time_at(p, 2), s[0], s[1], s[2], s[3], s[4], s[5], P.m, np.arange(n), keys)
+    t_res = time.perf_counter() - t
+    per = (2 * t_drift + t_build + t_coll + t_res) / n + t_walk / samples
+    detail = (f"full step on N={n:,} except the gravity walk, which ran on {samples} random "
+              f"targets (all 9 images) and is scaled per particle: drift x2 {2 * t_drift:.2f} s, "
+              f"tree build {t_build:.2f} s, walk sample {t_walk:.2f} s, collision tree search "
+              f"{t_coll:.2f} s ({len(keys)} pairs), resolution {t_res:.2f} s")
+    return per, detail, oracle.nthreads(), p, sel
+
+
+def cpu_baseline(sim, cfg, P, args):
+    """The oracle on this host's cores (bounded sample) and the force error of
+    the GPU walk against the oracle's direct sum on 256 targets."""
+    import oracle
+    from paper_1110_4876_gb300 import rb
+
+    per, detail, cores, p, _ = oracle_sample(P, args.cpu_samples)
+    base = {"value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": detail}
+    # force error of the benchmarked walk at the initial state
+    sim_f = rb.Sim(**cfg)
+    sim_f.set_particles(P)
+    a_gpu = sim_f.gravity()
+    sel = np.random.default_rng(1).choice(P.n, 256, replace=False)
+    a_dir = oracle.direct_gravity(p, 0.0, P.x, P.y, P.z, P.m, targets=sel)
+    a_tree = oracle.Tree(P.x, P.y, P.z, P.m, L_SHEET).gravity(p, 0.0, targets=sel)
+    es, rr, mr = oracle.force_errors(a_gpu[sel], a_dir)
+    _, _, mt = oracle.force_errors(a_gpu[sel], a_tree)
+    fe = {"vs_direct_sum": {"e_sum": es, "rms_rel": rr, "max_rel": mr},
+          "vs_oracle_tree_same_theta": {"max_rel": mt}, "targets": 256,
+          "floor": "per-particle denominator floored at 1e-3 rms|a|"}
+    return base, fe
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    from paper_1110_4876_gb300 import inputs as I
+
+    P = I.sheet(L_SHEET, N_SHEET, SEED)
+    times = []
+    detail = cores = None
+    for k in range(args.warmup + args.steps):
+        per, detail, cores, _, _ = oracle_sample(P, args.cpu_samples // 4, seed=k)
+        if k >= args.warmup:
+            times.append(per)
+    per = statistics.mean(times)
+    value = 1.0 / per
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * N_SHEET * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded shearing-sheet generator)",
+            "config": {"workload": workload_name("fp64 oracle"), "particles": N_SHEET},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": detail},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--walk", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--cpu-samples", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

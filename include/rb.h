@@ -1,0 +1,182 @@
+/*
+ * rb.h -- C ABI of librb, the GB300 (sm_103a) tree gravity + tree collision
+ * library for collisional N-body simulations after REBOUND (Rein & Liu 2012).
+ *
+ * Every step is the drift-kick-drift (DKD) scheme of Sect. 3: drift dt/2,
+ * boundaries (Sect. 2.3), octree at the mid-step positions (Sect. 4.2),
+ * Barnes-Hut self-gravity (Eq. 1, Sect. 4.2), kick dt, drift dt/2,
+ * boundaries, then the tree collision search (Sect. 5.2, Eq. 3) and the
+ * resolution of the collisions found (Sect. 5, Eq. 2).  All of it runs in the
+ * library's CUDA kernels on one GPU; nothing falls back to the CPU.
+ *
+ * Conventions shared by every call:
+ *  - Return value: RB_OK (0) or a negative RB_ERR_* code.  No call throws or
+ *    aborts across the ABI; rb_last_error() describes the last failure.
+ *  - Host pointers ("host") are read or written before the call returns and
+ *    stay owned by the caller.  Device memory is owned by the library and
+ *    allocated with cudaMallocAsync on the simulation's stream.
+ *  - Particle ids: 0..n-1 in the order given to rb_set_particles for that
+ *    box; they are stable while particles move, and removed particles (open
+ *    boundaries) leave gaps.  Per-particle outputs are in ascending id order.
+ *  - Units are the caller's; G fixes them.  Positions are relative to the box
+ *    centre: the root cube of a box of side L spans [-L/2, L/2) per axis.
+ */
+#ifndef RB_H
+#define RB_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RB_OK = 0,
+    RB_ERR_ARG = -1,       /* invalid argument or configuration */
+    RB_ERR_CAPACITY = -2,  /* a fixed-size device buffer overflowed twice in a row */
+    RB_ERR_TIMEOUT = -3,   /* a bounded device wait gave up */
+    RB_ERR_NONFINITE = -4, /* a position became NaN or infinite */
+    RB_ERR_CUDA = -5,      /* a CUDA runtime call failed */
+    RB_ERR_STATE = -6      /* call out of order (e.g. no particles yet) */
+};
+
+/* Boundary conditions of Sect. 2.3. */
+enum { RB_BC_OPEN = 0, RB_BC_PERIODIC = 1, RB_BC_SHEAR = 2 };
+/* Integrators: leap-frog (Sect. 3.1), symplectic epicycle integrator (Sect. 3.3). */
+enum { RB_INT_LEAPFROG = 0, RB_INT_SEI = 1 };
+/* Precision of the gravity walk.  Positions, velocities, moments and the
+ * kick/drift are FP64 in every mode. */
+enum { RB_WALK_FP64 = 0, RB_WALK_FP32 = 1, RB_WALK_FP32_LEARNED = 2 };
+
+typedef struct rb_config {
+    double G;               /* gravitational constant of Eq. 1 */
+    double omega;           /* epicyclic frequency Omega (SEI, shear offsets) */
+    double omega_z;         /* vertical frequency Omega_z; <= 0 means = omega (Sect. 3.3) */
+    double box[3];          /* box side per axis; the root cube has side box[0] == box[1] == box[2] */
+    double theta;           /* critical opening angle (Sect. 4.2), > 0 */
+    double eps_restitution; /* normal coefficient of restitution (Eq. 2), in [0, 1] */
+    double softening;       /* gravitational softening b of Eq. 1, >= 0 */
+    double dt;              /* time step (Sect. 3), > 0 */
+    double t0;              /* time at step 0 (sets the shear offset) */
+    int nghost[3];          /* ghost boxes per direction (Sect. 2.3); z needs z_periodic */
+    int boundary;           /* RB_BC_* */
+    int z_periodic;         /* 1: z periodic (RB_BC_PERIODIC/SHEAR); 0: open in z */
+    int integrator;         /* RB_INT_* */
+    int walk;               /* RB_WALK_* */
+    int quadrupole;         /* 1: monopole + quadrupole cells (Sect. 4.2); 0: monopole */
+    int gravity;            /* 1: tree self-gravity; 0: none */
+    int collisions;         /* 1: tree collision search + resolution; 0: none */
+    int reserved[5];        /* must be zero */
+} rb_config;
+
+typedef struct rb_stats_t {
+    int64_t steps;            /* steps taken since rb_set_particles / rb_set_time */
+    int64_t n_live;           /* particles in all boxes */
+    int64_t cells;            /* tree cells (branching nodes) in the last gravity tree */
+    int64_t pairs_found;      /* collision pairs found in the last step */
+    int64_t pairs_resolved;   /* pairs that were approaching and were resolved */
+    int64_t cell_interactions;/* accepted cells in the last gravity walk (all particles, images) */
+    int64_t leaf_interactions;/* exact particle terms in the last gravity walk */
+    int64_t mac_tests;        /* opening-angle tests in the last gravity walk */
+    int64_t fp64_rechecks;    /* FP32 opening tests decided again in FP64 (guard band) */
+    int64_t pair_capacity;    /* current pair buffer capacity */
+    int64_t kernels_per_step; /* kernel launches in one captured step graph */
+    double  t;                /* simulation time */
+    double  ms_last_step;     /* device time of the last step (events), ms */
+    /* device time of each stage of the last step when profiling is on (ms):
+     * 0 drift+keys, 1 sort+gather, 2 tree, 3 moments, 4 gravity walk,
+     * 5 kick+drift+keys, 6 sort+gather, 7 tree, 8 collision records,
+     * 9 collision search, 10 pair sort, 11 resolution */
+    double  ms_stage[12];
+} rb_stats_t;
+
+typedef struct rb_sim rb_sim; /* opaque, owned by the library */
+
+/* Create a simulation of `nbox` independent boxes (1, or B for an ensemble
+ * advanced together) that share `cfg`; box sizes default to cfg->box.
+ * cuda_stream: a cudaStream_t (NULL: the library creates its own).  The
+ * stream must outlive the simulation.  *out receives the handle.
+ * Errors: RB_ERR_ARG (theta <= 0, dt <= 0, eps outside [0,1], a non-cubic
+ * root box, nghost < 0 or > 7, SEI without omega, reserved != 0),
+ * RB_ERR_CUDA. */
+int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out);
+
+/* Set the side lengths of box `box` (host array of 3; cubic root box). */
+int rb_set_box(rb_sim* sim, int box, const double L[3]);
+
+/* Copy n particles (host arrays: positions, velocities, masses, radii) into
+ * box `box`, replacing what it held; ids become 0..n-1 in this order and
+ * the step counter restarts at 0 (time cfg->t0 or the last rb_set_time).
+ * Errors: RB_ERR_ARG (n < 0, box out of range, a particle outside the root
+ * box, r < 0, m < 0, total particles above 2^24), RB_ERR_NONFINITE. */
+int rb_set_particles(rb_sim* sim, int box, int64_t n, const double* x, const double* y,
+                     const double* z, const double* vx, const double* vy, const double* vz,
+                     const double* m, const double* r);
+
+/* Advance every box by nsteps DKD steps (Sect. 3) on the simulation's
+ * stream, replaying a captured CUDA graph per step; returns once the steps
+ * are done and the device error word was checked.  A pair-buffer overflow is
+ * repaired inside the step (buffer grown, the search re-run before any
+ * velocity changes); RB_ERR_CAPACITY only if that fails. */
+int rb_step(rb_sim* sim, int64_t nsteps);
+
+/* Copy the live particles of box `box`, in ascending id order, into host
+ * arrays of capacity cap (any output pointer may be NULL).  *n_out receives
+ * the live count (also when it exceeds cap; then RB_ERR_ARG). */
+int rb_get_particles(rb_sim* sim, int box, int64_t cap, int64_t* n_out, double* x, double* y,
+                     double* z, double* vx, double* vy, double* vz, double* m, double* r,
+                     int64_t* id);
+
+/* Energy and momentum of box `box` (Sect. 6.2) at the current time:
+ * E = sum m v^2 / 2 + W (+ sum m (Omega_z^2 z^2 / 2 - 3/2 Omega^2 x^2) for
+ * SEI), W = (1/2) sum m_i phi_i with phi from an FP64 tree walk at theta over
+ * the ghost images (0 when gravity is off); P = sum m v (host array of 3). */
+int rb_energy(rb_sim* sim, int box, double* E, double P[3]);
+
+/* Test and measurement hooks. */
+
+/* Build the gravity tree on the current positions and evaluate the walk
+ * without moving anything; results are read with rb_get_accelerations,
+ * rb_get_counts and rb_get_tree.  The time used for the ghost offsets is
+ * the current time. */
+int rb_compute_gravity(rb_sim* sim);
+/* Accelerations of the last gravity walk (kick or rb_compute_gravity), host
+ * arrays in id order. */
+int rb_get_accelerations(rb_sim* sim, int box, int64_t cap, double* ax, double* ay, double* az);
+/* Per-particle counts of the last gravity walk: accepted cells, exact
+ * particle terms, opening-angle tests (host arrays in id order). */
+int rb_get_counts(rb_sim* sim, int box, int64_t cap, int64_t* ncell, int64_t* nleaf,
+                  int64_t* nmac);
+/* Branching cells of the last gravity tree of box `box`: depth, the ids of
+ * their particles (concatenated, `count` each) and FP64 moments
+ * (M; centre of mass xyz; Q as xx, yy, zz, xy, xz, yz).  *ncell receives the
+ * number of cells; arrays may be NULL.  member_cap bounds member_ids. */
+int rb_get_tree(rb_sim* sim, int box, int64_t cap, int64_t* ncell, int32_t* depth,
+                int64_t* count, double* M, double* com, double* Q, int64_t member_cap,
+                int64_t* member_ids);
+/* Run the collision search (Sect. 5.2) on the current positions without
+ * resolving; read the pairs with rb_get_pairs. */
+int rb_detect_collisions(rb_sim* sim);
+/* Collision pairs of the last search of box `box` in resolution order: ids
+ * a < b and the ghost image code of b as seen from a,
+ * code = (gx+7) | (gy+7) << 4 | (gz+7) << 8 (host arrays). */
+int rb_get_pairs(rb_sim* sim, int box, int64_t cap, int64_t* n, int64_t* id_a, int64_t* id_b,
+                 int32_t* code);
+/* Set / read the simulation time (restarts the step counter at t). */
+int rb_set_time(rb_sim* sim, double t);
+int rb_get_time(rb_sim* sim, double* t);
+/* Counters of the last step (host struct). */
+int rb_stats(rb_sim* sim, rb_stats_t* out);
+/* on = 1: record CUDA events between the stages of every step (event nodes
+ * inside the step graph) so rb_stats reports per-stage device times. */
+int rb_set_profiling(rb_sim* sim, int on);
+/* Destroy the simulation and free its device memory. */
+void rb_destroy(rb_sim* sim);
+/* Description of the last error of `sim` (or of the last failed
+ * rb_create when sim is NULL); static storage owned by the library. */
+const char* rb_last_error(const rb_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,819 @@
+// rb_api.cu -- the C ABI of librb: simulation state, device memory, the
+// per-step CUDA graph and the test/measurement hooks.
+//
+// One step (Sect. 3, drift-kick-drift) is captured once into a CUDA graph:
+//   drift dt/2 + boundaries + Morton keys -> sort -> gather -> tree ->
+//   moments -> gravity walk -> kick + drift dt/2 + boundaries + keys ->
+//   sort -> gather -> tree -> collision search -> pair sort -> resolution.
+// Each gather moves the particles into the other SoA set, so two graphs are
+// captured (one per starting set) and replayed alternately.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "rb.h"
+#include "rb_internal.cuh"
+
+using namespace rb;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct BoxHost {
+    double L[3];
+    std::vector<double> x, y, z, vx, vy, vz, m, r;
+};
+
+}  // namespace
+
+struct rb_sim {
+    rb_config cfg{};
+    int nbox = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<BoxHost> hb;
+    std::vector<int64_t> base;  // first global id of each box
+    SimC C{};
+    // device state
+    PSet P[2]{};
+    int cur = 0;
+    Tree T{};
+    Pairs PR{};
+    Ctl* ctl = nullptr;
+    BoxP* d_boxes = nullptr;
+    double *acc_x = nullptr, *acc_y = nullptr, *acc_z = nullptr, *phi = nullptr;
+    int32_t *cnt_cell = nullptr, *cnt_leaf = nullptr, *cnt_mac = nullptr;
+    int acc_set = -1;     // particle set the last gravity walk ran on
+    double* e_part = nullptr;
+    double* e_out = nullptr;
+    int ncap = 0, ntot = 0, box_bits = 0;
+    double rmax = 0.0;
+    bool dirty = true, graphs_dirty = true;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gafter[2] = {0, 0};
+    std::vector<void*> allocs, pair_allocs;
+    std::string err;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_stage[13] = {};
+    bool profiling = false;
+    int kernels_per_step = 0;
+    float last_ms = 0.f;
+    float stage_ms[12] = {};
+    Ctl hctl{};
+};
+
+namespace {
+
+constexpr int kEnergyParts = 304;
+constexpr int kResolveRounds = 4;
+
+int fail(rb_sim* s, int code, const std::string& msg) {
+    if (s) s->err = msg; else g_create_error = msg;
+    return code;
+}
+
+#define RB_CUDA(sim, call)                                                               \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(sim, RB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int dalloc(rb_sim* s, T** p, size_t count, std::vector<void*>& list) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), s->stream);
+    if (e != cudaSuccess) return fail(s, RB_ERR_CUDA, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    list.push_back(q);
+    *p = static_cast<T*>(q);
+    return RB_OK;
+}
+
+void free_list(rb_sim* s, std::vector<void*>& list) {
+    for (void* q : list) cudaFreeAsync(q, s->stream);
+    list.clear();
+}
+
+void drop_graphs(rb_sim* s) {
+    for (int k = 0; k < 2; k++)
+        if (s->gexec[k]) {
+            cudaGraphExecDestroy(s->gexec[k]);
+            s->gexec[k] = nullptr;
+        }
+    s->graphs_dirty = true;
+}
+
+// SimC from the configuration.  The SEI drift coefficients are the exact
+// solution of Hill's equations over tau = dt/2 (Sect. 3.3).
+void make_constants(rb_sim* s) {
+    const rb_config& c = s->cfg;
+    SimC& C = s->C;
+    C.nbox = s->nbox;
+    C.boundary = c.boundary;
+    C.z_periodic = c.z_periodic;
+    C.integrator = c.integrator;
+    C.quadrupole = c.quadrupole;
+    C.ngx = c.boundary == RB_BC_OPEN ? 0 : c.nghost[0];
+    C.ngy = c.boundary == RB_BC_OPEN ? 0 : c.nghost[1];
+    C.ngz = (c.boundary == RB_BC_OPEN || !c.z_periodic) ? 0 : c.nghost[2];
+    C.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
+    C.G = c.G;
+    C.theta = c.theta;
+    C.theta2 = c.theta * c.theta;
+    C.crit_scale = 1.0 / (c.theta * c.theta);
+    C.soft2 = c.softening * c.softening;
+    C.eps = c.eps_restitution;
+    C.dt = c.dt;
+    C.half_dt = 0.5 * c.dt;
+    C.t0 = c.t0;
+    C.omega = c.omega;
+    C.omega_z = c.omega_z > 0.0 ? c.omega_z : c.omega;
+    if (c.integrator == RB_INT_SEI) {
+        const double O = C.omega, Oz = C.omega_z, tau = 0.5 * c.dt;
+        const double ph = O * tau, co = std::cos(ph), si = std::sin(ph);
+        const double phz = Oz * tau, cz = std::cos(phz), sz = std::sin(phz);
+        C.axx = 4.0 - 3.0 * co; C.axu = si / O; C.axv = (2.0 / O) * (1.0 - co);
+        C.ayx = 6.0 * (si - ph); C.ayu = -(2.0 / O) * (1.0 - co); C.ayv = (4.0 * si - 3.0 * ph) / O;
+        C.aux = (3.0 * O) * si; C.auu = co; C.auv = 2.0 * si;
+        C.avx = (6.0 * O) * (co - 1.0); C.avu = -2.0 * si; C.avv = 4.0 * co - 3.0;
+        C.azz = cz; C.azw = sz / Oz; C.awz = -(Oz * sz); C.aww = cz;
+    }
+}
+
+int box_params(rb_sim* s) {
+    std::vector<BoxP> hb(s->nbox);
+    for (int b = 0; b < s->nbox; b++) {
+        BoxP& p = hb[b];
+        memset(&p, 0, sizeof(p));
+        p.L = s->hb[b].L[0];
+        p.Lx = s->hb[b].L[0]; p.Ly = s->hb[b].L[1]; p.Lz = s->hb[b].L[2];
+        p.shear_speed = s->cfg.boundary == RB_BC_SHEAR ? (1.5 * s->cfg.omega) * p.Lx : 0.0;
+    }
+    RB_CUDA(s, cudaMemcpyAsync(s->d_boxes, hb.data(), sizeof(BoxP) * s->nbox, cudaMemcpyHostToDevice,
+                               s->stream));
+    return RB_OK;
+}
+
+int alloc_pairs(rb_sim* s, int cap) {
+    free_list(s, s->pair_allocs);
+    Pairs& R = s->PR;
+    int32_t* keep_slot = R.slot_of_id;
+    int32_t* keep_minp = R.minp;
+    R.cap = cap;
+    int rc = RB_OK;
+    rc |= dalloc(s, &R.key, cap, s->pair_allocs);
+    rc |= dalloc(s, &R.key_alt, cap, s->pair_allocs);
+    rc |= dalloc(s, &R.val, cap, s->pair_allocs);
+    rc |= dalloc(s, &R.val_alt, cap, s->pair_allocs);
+    rc |= dalloc(s, &R.done, cap, s->pair_allocs);
+    rc |= dalloc(s, &R.hist, radix_hist_words(cap), s->pair_allocs);
+    R.slot_of_id = keep_slot;
+    R.minp = keep_minp;
+    return rc ? RB_ERR_CUDA : RB_OK;
+}
+
+// Allocate for capacity n and upload the staged boxes.
+int upload(rb_sim* s) {
+    int64_t tot = 0;
+    s->base.assign(s->nbox, 0);
+    for (int b = 0; b < s->nbox; b++) {
+        s->base[b] = tot;
+        tot += (int64_t)s->hb[b].x.size();
+    }
+    if (tot >= (1 << 24)) return fail(s, RB_ERR_ARG, "more than 2^24 - 1 particles");
+    const int n = (int)tot;
+    if (n > s->ncap || s->ncap == 0) {
+        drop_graphs(s);   // the graphs hold the old buffers
+        free_list(s, s->allocs);
+        free_list(s, s->pair_allocs);
+        const int cap = std::max(n, 1);
+        const int ecap = 2 * cap;
+        auto& L = s->allocs;
+        int rc = RB_OK;
+        for (int k = 0; k < 2; k++) {
+            PSet& P = s->P[k];
+            rc |= dalloc(s, &P.x, cap, L); rc |= dalloc(s, &P.y, cap, L); rc |= dalloc(s, &P.z, cap, L);
+            rc |= dalloc(s, &P.vx, cap, L); rc |= dalloc(s, &P.vy, cap, L); rc |= dalloc(s, &P.vz, cap, L);
+            rc |= dalloc(s, &P.m, cap, L); rc |= dalloc(s, &P.r, cap, L);
+            rc |= dalloc(s, &P.id, cap, L); rc |= dalloc(s, &P.box, cap, L);
+        }
+        Tree& T = s->T;
+        T = Tree{};
+        T.cap_n = cap;
+        T.cap_e = ecap;
+        rc |= dalloc(s, &T.key, cap, L); rc |= dalloc(s, &T.key_alt, cap, L);
+        rc |= dalloc(s, &T.idx, cap, L); rc |= dalloc(s, &T.idx_alt, cap, L);
+        rc |= dalloc(s, &T.sbox, cap, L);
+        rc |= dalloc(s, &T.hist, radix_hist_words(cap), L);
+        rc |= dalloc(s, &T.scan_part, scan_part_words(cap), L);
+        rc |= dalloc(s, &T.mask, cap, L);
+        rc |= dalloc(s, &T.start, cap + 1, L);
+        rc |= dalloc(s, &T.node_a, cap, L); rc |= dalloc(s, &T.node_b, cap, L);
+        rc |= dalloc(s, &T.node_v, cap, L);
+        rc |= dalloc(s, &T.e_first, ecap, L); rc |= dalloc(s, &T.e_count, ecap, L);
+        rc |= dalloc(s, &T.e_skip, ecap, L); rc |= dalloc(s, &T.e_parent, ecap, L);
+        rc |= dalloc(s, &T.e_nchild, ecap, L); rc |= dalloc(s, &T.e_arrive, ecap, L);
+        rc |= dalloc(s, &T.e_level, ecap, L);
+        rc |= dalloc(s, &T.leaf_of, cap, L);
+        rc |= dalloc(s, &T.ra, ecap, L); rc |= dalloc(s, &T.rb, ecap, L);
+        rc |= dalloc(s, &T.rq0, ecap, L); rc |= dalloc(s, &T.rq1, ecap, L);
+        rc |= dalloc(s, &T.rc_hi, ecap, L); rc |= dalloc(s, &T.rc_lo, ecap, L);
+        rc |= dalloc(s, &T.d_a, ecap, L); rc |= dalloc(s, &T.d_q0, ecap, L);
+        rc |= dalloc(s, &T.d_q1, ecap, L); rc |= dalloc(s, &T.d_c, ecap, L);
+        rc |= dalloc(s, &T.box_first, s->nbox + 1, L);
+        rc |= dalloc(s, &T.box_root, s->nbox, L);
+        rc |= dalloc(s, &s->PR.slot_of_id, cap, L);
+        rc |= dalloc(s, &s->PR.minp, cap, L);
+        rc |= dalloc(s, &s->acc_x, cap, L); rc |= dalloc(s, &s->acc_y, cap, L);
+        rc |= dalloc(s, &s->acc_z, cap, L); rc |= dalloc(s, &s->phi, cap, L);
+        rc |= dalloc(s, &s->cnt_cell, cap, L); rc |= dalloc(s, &s->cnt_leaf, cap, L);
+        rc |= dalloc(s, &s->cnt_mac, cap, L);
+        rc |= dalloc(s, &s->ctl, 1, L);
+        rc |= dalloc(s, &s->d_boxes, s->nbox, L);
+        rc |= dalloc(s, &s->e_part, 7 * kEnergyParts, L);
+        rc |= dalloc(s, &s->e_out, 8, L);
+        if (rc) return RB_ERR_CUDA;
+        s->ncap = cap;
+        // a freshly drawn dense sheet overlaps about one pair per particle
+        if (alloc_pairs(s, 2 * cap + 4096) != RB_OK) return RB_ERR_CUDA;
+    }
+    s->ntot = n;
+    // stage into one contiguous host buffer per field
+    const int cap = s->ncap;
+    std::vector<double> f(cap);
+    std::vector<int32_t> ids(cap), bx(cap);
+    double* dst[8] = {s->P[0].x, s->P[0].y, s->P[0].z, s->P[0].vx,
+                      s->P[0].vy, s->P[0].vz, s->P[0].m, s->P[0].r};
+    double rmax = 0.0;
+    for (int fld = 0; fld < 8; fld++) {
+        int k = 0;
+        for (int b = 0; b < s->nbox; b++) {
+            const BoxHost& h = s->hb[b];
+            const std::vector<double>* src[8] = {&h.x, &h.y, &h.z, &h.vx, &h.vy, &h.vz, &h.m, &h.r};
+            for (double v : *src[fld]) {
+                f[k++] = v;
+                if (fld == 7) rmax = std::max(rmax, v);
+            }
+        }
+        for (; k < cap; k++) f[k] = 0.0;
+        RB_CUDA(s, cudaMemcpyAsync(dst[fld], f.data(), sizeof(double) * cap, cudaMemcpyHostToDevice,
+                                   s->stream));
+        RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    }
+    {
+        int k = 0;
+        for (int b = 0; b < s->nbox; b++)
+            for (size_t i = 0; i < s->hb[b].x.size(); i++) {
+                ids[k] = k;
+                bx[k] = b;
+                k++;
+            }
+        for (; k < cap; k++) {
+            ids[k] = k;
+            bx[k] = s->nbox;   // unused slot: treated as removed
+        }
+    }
+    RB_CUDA(s, cudaMemcpyAsync(s->P[0].id, ids.data(), sizeof(int32_t) * cap, cudaMemcpyHostToDevice, s->stream));
+    RB_CUDA(s, cudaMemcpyAsync(s->P[0].box, bx.data(), sizeof(int32_t) * cap, cudaMemcpyHostToDevice, s->stream));
+    RB_CUDA(s, cudaMemcpyAsync(s->PR.slot_of_id, ids.data(), sizeof(int32_t) * cap, cudaMemcpyHostToDevice, s->stream));
+    Ctl c{};
+    c.n_live = n;
+    RB_CUDA(s, cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+    RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (rmax != s->rmax) drop_graphs(s);   // R_max is a launch argument of the graphs
+    s->rmax = rmax;
+    s->cur = 0;
+    s->acc_set = -1;
+    s->box_bits = 0;
+    if (s->nbox > 1) {
+        while ((1 << s->box_bits) <= s->nbox) s->box_bits++;
+    }
+    make_constants(s);
+    if (box_params(s) != RB_OK) return RB_ERR_CUDA;
+    s->dirty = false;
+    return RB_OK;
+}
+
+WalkOut walk_out(rb_sim* s) {
+    WalkOut o;
+    o.ax = s->acc_x; o.ay = s->acc_y; o.az = s->acc_z; o.phi = s->phi;
+    o.ncell = s->cnt_cell; o.nleaf = s->cnt_leaf; o.nmac = s->cnt_mac;
+    return o;
+}
+
+// Stage marker: an event record node in the step graph when profiling.
+void mark(rb_sim* s, int k) {
+    if (s->profiling) cudaEventRecord(s->ev_stage[k], s->stream);
+}
+
+// The launches of one step starting from particle set p; returns the set
+// that holds the particles afterwards.
+int record_step(rb_sim* s, int p) {
+    cudaStream_t st = s->stream;
+    cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), st);
+    cudaMemsetAsync(&s->ctl->err, 0, sizeof(int), st);
+    clear_walk_stats(s->ctl, st);
+    int c = p;
+    mark(s, 0);
+    if (s->cfg.gravity) {
+        drift_keys(s->P[c], s->T, s->ctl, s->d_boxes, s->C, s->ncap, 1, 1, nullptr, nullptr, nullptr,
+                   false, st);
+        mark(s, 1);
+        sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, st);
+        c = 1 - c;
+        mark(s, 2);
+        build_topology(s->T, s->P[c], s->ctl, s->d_boxes, s->C, st);
+        mark(s, 3);
+        build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st);
+        mark(s, 4);
+        gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk, 1, walk_out(s), false, true,
+                     st);
+        mark(s, 5);
+        drift_keys(s->P[c], s->T, s->ctl, s->d_boxes, s->C, s->ncap, 1, 2, s->acc_x, s->acc_y,
+                   s->acc_z, true, st);
+    } else {
+        drift_keys(s->P[c], s->T, s->ctl, s->d_boxes, s->C, s->ncap, 2, 1, nullptr, nullptr, nullptr,
+                   false, st);
+        for (int k = 1; k <= 5; k++) mark(s, k);
+    }
+    mark(s, 6);
+    if (s->cfg.collisions) {
+        sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, st);
+        c = 1 - c;
+        mark(s, 7);
+        build_topology(s->T, s->P[c], s->ctl, s->d_boxes, s->C, st);
+        mark(s, 8);
+        build_collision_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
+        mark(s, 9);
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st);
+        mark(s, 10);
+        sort_pairs(s->PR, s->ctl, st);
+        mark(s, 11);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, st);
+    } else {
+        for (int k = 7; k <= 11; k++) mark(s, k);
+    }
+    mark(s, 12);
+    step_advance(s->ctl, st);
+    return c;
+}
+
+int capture_graphs(rb_sim* s) {
+    drop_graphs(s);
+    for (int p = 0; p < 2; p++) {
+        cudaGraph_t g = nullptr;
+        RB_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        const int after = record_step(s, p);
+        cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+        if (e != cudaSuccess) return fail(s, RB_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int nk = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaGraphNodeGetType(nd, &ty);
+            nk += ty == cudaGraphNodeTypeKernel;
+        }
+        s->kernels_per_step = nk;
+        e = cudaGraphInstantiate(&s->gexec[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(s, RB_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        s->gafter[p] = after;
+    }
+    s->graphs_dirty = false;
+    return RB_OK;
+}
+
+int read_ctl(rb_sim* s) {
+    RB_CUDA(s, cudaMemcpyAsync(&s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+    RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    return RB_OK;
+}
+
+int clear_err(rb_sim* s) {
+    RB_CUDA(s, cudaMemsetAsync(&s->ctl->err, 0, sizeof(int), s->stream));
+    return RB_OK;
+}
+
+// Collision search + pair sort on set c at half-step offset hs; grows the
+// pair buffer and searches again if it overflowed.  Resolves when asked.
+int collide_with_retry(rb_sim* s, int c, int hs, bool resolve) {
+    for (int attempt = 0; attempt < 2; attempt++) {
+        RB_CUDA(s, cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream));
+        if (clear_err(s)) return RB_ERR_CUDA;
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream);
+        sort_pairs(s->PR, s->ctl, s->stream);
+        if (read_ctl(s)) return RB_ERR_CUDA;
+        if (s->hctl.pair_count <= s->PR.cap) {
+            if (resolve) {
+                resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, kResolveRounds, s->stream);
+                if (read_ctl(s)) return RB_ERR_CUDA;
+            }
+            return RB_OK;
+        }
+        int cap = s->PR.cap;
+        while (cap < s->hctl.pair_count) cap *= 2;
+        if (alloc_pairs(s, cap + 4096) != RB_OK) return RB_ERR_CUDA;
+        drop_graphs(s);
+    }
+    return fail(s, RB_ERR_CAPACITY, "collision pair buffer overflow persisted after growing");
+}
+
+int ensure_ready(rb_sim* s) {
+    if (s->dirty) {
+        int rc = upload(s);
+        if (rc) return rc;
+    }
+    return RB_OK;
+}
+
+// Keys of the current positions (no drift), sort, gather, topology.
+int rebuild_now(rb_sim* s) {
+    const int c = s->cur;
+    drift_keys(s->P[c], s->T, s->ctl, s->d_boxes, s->C, s->ncap, 0, 0, nullptr, nullptr, nullptr,
+               false, s->stream);
+    sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, s->stream);
+    s->cur = 1 - c;
+    build_topology(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->stream);
+    return RB_OK;
+}
+
+int gravity_now(rb_sim* s, bool potential) {
+    rebuild_now(s);
+    const bool fp64 = potential || s->cfg.walk == RB_WALK_FP64;
+    build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
+    clear_walk_stats(s->ctl, s->stream);
+    gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64 ? RB_WALK_FP64 : s->cfg.walk, 0,
+                 walk_out(s), potential, true, s->stream);
+    s->acc_set = s->cur;
+    RB_CUDA(s, cudaGetLastError());
+    return read_ctl(s);
+}
+
+template <typename T>
+int d2h(rb_sim* s, std::vector<T>& v, const T* src, size_t n) {
+    v.resize(std::max<size_t>(n, 1));
+    RB_CUDA(s, cudaMemcpyAsync(v.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost, s->stream));
+    RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    return RB_OK;
+}
+
+// (local id, slot) of the live particles of box b in set c, by id.
+int live_slots(rb_sim* s, int c, int b, std::vector<std::pair<int64_t, int>>& out) {
+    std::vector<int32_t> id, bx;
+    if (d2h(s, id, s->P[c].id, s->ncap) || d2h(s, bx, s->P[c].box, s->ncap)) return RB_ERR_CUDA;
+    out.clear();
+    for (int i = 0; i < s->ncap; i++)
+        if (bx[i] == b) out.emplace_back((int64_t)id[i] - s->base[b], i);
+    std::sort(out.begin(), out.end());
+    return RB_OK;
+}
+
+bool bad_box(rb_sim* s, int box) { return !s || box < 0 || box >= s->nbox; }
+
+}  // namespace
+
+extern "C" {
+
+int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
+    if (!cfg || !out) return fail(nullptr, RB_ERR_ARG, "null argument");
+    *out = nullptr;
+    const rb_config& c = *cfg;
+    if (nbox < 1 || nbox > 65535) return fail(nullptr, RB_ERR_ARG, "nbox must be in [1, 65535]");
+    if (!(c.theta > 0.0)) return fail(nullptr, RB_ERR_ARG, "theta must be > 0");
+    if (!(c.dt > 0.0)) return fail(nullptr, RB_ERR_ARG, "dt must be > 0");
+    if (!(c.eps_restitution >= 0.0 && c.eps_restitution <= 1.0))
+        return fail(nullptr, RB_ERR_ARG, "eps_restitution must be in [0, 1]");
+    if (!(c.softening >= 0.0)) return fail(nullptr, RB_ERR_ARG, "softening must be >= 0");
+    if (!(c.box[0] > 0.0) || c.box[0] != c.box[1] || c.box[0] != c.box[2])
+        return fail(nullptr, RB_ERR_ARG, "the root box must be a cube with box[0] == box[1] == box[2] > 0");
+    for (int a = 0; a < 3; a++)
+        if (c.nghost[a] < 0 || c.nghost[a] > 7) return fail(nullptr, RB_ERR_ARG, "nghost must be in [0, 7]");
+    if (c.boundary < 0 || c.boundary > 2) return fail(nullptr, RB_ERR_ARG, "unknown boundary");
+    if (c.integrator < 0 || c.integrator > 1) return fail(nullptr, RB_ERR_ARG, "unknown integrator");
+    if (c.walk < 0 || c.walk > 2) return fail(nullptr, RB_ERR_ARG, "unknown walk mode");
+    if (c.walk == RB_WALK_FP32_LEARNED) return fail(nullptr, RB_ERR_ARG, "learned walk needs rb_load_mlp (not built)");
+    if (c.integrator == RB_INT_SEI && !(c.omega > 0.0)) return fail(nullptr, RB_ERR_ARG, "SEI needs omega > 0");
+    if (c.boundary == RB_BC_SHEAR && !(c.omega > 0.0)) return fail(nullptr, RB_ERR_ARG, "shear boundaries need omega > 0");
+    if (c.nghost[2] > 0 && !c.z_periodic) return fail(nullptr, RB_ERR_ARG, "ghost boxes in z need z_periodic");
+    if (c.z_periodic && c.boundary == RB_BC_OPEN) return fail(nullptr, RB_ERR_ARG, "z_periodic needs periodic or shear boundaries");
+    for (int k = 0; k < 5; k++)
+        if (c.reserved[k] != 0) return fail(nullptr, RB_ERR_ARG, "reserved fields must be zero");
+    rb_sim* s = new rb_sim();
+    s->cfg = c;
+    s->nbox = nbox;
+    s->hb.resize(nbox);
+    for (auto& b : s->hb)
+        for (int a = 0; a < 3; a++) b.L[a] = c.box[a];
+    if (cuda_stream) {
+        s->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return fail(nullptr, RB_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        s->own_stream = true;
+    }
+    cudaEventCreate(&s->ev0);
+    cudaEventCreate(&s->ev1);
+    for (auto& ev : s->ev_stage) cudaEventCreate(&ev);
+    make_constants(s);
+    *out = s;
+    return RB_OK;
+}
+
+int rb_set_box(rb_sim* s, int box, const double L[3]) {
+    if (bad_box(s, box) || !L) return fail(s, RB_ERR_ARG, "bad box or null L");
+    if (!(L[0] > 0.0) || L[0] != L[1] || L[0] != L[2]) return fail(s, RB_ERR_ARG, "the root box must be a cube");
+    for (int a = 0; a < 3; a++) s->hb[box].L[a] = L[a];
+    s->dirty = true;
+    return RB_OK;
+}
+
+int rb_set_particles(rb_sim* s, int box, int64_t n, const double* x, const double* y,
+                     const double* z, const double* vx, const double* vy, const double* vz,
+                     const double* m, const double* r) {
+    if (bad_box(s, box) || n < 0) return fail(s, RB_ERR_ARG, "bad box or n < 0");
+    if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !m || !r)) return fail(s, RB_ERR_ARG, "null array");
+    for (int64_t i = 0; i < n; i++) {
+        if (!(std::isfinite(x[i]) && std::isfinite(y[i]) && std::isfinite(z[i]) && std::isfinite(vx[i]) &&
+              std::isfinite(vy[i]) && std::isfinite(vz[i])))
+            return fail(s, RB_ERR_NONFINITE, "non-finite particle state");
+        if (!(m[i] >= 0.0) || !(r[i] >= 0.0)) return fail(s, RB_ERR_ARG, "negative mass or radius");
+    }
+    BoxHost& h = s->hb[box];
+    h.x.assign(x, x + n); h.y.assign(y, y + n); h.z.assign(z, z + n);
+    h.vx.assign(vx, vx + n); h.vy.assign(vy, vy + n); h.vz.assign(vz, vz + n);
+    h.m.assign(m, m + n); h.r.assign(r, r + n);
+    if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN) {
+        double rm = 0.0;
+        for (int64_t i = 0; i < n; i++) rm = std::max(rm, r[i]);
+        if (2.0 * rm >= std::min(h.L[0], h.L[1])) return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
+    }
+    s->dirty = true;
+    return RB_OK;
+}
+
+int rb_step(rb_sim* s, int64_t nsteps) {
+    if (!s || nsteps < 0) return fail(s, RB_ERR_ARG, "bad arguments");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (s->ntot == 0) return RB_OK;
+    for (int64_t k = 0; k < nsteps; k++) {
+        if (s->graphs_dirty && (rc = capture_graphs(s))) return rc;
+        const int p = s->cur;
+        RB_CUDA(s, cudaEventRecord(s->ev0, s->stream));
+        RB_CUDA(s, cudaGraphLaunch(s->gexec[p], s->stream));
+        RB_CUDA(s, cudaEventRecord(s->ev1, s->stream));
+        if ((rc = read_ctl(s))) return rc;
+        cudaEventElapsedTime(&s->last_ms, s->ev0, s->ev1);
+        if (s->profiling)
+            for (int q = 0; q < 12; q++)
+                cudaEventElapsedTime(&s->stage_ms[q], s->ev_stage[q], s->ev_stage[q + 1]);
+        s->cur = s->gafter[p];
+        s->acc_set = s->cfg.gravity ? (s->cfg.collisions ? 1 - s->cur : s->cur) : -1;
+        if (s->hctl.err & kErrNonFinite) return fail(s, RB_ERR_NONFINITE, "a position became non-finite");
+        if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
+            // the step ended before resolution: search again with a larger buffer
+            if ((rc = collide_with_retry(s, s->cur, 0, true))) return rc;
+        }
+    }
+    return RB_OK;
+}
+
+int rb_get_particles(rb_sim* s, int box, int64_t cap, int64_t* n_out, double* x, double* y,
+                     double* z, double* vx, double* vy, double* vz, double* m, double* r,
+                     int64_t* id) {
+    if (bad_box(s, box)) return fail(s, RB_ERR_ARG, "bad box");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    std::vector<std::pair<int64_t, int>> sl;
+    if (live_slots(s, s->cur, box, sl)) return RB_ERR_CUDA;
+    if (n_out) *n_out = (int64_t)sl.size();
+    if ((int64_t)sl.size() > cap) return fail(s, RB_ERR_ARG, "capacity too small");
+    const PSet& P = s->P[s->cur];
+    const double* src[8] = {P.x, P.y, P.z, P.vx, P.vy, P.vz, P.m, P.r};
+    double* dst[8] = {x, y, z, vx, vy, vz, m, r};
+    std::vector<double> buf;
+    for (int f = 0; f < 8; f++) {
+        if (!dst[f]) continue;
+        if (d2h(s, buf, src[f], s->ncap)) return RB_ERR_CUDA;
+        for (size_t k = 0; k < sl.size(); k++) dst[f][k] = buf[sl[k].second];
+    }
+    if (id)
+        for (size_t k = 0; k < sl.size(); k++) id[k] = sl[k].first;
+    return RB_OK;
+}
+
+int rb_compute_gravity(rb_sim* s) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (!s->cfg.gravity) return fail(s, RB_ERR_STATE, "gravity is off");
+    if (s->ntot == 0) return RB_OK;
+    return gravity_now(s, false);
+}
+
+int rb_get_accelerations(rb_sim* s, int box, int64_t cap, double* ax, double* ay, double* az) {
+    if (bad_box(s, box)) return fail(s, RB_ERR_ARG, "bad box");
+    if (s->acc_set < 0) return fail(s, RB_ERR_STATE, "no gravity walk yet");
+    std::vector<std::pair<int64_t, int>> sl;
+    if (live_slots(s, s->acc_set, box, sl)) return RB_ERR_CUDA;
+    if ((int64_t)sl.size() > cap) return fail(s, RB_ERR_ARG, "capacity too small");
+    const double* src[3] = {s->acc_x, s->acc_y, s->acc_z};
+    double* dst[3] = {ax, ay, az};
+    std::vector<double> buf;
+    for (int f = 0; f < 3; f++) {
+        if (!dst[f]) continue;
+        if (d2h(s, buf, src[f], s->ncap)) return RB_ERR_CUDA;
+        for (size_t k = 0; k < sl.size(); k++) dst[f][k] = buf[sl[k].second];
+    }
+    return RB_OK;
+}
+
+int rb_get_counts(rb_sim* s, int box, int64_t cap, int64_t* ncell, int64_t* nleaf, int64_t* nmac) {
+    if (bad_box(s, box)) return fail(s, RB_ERR_ARG, "bad box");
+    if (s->acc_set < 0) return fail(s, RB_ERR_STATE, "no gravity walk yet");
+    std::vector<std::pair<int64_t, int>> sl;
+    if (live_slots(s, s->acc_set, box, sl)) return RB_ERR_CUDA;
+    if ((int64_t)sl.size() > cap) return fail(s, RB_ERR_ARG, "capacity too small");
+    const int32_t* src[3] = {s->cnt_cell, s->cnt_leaf, s->cnt_mac};
+    int64_t* dst[3] = {ncell, nleaf, nmac};
+    std::vector<int32_t> buf;
+    for (int f = 0; f < 3; f++) {
+        if (!dst[f]) continue;
+        if (d2h(s, buf, src[f], s->ncap)) return RB_ERR_CUDA;
+        for (size_t k = 0; k < sl.size(); k++) dst[f][k] = buf[sl[k].second];
+    }
+    return RB_OK;
+}
+
+int rb_get_tree(rb_sim* s, int box, int64_t cap, int64_t* ncell, int32_t* depth, int64_t* count,
+                double* M, double* com, double* Q, int64_t member_cap, int64_t* member_ids) {
+    if (bad_box(s, box)) return fail(s, RB_ERR_ARG, "bad box");
+    if (s->acc_set < 0) return fail(s, RB_ERR_STATE, "no gravity tree yet");
+    if (read_ctl(s)) return RB_ERR_CUDA;
+    const int E = s->hctl.n_entries;
+    std::vector<int8_t> lev;
+    std::vector<int32_t> first, cnt, skip, ids, roots;
+    std::vector<double4_32a> da, q0, q1;
+    if (d2h(s, lev, s->T.e_level, E) || d2h(s, first, s->T.e_first, E) || d2h(s, cnt, s->T.e_count, E) ||
+        d2h(s, skip, s->T.e_skip, E) || d2h(s, ids, s->P[s->acc_set].id, s->ncap) ||
+        d2h(s, roots, s->T.box_root, s->nbox) || d2h(s, da, s->T.d_a, E) || d2h(s, q0, s->T.d_q0, E) ||
+        d2h(s, q1, s->T.d_q1, E))
+        return RB_ERR_CUDA;
+    int64_t k = 0, mk = 0;
+    const int r0 = roots[box];
+    if (r0 >= 0) {
+        const int end = skip[r0];
+        for (int e = r0; e < end; e++) {
+            if (lev[e] == 22) continue;
+            if (k < cap) {
+                if (depth) depth[k] = lev[e];
+                if (count) count[k] = cnt[e];
+                if (M) M[k] = q0[e].x;
+                if (com) { com[3 * k] = da[e].x; com[3 * k + 1] = da[e].y; com[3 * k + 2] = da[e].z; }
+                if (Q) {
+                    Q[6 * k] = q0[e].y; Q[6 * k + 1] = q0[e].z; Q[6 * k + 2] = q0[e].w;
+                    Q[6 * k + 3] = q1[e].x; Q[6 * k + 4] = q1[e].y; Q[6 * k + 5] = q1[e].z;
+                }
+                if (member_ids && mk + cnt[e] <= member_cap)
+                    for (int j = 0; j < cnt[e]; j++) member_ids[mk++] = ids[first[e] + j] - s->base[box];
+            }
+            k++;
+        }
+    }
+    if (ncell) *ncell = k;
+    return k > cap ? fail(s, RB_ERR_ARG, "capacity too small") : RB_OK;
+}
+
+int rb_detect_collisions(rb_sim* s) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (s->ntot == 0) return RB_OK;
+    rebuild_now(s);
+    build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+    return collide_with_retry(s, s->cur, 0, false);
+}
+
+int rb_get_pairs(rb_sim* s, int box, int64_t cap, int64_t* n, int64_t* id_a, int64_t* id_b,
+                 int32_t* code) {
+    if (bad_box(s, box)) return fail(s, RB_ERR_ARG, "bad box");
+    if (read_ctl(s)) return RB_ERR_CUDA;
+    const int np = s->hctl.pair_n;
+    std::vector<uint64_t> keys;
+    if (d2h(s, keys, s->PR.key, np)) return RB_ERR_CUDA;
+    const int64_t lo = s->base[box];
+    const int64_t hi = lo + (int64_t)s->hb[box].x.size();
+    int64_t k = 0;
+    for (int i = 0; i < np; i++) {
+        const int64_t a = (int64_t)(keys[i] >> 36);
+        if (a < lo || a >= hi) continue;
+        if (k < cap) {
+            if (id_a) id_a[k] = a - lo;
+            if (id_b) id_b[k] = (int64_t)((keys[i] >> 12) & 0xFFFFFFull) - lo;
+            if (code) code[k] = (int32_t)(keys[i] & 0xFFFull);
+        }
+        k++;
+    }
+    if (n) *n = k;
+    return k > cap ? fail(s, RB_ERR_ARG, "capacity too small") : RB_OK;
+}
+
+int rb_energy(rb_sim* s, int box, double* E, double P[3]) {
+    if (bad_box(s, box) || !E || !P) return fail(s, RB_ERR_ARG, "bad arguments");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    const double* phi = nullptr;
+    if (s->cfg.gravity && s->ntot > 0) {
+        if ((rc = gravity_now(s, true))) return rc;
+        phi = s->phi;
+    }
+    energy_terms(s->P[s->cur], s->ctl, s->C, phi, box, s->e_part, kEnergyParts, s->e_out, s->stream);
+    double h[8];
+    RB_CUDA(s, cudaMemcpyAsync(h, s->e_out, sizeof(double) * 7, cudaMemcpyDeviceToHost, s->stream));
+    RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    *E = h[0] + h[1] + h[2];
+    P[0] = h[3]; P[1] = h[4]; P[2] = h[5];
+    return RB_OK;
+}
+
+int rb_set_time(rb_sim* s, double t) {
+    if (!s || !std::isfinite(t)) return fail(s, RB_ERR_ARG, "bad time");
+    s->cfg.t0 = t;
+    make_constants(s);
+    drop_graphs(s);
+    if (!s->dirty && s->ctl) RB_CUDA(s, cudaMemsetAsync(&s->ctl->step, 0, sizeof(long long), s->stream));
+    return RB_OK;
+}
+
+int rb_get_time(rb_sim* s, double* t) {
+    if (!s || !t) return fail(s, RB_ERR_ARG, "bad arguments");
+    long long step = 0;
+    if (!s->dirty && s->ctl) {
+        if (read_ctl(s)) return RB_ERR_CUDA;
+        step = s->hctl.step;
+    }
+    *t = s->cfg.t0 + (double)(2 * step) * (0.5 * s->cfg.dt);
+    return RB_OK;
+}
+
+int rb_stats(rb_sim* s, rb_stats_t* out) {
+    if (!s || !out) return fail(s, RB_ERR_ARG, "bad arguments");
+    memset(out, 0, sizeof(*out));
+    if (s->dirty || !s->ctl) return RB_OK;
+    if (read_ctl(s)) return RB_ERR_CUDA;
+    const Ctl& c = s->hctl;
+    out->steps = c.step;
+    out->n_live = c.n_live;
+    out->cells = c.n_cells;
+    out->pairs_found = c.pair_n;
+    out->pairs_resolved = c.resolved;
+    out->cell_interactions = (int64_t)c.n_cell;
+    out->leaf_interactions = (int64_t)c.n_leaf;
+    out->mac_tests = (int64_t)c.n_mac;
+    out->fp64_rechecks = (int64_t)c.n_recheck;
+    out->pair_capacity = s->PR.cap;
+    out->t = s->cfg.t0 + (double)(2 * c.step) * (0.5 * s->cfg.dt);
+    out->ms_last_step = s->last_ms;
+    out->kernels_per_step = s->kernels_per_step;
+    for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
+    return RB_OK;
+}
+
+int rb_set_profiling(rb_sim* s, int on) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    if ((on != 0) != s->profiling) {
+        s->profiling = on != 0;
+        drop_graphs(s);
+    }
+    return RB_OK;
+}
+
+void rb_destroy(rb_sim* s) {
+    if (!s) return;
+    drop_graphs(s);
+    free_list(s, s->pair_allocs);
+    free_list(s, s->allocs);
+    cudaStreamSynchronize(s->stream);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
+    for (auto& ev : s->ev_stage)
+        if (ev) cudaEventDestroy(ev);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+const char* rb_last_error(const rb_sim* s) {
+    return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// rb_internal.cuh -- device-side data layout and launch helpers of librb.
+//
+// Layout in HBM (one simulation, all boxes concatenated):
+//  * particles: two FP64 SoA sets (x, y, z, vx, vy, vz, m, r) plus the
+//    global id and the box of each particle; every tree build gathers the
+//    current set into the other one in Morton order, so the arrays stay
+//    sorted and every walk reads them coalesced;
+//  * tree: "entries" in pre-order (depth-first) order, one per branching
+//    cell and one per particle leaf, each with a skip index (the entry after
+//    its subtree) so a walk needs no stack;
+//  * walk records: 32-byte float4 pairs per entry for the FP32 walk (centre
+//    of mass as a hi/lo float pair per axis, so differences of nearby points
+//    keep ~1e-7 relative accuracy), 32-byte double4 records for the FP64
+//    walk, and the FP64 moments (M, centre of mass, traceless quadrupole).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rb {
+
+constexpr int kMaxDepth = 21;           // 21 bits per axis in a 63-bit Morton key
+constexpr uint64_t kRemovedKey = ~0ull; // sorts after every valid key (bit 63 set)
+constexpr int kCentralCode = 7 | (7 << 4) | (7 << 8);
+constexpr int kEnd = 0x7fffffff;        // "walk finished" marker
+
+// Per-box parameters (device array, one entry per box).
+struct BoxP {
+    double L;            // root cube side (= Lx = Ly = Lz)
+    double Lx, Ly, Lz;   // box sides (periodic lengths)
+    double shear_speed;  // (1.5 * Omega) * Lx for shear-periodic boxes, else 0
+    double pad[3];
+};
+
+// Constants of a simulation, passed by value to kernels.
+struct SimC {
+    int nbox, nimg, ngx, ngy, ngz;
+    int boundary, z_periodic, integrator, quadrupole;
+    double G, theta, theta2, soft2, eps, dt, half_dt, t0, omega, omega_z;
+    double crit_scale;   // 1 / theta^2 (FP32 criterion (w / theta)^2)
+    // SEI drift coefficients for tau = dt / 2 (x, vx, vy) -> (x, y, vx, vy), and z
+    double axx, axu, axv, ayx, ayu, ayv, aux, auu, auv, avx, avu, avv;
+    double azz, azw, awz, aww;
+};
+
+// One FP64 particle set (structure of arrays).
+struct PSet {
+    double *x, *y, *z, *vx, *vy, *vz, *m, *r;
+    int32_t* id;   // global id (box base + id within the box)
+    int32_t* box;  // box index; nbox marks a particle removed by an open boundary
+};
+
+// Device control block (scalars written by kernels).
+struct Ctl {
+    long long step;            // steps since the last set_particles / set_time
+    int n_live;                // live particles after the last sort
+    int n_live_next;           // live particles counted by the keys kernel
+    int n_entries;             // tree entries (cells + leaves) of the last build
+    int n_cells;
+    int pair_count;            // pairs found by the last search (may exceed capacity)
+    int pair_n;                // min(pair_count, capacity)
+    int pending;               // pairs not yet resolved
+    int resolved;              // pairs that were approaching and were resolved
+    int err;                   // error bits (kErr*)
+    int pad;
+    unsigned long long n_cell, n_leaf, n_mac, n_recheck;
+};
+constexpr int kErrNonFinite = 1;
+constexpr int kErrPairOverflow = 2;
+
+// Tree and scratch buffers of one build (sized for capacity n).
+struct Tree {
+    uint64_t *key, *key_alt;    // sort keys (ping-pong)
+    uint32_t *idx, *idx_alt;    // sort values: slot in the unsorted set
+    int32_t* sbox;              // box digit per unsorted slot (nbox for removed)
+    uint32_t* hist;             // radix sort block histograms
+    int32_t* scan_part;         // block partials of the entry scan
+    uint32_t* mask;             // per particle: levels of cells starting there
+    int32_t* start;             // per particle: first entry starting there (n + 1)
+    int32_t *node_a, *node_b;   // per split: particle range of the cell (reps only)
+    int8_t* node_v;             // per split: cell depth if representative, else -1
+    int32_t *e_first, *e_count, *e_skip, *e_parent, *e_nchild, *e_arrive;
+    int8_t* e_level;            // depth of a cell; 22 marks a particle leaf
+    int32_t* leaf_of;           // per particle: its leaf entry
+    double *M, *cx, *cy, *cz, *Q;   // FP64 moments per entry (Q: 6 x cap, xx yy zz xy xz yz)
+    float4 *ra, *rb, *rq0, *rq1;    // FP32 walk records
+    float4 *rc_hi, *rc_lo;          // FP32 cell corner (hi/lo) + width, inside test
+    double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
+    int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
+    int cap_n, cap_e;
+};
+
+// Pairs and their resolution.
+struct Pairs {
+    uint64_t *key, *key_alt;
+    uint32_t *val, *val_alt;   // unused payload for the sort
+    int32_t* minp;             // per particle slot: lowest pending pair
+    uint8_t* done;
+    int32_t* slot_of_id;       // global id -> slot in the current set
+    uint32_t* hist;
+    int cap;
+};
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---- launch wrappers (implemented in the .cu files) ----
+// rb_sort.cu
+int radix_sort_passes(int key_bits, bool box_pass, int box_bits);
+// Sorts (key, val) pairs stably by key bits [0, key_bits) and then, when
+// box_digits is non-null, by box_digits[val] (bits [0, box_bits)).
+// Ping-pongs between the two buffers; returns 0 if the result is in
+// (k0, v0) and 1 if it is in (k1, v1).
+int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap, const int* d_n,
+               int key_bits, const int32_t* box_digits, int box_bits, uint32_t* hist,
+               cudaStream_t s);
+size_t radix_hist_words(int ncap);
+void exclusive_scan_i32(int32_t* data, int n_cap, const int* d_n, int32_t* part, int32_t* total,
+                        cudaStream_t s);
+size_t scan_part_words(int ncap);
+
+// rb_tree.cu
+void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                    cudaStream_t s);
+void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
+                           const SimC& C, bool fp64, cudaStream_t s);
+void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
+                             const SimC& C, double rmax, cudaStream_t s);
+
+// rb_walk.cu
+struct WalkOut {
+    double *ax, *ay, *az, *phi;   // per sorted slot
+    int32_t *ncell, *nleaf, *nmac;
+};
+void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                  int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
+                  bool counts, cudaStream_t s);
+void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                      const Pairs& PR, int half_step_offset, cudaStream_t s);
+
+// rb_step.cu
+void drift_keys(const PSet& P, const Tree& T, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                int ncap, int ndrift, int half_step_offset, const double* ax, const double* ay,
+                const double* az, bool kick, cudaStream_t s);
+void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl* ctl,
+                      const SimC& C, int ncap, int box_bits, cudaStream_t s);
+void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
+                   int half_step_offset, int rounds, cudaStream_t s);
+void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s);
+void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
+                  double* partials, int nparts, double* out7, cudaStream_t s);
+void step_advance(Ctl* ctl, cudaStream_t s);
+void clear_walk_stats(Ctl* ctl, cudaStream_t s);
+
+}  // namespace rb

@@ -1,0 +1,399 @@
+// rb_step.cu -- the per-particle parts of a DKD step (Sect. 3): drift with
+// boundaries (Sect. 2.3) fused with the Morton keys of the next tree build,
+// the kick, the gather into Morton order, collision resolution (Sect. 5,
+// Eq. 2) and the energy/momentum sums (Sect. 6.2).
+//
+// Drift, kick, boundary wrap, the overlap geometry and the resolution use
+// explicitly rounded FP64 operations (__dadd_rn, __dmul_rn, ...) so the
+// compiler never fuses them: they give bit-identical results to any other
+// IEEE FP64 implementation that evaluates the same expressions in the same
+// order without fused multiply-adds.
+#include <algorithm>
+#include <climits>
+
+#include "rb_internal.cuh"
+
+namespace rb {
+namespace {
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Integer coordinate floor(((x - lo) / L) * 2^21), clamped to [0, 2^21 - 1].
+__device__ __forceinline__ uint32_t icoord(double x, double lo, double L) {
+    const double u = __ddiv_rn(__dsub_rn(x, lo), L);
+    double k = floor(__dmul_rn(u, 2097152.0));
+    if (!(k >= 0.0)) k = 0.0;
+    if (k > 2097151.0) k = 2097151.0;
+    return (uint32_t)k;
+}
+
+__device__ __forceinline__ double time_at(const Ctl* ctl, const SimC& C, int hs) {
+    const double h = (double)(2 * ctl->step + hs);
+    return __dadd_rn(C.t0, __dmul_rn(h, C.half_dt));
+}
+
+__device__ __forceinline__ void drift_one(const SimC& C, double& x, double& y, double& z,
+                                          double& vx, double& vy, double& vz) {
+    if (C.integrator == 0) {
+        x = __dadd_rn(x, __dmul_rn(vx, C.half_dt));
+        y = __dadd_rn(y, __dmul_rn(vy, C.half_dt));
+        z = __dadd_rn(z, __dmul_rn(vz, C.half_dt));
+        return;
+    }
+    const double x0 = x, u0 = vx, v0 = vy, z0 = z, w0 = vz;
+    x = __dadd_rn(__dadd_rn(__dmul_rn(C.axx, x0), __dmul_rn(C.axu, u0)), __dmul_rn(C.axv, v0));
+    y = __dadd_rn(y, __dadd_rn(__dadd_rn(__dmul_rn(C.ayx, x0), __dmul_rn(C.ayu, u0)),
+                               __dmul_rn(C.ayv, v0)));
+    vx = __dadd_rn(__dadd_rn(__dmul_rn(C.aux, x0), __dmul_rn(C.auu, u0)), __dmul_rn(C.auv, v0));
+    vy = __dadd_rn(__dadd_rn(__dmul_rn(C.avx, x0), __dmul_rn(C.avu, u0)), __dmul_rn(C.avv, v0));
+    z = __dadd_rn(__dmul_rn(C.azz, z0), __dmul_rn(C.azw, w0));
+    vz = __dadd_rn(__dmul_rn(C.awz, z0), __dmul_rn(C.aww, w0));
+}
+
+// Boundaries after a drift half; returns false if the particle left an open
+// boundary.
+__device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, double t, double& x,
+                                         double& y, double& z, double& vy) {
+    const double hx = 0.5 * bp.Lx, hy = 0.5 * bp.Ly, hz = 0.5 * bp.Lz;
+    if (C.boundary == 0)
+        return !(x < -hx || x >= hx || y < -hy || y >= hy || z < -hz || z >= hz);
+    const double s = bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
+    const double vs = bp.shear_speed;
+    if (x >= hx) {
+        x = __dsub_rn(x, bp.Lx);
+        y = __dadd_rn(y, s);
+        vy = __dadd_rn(vy, vs);
+    } else if (x < -hx) {
+        x = __dadd_rn(x, bp.Lx);
+        y = __dsub_rn(y, s);
+        vy = __dsub_rn(vy, vs);
+    }
+    for (int k = 0; k < 8 && y >= hy; k++) y = __dsub_rn(y, bp.Ly);
+    for (int k = 0; k < 8 && y < -hy; k++) y = __dadd_rn(y, bp.Ly);
+    if (C.z_periodic) {
+        for (int k = 0; k < 8 && z >= hz; k++) z = __dsub_rn(z, bp.Lz);
+        for (int k = 0; k < 8 && z < -hz; k++) z = __dadd_rn(z, bp.Lz);
+        return true;
+    }
+    return !(z < -hz || z >= hz);
+}
+
+struct DriftArgs {
+    PSet P;
+    uint64_t* key;
+    uint32_t* idx;
+    int32_t* sbox;
+    Ctl* ctl;
+    const BoxP* boxes;
+    const double *ax, *ay, *az;
+    int ncap, ndrift, hs;
+    bool kick;
+};
+
+// Optional kick (v += a dt), one or two drift halves each followed by the
+// boundaries, then the Morton key of the new position for the next sort.
+__global__ void __launch_bounds__(256) k_drift_keys(DriftArgs A, SimC C) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.ncap) return;
+    A.idx[i] = (uint32_t)i;
+    bool live = A.P.box[i] < C.nbox;
+    uint64_t key = kRemovedKey;
+    if (live) {
+        double x = A.P.x[i], y = A.P.y[i], z = A.P.z[i];
+        double vx = A.P.vx[i], vy = A.P.vy[i], vz = A.P.vz[i];
+        const BoxP bp = A.boxes[A.P.box[i]];
+        if (A.kick) {
+            vx = __dadd_rn(vx, __dmul_rn(A.ax[i], C.dt));
+            vy = __dadd_rn(vy, __dmul_rn(A.ay[i], C.dt));
+            vz = __dadd_rn(vz, __dmul_rn(A.az[i], C.dt));
+        }
+        for (int d = 0; d < A.ndrift && live; d++) {
+            drift_one(C, x, y, z, vx, vy, vz);
+            live = wrap_one(C, bp, time_at(A.ctl, C, A.hs + d), x, y, z, vy);
+        }
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            atomicOr(&A.ctl->err, kErrNonFinite);
+            live = false;
+        }
+        A.P.x[i] = x; A.P.y[i] = y; A.P.z[i] = z;
+        A.P.vx[i] = vx; A.P.vy[i] = vy; A.P.vz[i] = vz;
+        if (live) {
+            const double lo = -0.5 * bp.L;
+            key = (spread3(icoord(x, lo, bp.L)) << 2) | (spread3(icoord(y, lo, bp.L)) << 1) |
+                  spread3(icoord(z, lo, bp.L));
+        }
+    }
+    A.key[i] = key;
+    A.sbox[i] = live ? A.P.box[i] : C.nbox;
+    if (!live) A.P.box[i] = C.nbox;
+    const unsigned b = __ballot_sync(0xffffffffu, live);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&A.ctl->n_live_next, __popc(b));
+}
+
+__global__ void __launch_bounds__(256) k_permute(PSet S, PSet D, const uint32_t* __restrict__ idx,
+                                                 int32_t* __restrict__ slot_of_id, const Ctl* ctl,
+                                                 int ncap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncap) return;
+    const int j = (int)idx[i];
+    D.x[i] = S.x[j]; D.y[i] = S.y[j]; D.z[i] = S.z[j];
+    D.vx[i] = S.vx[j]; D.vy[i] = S.vy[j]; D.vz[i] = S.vz[j];
+    D.m[i] = S.m[j]; D.r[i] = S.r[j];
+    const int id = S.id[j];
+    D.id[i] = id;
+    D.box[i] = S.box[j];
+    if (i < ctl->n_live_next) slot_of_id[id] = i;
+}
+
+__global__ void k_commit_live(Ctl* ctl) {
+    ctl->n_live = ctl->n_live_next;
+    ctl->n_live_next = 0;
+}
+
+// An overflowing search resolves nothing: the host grows the buffer and runs
+// the search again on the unchanged state.
+__global__ void k_pairs_prep(Ctl* ctl, int cap) {
+    const int c = ctl->pair_count;
+    const int n = c <= cap ? c : 0;
+    ctl->pair_n = n;
+    ctl->pending = n;
+    ctl->resolved = 0;
+}
+
+struct ResolveArgs {
+    PSet P;
+    const uint64_t* key;
+    const int32_t* slot_of_id;
+    int32_t* minp;
+    uint8_t* done;
+    Ctl* ctl;
+    const BoxP* boxes;
+    int hs;
+};
+
+__device__ __forceinline__ void pair_slots(const ResolveArgs& A, uint64_t k, int& sa, int& sb) {
+    sa = A.slot_of_id[(int)(k >> 36)];
+    sb = A.slot_of_id[(int)((k >> 12) & 0xFFFFFFull)];
+}
+
+// Eq. 2 for one pair, in the oracle's operation order.
+__device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C, uint64_t k) {
+    int a, b;
+    pair_slots(A, k, a, b);
+    const int code = (int)(k & 0xFFFull);
+    const int gx = (code & 15) - 7, gy = ((code >> 4) & 15) - 7, gz = ((code >> 8) & 15) - 7;
+    const BoxP bp = A.boxes[A.P.box[a]];
+    const double t = time_at(A.ctl, C, A.hs);
+    const double s = bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
+    const double ox = __dmul_rn((double)gx, bp.Lx);
+    const double oy = __dsub_rn(__dmul_rn((double)gy, bp.Ly), __dmul_rn((double)gx, s));
+    const double oz = __dmul_rn((double)gz, bp.Lz);
+    const double dvg = __dmul_rn(-(double)gx, bp.shear_speed);
+    const double rx = __dsub_rn(__dadd_rn(A.P.x[b], ox), A.P.x[a]);
+    const double ry = __dsub_rn(__dadd_rn(A.P.y[b], oy), A.P.y[a]);
+    const double rz = __dsub_rn(__dadd_rn(A.P.z[b], oz), A.P.z[a]);
+    double vxa = A.P.vx[a], vya = A.P.vy[a], vza = A.P.vz[a];
+    double vxb = A.P.vx[b], vyb = A.P.vy[b], vzb = A.P.vz[b];
+    const double ux = __dsub_rn(vxb, vxa), uy = __dsub_rn(__dadd_rn(vyb, dvg), vya),
+                 uz = __dsub_rn(vzb, vza);
+    const double rv = __dadd_rn(__dadd_rn(__dmul_rn(rx, ux), __dmul_rn(ry, uy)), __dmul_rn(rz, uz));
+    if (rv >= 0.0) return false;
+    const double rr =
+        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz)));
+    const double nx = __ddiv_rn(rx, rr), ny = __ddiv_rn(ry, rr), nz = __ddiv_rn(rz, rr);
+    const double vn = __dadd_rn(__dadd_rn(__dmul_rn(ux, nx), __dmul_rn(uy, ny)), __dmul_rn(uz, nz));
+    const double dlt = __dmul_rn(-__dadd_rn(1.0, C.eps), vn);
+    const double ma = A.P.m[a], mb = A.P.m[b];
+    const double mt = __dadd_rn(ma, mb);
+    const double fa = __dmul_rn(__ddiv_rn(mb, mt), dlt), fb = __dmul_rn(__ddiv_rn(ma, mt), dlt);
+    A.P.vx[a] = __dsub_rn(vxa, __dmul_rn(fa, nx));
+    A.P.vy[a] = __dsub_rn(vya, __dmul_rn(fa, ny));
+    A.P.vz[a] = __dsub_rn(vza, __dmul_rn(fa, nz));
+    A.P.vx[b] = __dadd_rn(vxb, __dmul_rn(fb, nx));
+    A.P.vy[b] = __dadd_rn(vyb, __dmul_rn(fb, ny));
+    A.P.vz[b] = __dadd_rn(vzb, __dmul_rn(fb, nz));
+    return true;
+}
+
+// Conflict-free rounds: a pending pair is resolved in a round when it is the
+// lowest pending pair of both its particles.  Pairs resolved together touch
+// disjoint particles, and every pair sees the results of all earlier pairs
+// that share a particle with it: the outcome equals resolving the sorted
+// queue one pair at a time.
+__global__ void __launch_bounds__(256) k_res_reset(ResolveArgs A) {
+    const int n = A.ctl->pair_n;
+    if (A.ctl->pending == 0) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (A.done[k]) continue;
+        int a, b;
+        pair_slots(A, A.key[k], a, b);
+        A.minp[a] = INT_MAX;
+        A.minp[b] = INT_MAX;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_res_claim(ResolveArgs A) {
+    const int n = A.ctl->pair_n;
+    if (A.ctl->pending == 0) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (A.done[k]) continue;
+        int a, b;
+        pair_slots(A, A.key[k], a, b);
+        atomicMin(&A.minp[a], k);
+        atomicMin(&A.minp[b], k);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_res_apply(ResolveArgs A, SimC C) {
+    const int n = A.ctl->pair_n;
+    if (A.ctl->pending == 0) return;
+    int nd = 0, nr = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (A.done[k]) continue;
+        int a, b;
+        pair_slots(A, A.key[k], a, b);
+        if (A.minp[a] == k && A.minp[b] == k) {
+            nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
+            A.done[k] = 1;
+            nd++;
+        }
+    }
+    if (nd) atomicSub(&A.ctl->pending, nd);
+    if (nr) atomicAdd(&A.ctl->resolved, nr);
+}
+
+// Whatever the rounds left: one thread, in queue order.
+__global__ void k_res_tail(ResolveArgs A, SimC C) {
+    if (A.ctl->pending == 0) return;
+    const int n = A.ctl->pair_n;
+    int nr = 0;
+    for (int k = 0; k < n; k++) {
+        if (A.done[k]) continue;
+        nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
+        A.done[k] = 1;
+    }
+    A.ctl->resolved += nr;
+    A.ctl->pending = 0;
+}
+
+__global__ void k_step_advance(Ctl* ctl) { ctl->step += 1; }
+
+// Energy terms of one box, per block: K, tidal, W, Px, Py, Pz, count.
+__global__ void __launch_bounds__(256) k_energy_partial(PSet P, const Ctl* ctl, SimC C,
+                                                        const double* __restrict__ phi, int box,
+                                                        double* __restrict__ partials) {
+    const int n = ctl->n_live;
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (P.box[i] != box) continue;
+        const double m = P.m[i];
+        const double vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
+        s[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        if (C.integrator == 1)
+            s[1] += m * (0.5 * (C.omega_z * C.omega_z) * (P.z[i] * P.z[i]) -
+                          1.5 * (C.omega * C.omega) * (P.x[i] * P.x[i]));
+        if (phi) s[2] += 0.5 * m * phi[i];
+        s[3] += m * vx;
+        s[4] += m * vy;
+        s[5] += m * vz;
+        s[6] += 1.0;
+    }
+    __shared__ double red[7][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+        double v = s[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int k = 0; k < 8; k++) v += red[threadIdx.x][k];
+        partials[threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_energy_final(const double* __restrict__ partials, int nparts,
+                               double* __restrict__ out7) {
+    const int q = threadIdx.x;
+    if (q >= 7) return;
+    double v = 0.0;
+    for (int k = 0; k < nparts; k++) v += partials[q * nparts + k];
+    out7[q] = v;
+}
+
+}  // namespace
+
+void drift_keys(const PSet& P, const Tree& T, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                int ncap, int ndrift, int half_step_offset, const double* ax, const double* ay,
+                const double* az, bool kick, cudaStream_t s) {
+    if (ncap <= 0) return;
+    DriftArgs A;
+    A.P = P; A.key = T.key; A.idx = T.idx; A.sbox = T.sbox; A.ctl = ctl; A.boxes = boxes;
+    A.ax = ax; A.ay = ay; A.az = az;
+    A.ncap = ncap; A.ndrift = ndrift; A.hs = half_step_offset; A.kick = kick;
+    k_drift_keys<<<ceil_div(ncap, 256), 256, 0, s>>>(A, C);
+}
+
+void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl* ctl,
+                      const SimC& C, int ncap, int box_bits, cudaStream_t s) {
+    if (ncap <= 0) return;
+    const int which = radix_sort(T.key, T.idx, T.key_alt, T.idx_alt, ncap, nullptr, 64,
+                                 C.nbox > 1 ? T.sbox : nullptr, box_bits, T.hist, s);
+    if (which == 1) {
+        // keep the sorted keys in T.key for the topology kernels
+        uint64_t* k = T.key; T.key = T.key_alt; T.key_alt = k;
+        uint32_t* v = T.idx; T.idx = T.idx_alt; T.idx_alt = v;
+    }
+    k_permute<<<ceil_div(ncap, 256), 256, 0, s>>>(src, dst, T.idx, PR.slot_of_id, ctl, ncap);
+    k_commit_live<<<1, 1, 0, s>>>(ctl);
+}
+
+void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s) {
+    k_pairs_prep<<<1, 1, 0, s>>>(ctl, PR.cap);
+    const int which = radix_sort(PR.key, PR.val, PR.key_alt, PR.val_alt, PR.cap, &ctl->pair_n, 60,
+                                 nullptr, 0, PR.hist, s);
+    if (which == 1) {
+        uint64_t* k = PR.key; PR.key = PR.key_alt; PR.key_alt = k;
+        uint32_t* v = PR.val; PR.val = PR.val_alt; PR.val_alt = v;
+    }
+}
+
+void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
+                   int half_step_offset, int rounds, cudaStream_t s) {
+    ResolveArgs A;
+    A.P = P; A.key = PR.key; A.slot_of_id = PR.slot_of_id; A.minp = PR.minp; A.done = PR.done;
+    A.ctl = ctl; A.boxes = boxes; A.hs = half_step_offset;
+    cudaMemsetAsync(PR.done, 0, (size_t)PR.cap, s);
+    const int grid = std::min(ceil_div(PR.cap, 256), 2 * 152);
+    for (int r = 0; r < rounds; r++) {
+        k_res_reset<<<grid, 256, 0, s>>>(A);
+        k_res_claim<<<grid, 256, 0, s>>>(A);
+        k_res_apply<<<grid, 256, 0, s>>>(A, C);
+    }
+    k_res_tail<<<1, 1, 0, s>>>(A, C);
+}
+
+void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
+                  double* partials, int nparts, double* out7, cudaStream_t s) {
+    k_energy_partial<<<nparts, 256, 0, s>>>(P, ctl, C, phi, box, partials);
+    k_energy_final<<<1, 32, 0, s>>>(partials, nparts, out7);
+}
+
+void step_advance(Ctl* ctl, cudaStream_t s) { k_step_advance<<<1, 1, 0, s>>>(ctl); }
+
+void clear_walk_stats(Ctl* ctl, cudaStream_t s) {
+    cudaMemsetAsync(&ctl->n_cell, 0, 4 * sizeof(unsigned long long), s);
+}
+
+}  // namespace rb

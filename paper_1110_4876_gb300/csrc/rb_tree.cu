@@ -1,0 +1,449 @@
+// rb_tree.cu -- the octree of Sect. 4.2 built from Morton-sorted particles,
+// its cell moments and the records the walks read.
+//
+// Cells are the key prefixes (3 bits per depth) shared by two or more
+// particles that split at the next depth (or sit at the depth cap of 21,
+// where they are leaf groups).  Cells with a single occupied octant are
+// skipped: they hold the same particles, centre of mass and quadrupole as
+// that octant and a wider cell is never accepted where the narrower one is
+// not, so the forces equal those of the paper's insertion tree.
+//
+// Between sorted particles i and i+1 ("split" i) the shared prefix depth is
+// delta_i.  A cell of depth v is a maximal run of splits with delta >= v that
+// contains a split with delta == v; its first such split is its
+// representative.  Range minima of delta come straight from the keys
+// (clz of the xor of the run's end keys), so each split finds its run with a
+// galloping search.  Cells are laid out in depth-first pre-order together
+// with one leaf entry per particle: entry order is (first particle, depth),
+// and a per-particle bitmask of the depths of cells starting there gives
+// every entry's position after one scan.
+#include <cfloat>
+
+#include "rb_internal.cuh"
+
+namespace rb {
+namespace {
+
+template <bool kMultiBox>
+__device__ __forceinline__ int lcp_level(const uint64_t* __restrict__ key,
+                                         const int32_t* __restrict__ box, int a, int b) {
+    if (kMultiBox && box[a] != box[b]) return -1;
+    const uint64_t x = key[a] ^ key[b];
+    if (x == 0ull) return kMaxDepth;
+    return (__clzll((long long)x) - 1) / 3;
+}
+
+// One thread per split i in [0, n - 2]: find the run of cell depth
+// v = delta_i; if i represents its cell, record the particle range and mark
+// the cell's depth in mask[first].
+template <bool kMultiBox>
+__global__ void __launch_bounds__(256) k_nodes(const uint64_t* __restrict__ key,
+                                               const int32_t* __restrict__ box,
+                                               const Ctl* __restrict__ ctl, int ncap,
+                                               int32_t* __restrict__ node_a,
+                                               int32_t* __restrict__ node_b,
+                                               int8_t* __restrict__ node_v,
+                                               uint32_t* __restrict__ mask) {
+    const int n = min(ctl->n_live, ncap);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int v = lcp_level<kMultiBox>(key, box, i, i + 1);
+    int8_t outv = -1;
+    if (v >= 0) {
+        // leftmost particle a with min(delta_a .. delta_i) >= v
+        int good = i, step = 1, bad = -1;
+        for (;;) {
+            const int c = i - step;
+            if (c < 0) { bad = -1; break; }
+            if (lcp_level<kMultiBox>(key, box, c, i + 1) < v) { bad = c; break; }
+            good = c;
+            step <<= 1;
+        }
+        while (good - bad > 1) {
+            const int mid = (good + bad) >> 1;
+            if (lcp_level<kMultiBox>(key, box, mid, i + 1) >= v) good = mid; else bad = mid;
+        }
+        const int a = good;
+        const bool rep = (a == i) || (lcp_level<kMultiBox>(key, box, a, i) > v);
+        if (rep) {
+            // rightmost particle b with min(delta_i .. delta_{b-1}) >= v
+            int g2 = i + 1, st = 1, b2 = n;
+            for (;;) {
+                const int c = i + 1 + st;
+                if (c >= n) { b2 = n; break; }
+                if (lcp_level<kMultiBox>(key, box, i, c) < v) { b2 = c; break; }
+                g2 = c;
+                st <<= 1;
+            }
+            while (b2 - g2 > 1) {
+                const int mid = (g2 + b2) >> 1;
+                if (lcp_level<kMultiBox>(key, box, i, mid) >= v) g2 = mid; else b2 = mid;
+            }
+            node_a[i] = a;
+            node_b[i] = g2;
+            outv = (int8_t)v;
+            atomicOr(&mask[a], 1u << v);
+        }
+    }
+    node_v[i] = outv;
+}
+
+__global__ void __launch_bounds__(256) k_entry_counts(const uint32_t* __restrict__ mask,
+                                                      const Ctl* __restrict__ ctl, int ncap,
+                                                      int32_t* __restrict__ start) {
+    const int n = min(ctl->n_live, ncap);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) start[i] = 1 + __popc(mask[i]);
+}
+
+// Entries in pre-order: cells (from their representative split) and leaves.
+__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ mask,
+                                              const int32_t* __restrict__ start,
+                                              const int32_t* __restrict__ node_a,
+                                              const int32_t* __restrict__ node_b,
+                                              const int8_t* __restrict__ node_v,
+                                              const Ctl* __restrict__ ctl, int ncap,
+                                              int32_t* __restrict__ e_first,
+                                              int32_t* __restrict__ e_count,
+                                              int32_t* __restrict__ e_skip,
+                                              int8_t* __restrict__ e_level,
+                                              int32_t* __restrict__ leaf_of) {
+    const int n = min(ctl->n_live, ncap);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t mk = mask[i];
+    const int li = start[i] + __popc(mk);
+    e_first[li] = i;
+    e_count[li] = 1;
+    e_skip[li] = li + 1;
+    e_level[li] = 22;
+    leaf_of[i] = li;
+    if (i < n - 1) {
+        const int v = node_v[i];
+        if (v >= 0) {
+            const int a = node_a[i], b = node_b[i];
+            const int idx = start[a] + __popc(mask[a] & ((1u << v) - 1u));
+            e_first[idx] = a;
+            e_count[idx] = b - a + 1;
+            e_skip[idx] = start[b + 1];
+            e_level[idx] = (int8_t)v;
+        }
+    }
+}
+
+// Box ranges in sorted order (empty boxes get empty ranges) and box roots.
+__global__ void __launch_bounds__(256) k_box_ranges(const int32_t* __restrict__ box,
+                                                    const Ctl* __restrict__ ctl, int ncap, int nbox,
+                                                    int32_t* __restrict__ box_first) {
+    const int n = min(ctl->n_live, ncap);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n == 0) {
+        if (p <= nbox) box_first[p] = 0;
+        return;
+    }
+    if (p >= n) return;
+    const int b = box[p];
+    const int prev = p == 0 ? -1 : box[p - 1];
+    for (int q = prev + 1; q <= b; q++) box_first[q] = p;
+    if (p == n - 1)
+        for (int q = b + 1; q <= nbox; q++) box_first[q] = n;
+}
+
+__global__ void k_box_roots(const int32_t* __restrict__ box_first,
+                            const int32_t* __restrict__ start, int nbox,
+                            int32_t* __restrict__ box_root) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    box_root[b] = box_first[b] < box_first[b + 1] ? start[box_first[b]] : -1;
+}
+
+// Parent links and child counts: a cell's children are entry k + 1 and then
+// each child's skip until the cell's own skip.
+__global__ void __launch_bounds__(256) k_link(const int32_t* __restrict__ e_skip,
+                                              const int8_t* __restrict__ e_level,
+                                              const Ctl* __restrict__ ctl, int ecap,
+                                              int32_t* __restrict__ e_parent,
+                                              int32_t* __restrict__ e_nchild) {
+    const int E = min(ctl->n_entries, ecap);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= E || e_level[k] == 22) return;
+    const int end = e_skip[k];
+    int c = k + 1, nc = 0;
+    while (c < end) {
+        e_parent[c] = k;
+        nc++;
+        c = e_skip[c];
+    }
+    e_nchild[k] = nc;
+}
+
+__global__ void __launch_bounds__(256) k_count_cells(const int8_t* __restrict__ e_level,
+                                                     Ctl* __restrict__ ctl, int ecap) {
+    const int E = min(ctl->n_entries, ecap);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool cell = k < E && e_level[k] != 22;
+    const unsigned b = __ballot_sync(0xffffffffu, cell);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&ctl->n_cells, __popc(b));
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+// Loads that bypass L1: moments written by other blocks of this kernel are
+// read only after their writers' fence + arrival count.
+__device__ __forceinline__ double4_32a ldcg_d4(const double4_32a* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ int ldcg_i8(const int8_t* p) {
+    return (int)__ldcg(reinterpret_cast<const signed char*>(p));
+}
+
+__device__ __forceinline__ void split_hilo(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+// Integer cell index of depth v along each axis, from a member's key.
+__device__ __forceinline__ void cell_index(uint64_t key, int v, double& ix, double& iy, double& iz) {
+    const int sh = kMaxDepth - v;
+    ix = (double)(compact3(key >> 2) >> sh);
+    iy = (double)(compact3(key >> 1) >> sh);
+    iz = (double)(compact3(key) >> sh);
+}
+
+struct GravRecArgs {
+    const double *x, *y, *z, *m;
+    const int32_t* box;
+    const uint64_t* key;
+    const BoxP* boxes;
+    const int32_t *e_first, *e_skip, *e_parent, *e_nchild, *leaf_of;
+    const int8_t* e_level;
+    int32_t* e_arrive;
+    double4_32a *d_a, *d_q0, *d_q1, *d_c;
+    float4 *ra, *rb, *rq0, *rq1, *rc_hi, *rc_lo;
+    const Ctl* ctl;
+    int ncap;
+    double crit_scale;  // 1 / theta^2
+    bool fp32, inside;
+};
+
+// Leaf records, then bottom-up cell moments: the last child to finish
+// computes its parent (atomic arrival count, no waiting).  A cell's moments
+// come from its children: M = sum M_c, centre of mass = sum M_c com_c / M,
+// Q = sum [Q_c + M_c (3 d d^T - |d|^2 I)], d = com_c - com (the traceless
+// quadrupole about the centre of mass; parallel-axis theorem).
+__global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int e = A.leaf_of[p];
+    {
+        const double x = A.x[p], y = A.y[p], z = A.z[p], m = A.m[p];
+        A.d_a[e] = make_double4_32a(x, y, z, -m);
+        if (A.fp32) {
+            float hx, lx, hy, ly, hz, lz;
+            split_hilo(x, hx, lx);
+            split_hilo(y, hy, ly);
+            split_hilo(z, hz, lz);
+            A.ra[e] = make_float4(hx, hy, hz, -(float)m);
+            A.rb[e] = make_float4(lx, ly, lz, __int_as_float(e + 1));
+        }
+    }
+    for (;;) {
+        const int k = A.e_parent[e];
+        if (k < 0) return;
+        __threadfence();
+        const int prev = atomicAdd(&A.e_arrive[k], 1);
+        if (prev != A.e_nchild[k] - 1) return;
+        __threadfence();
+        // all children of k are final: compute k
+        const int end = A.e_skip[k];
+        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int c = k + 1; c < end; c = __ldcg(&A.e_skip[c])) {
+            const double4_32a a = ldcg_d4(&A.d_a[c]);
+            const bool leaf = ldcg_i8(&A.e_level[c]) == 22;
+            const double mc = leaf ? -a.w : ldcg_d4(&A.d_q0[c]).x;
+            M += mc;
+            sx += mc * a.x;
+            sy += mc * a.y;
+            sz += mc * a.z;
+        }
+        const int v = A.e_level[k];
+        const int first = A.e_first[k];
+        const BoxP bp = A.boxes[A.box[first]];
+        const double w = ldexp(bp.L, -v);
+        double ix, iy, iz;
+        cell_index(A.key[first], v, ix, iy, iz);
+        const double lo = -0.5 * bp.L;
+        double cx, cy, cz;
+        if (M > 0.0) {
+            cx = sx / M; cy = sy / M; cz = sz / M;
+        } else {
+            cx = lo + (ix + 0.5) * w; cy = lo + (iy + 0.5) * w; cz = lo + (iz + 0.5) * w;
+        }
+        double q[6] = {0, 0, 0, 0, 0, 0};
+        for (int c = k + 1; c < end; c = __ldcg(&A.e_skip[c])) {
+            const double4_32a a = ldcg_d4(&A.d_a[c]);
+            const bool leaf = ldcg_i8(&A.e_level[c]) == 22;
+            double mc;
+            if (leaf) {
+                mc = -a.w;
+            } else {
+                const double4_32a q0 = ldcg_d4(&A.d_q0[c]);
+                const double4_32a q1 = ldcg_d4(&A.d_q1[c]);
+                mc = q0.x;
+                q[0] += q0.y; q[1] += q0.z; q[2] += q0.w;
+                q[3] += q1.x; q[4] += q1.y; q[5] += q1.z;
+            }
+            const double dx = a.x - cx, dy = a.y - cy, dz = a.z - cz;
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            q[0] += mc * (3.0 * dx * dx - d2);
+            q[1] += mc * (3.0 * dy * dy - d2);
+            q[2] += mc * (3.0 * dz * dz - d2);
+            q[3] += mc * (3.0 * dx * dy);
+            q[4] += mc * (3.0 * dx * dz);
+            q[5] += mc * (3.0 * dy * dz);
+        }
+        const bool group = v == kMaxDepth;   // leaf group: never used as a multipole
+        const double ww = w * w;
+        A.d_a[k] = make_double4_32a(cx, cy, cz, group ? __longlong_as_double(0x7ff0000000000000ll) : ww);
+        A.d_q0[k] = make_double4_32a(M, q[0], q[1], q[2]);
+        A.d_q1[k] = make_double4_32a(q[3], q[4], q[5], w);
+        // cell corner lo + i w, rounded as two separate operations
+        const double c0x = __dadd_rn(lo, __dmul_rn(ix, w)), c0y = __dadd_rn(lo, __dmul_rn(iy, w));
+        const double c0z = __dadd_rn(lo, __dmul_rn(iz, w));
+        if (A.inside) A.d_c[k] = make_double4_32a(c0x, c0y, c0z, w);
+        if (A.fp32) {
+            float hx, lx, hy, ly, hz, lz;
+            split_hilo(cx, hx, lx);
+            split_hilo(cy, hy, ly);
+            split_hilo(cz, hz, lz);
+            const float crit = group ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
+            A.ra[k] = make_float4(hx, hy, hz, crit);
+            A.rb[k] = make_float4(lx, ly, lz, __int_as_float(end));
+            A.rq0[k] = make_float4((float)M, (float)q[0], (float)q[1], (float)q[2]);
+            A.rq1[k] = make_float4((float)q[3], (float)q[4], (float)q[5], 0.f);
+            if (A.inside) {
+                split_hilo(c0x, hx, lx);
+                split_hilo(c0y, hy, ly);
+                split_hilo(c0z, hz, lz);
+                A.rc_hi[k] = make_float4(hx, hy, hz, (float)w);
+                A.rc_lo[k] = make_float4(lx, ly, lz, 0.f);
+            }
+        }
+        __threadfence();
+        e = k;
+    }
+}
+
+struct CollRecArgs {
+    const int32_t* box;
+    const uint64_t* key;
+    const BoxP* boxes;
+    const int32_t *e_first, *e_skip;
+    const int8_t* e_level;
+    float4 *ra, *rb;
+    const Ctl* ctl;
+    int ecap;
+    double rmax;
+};
+
+// Collision-search records (Sect. 5.2): per cell its geometric centre
+// (hi/lo) and the opening radius (sqrt(3)/2) w + R_max of Eq. 3, rounded up;
+// per leaf the particle slot.
+__global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
+    const int E = min(A.ctl->n_entries, A.ecap);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= E) return;
+    const int v = A.e_level[k];
+    const int first = A.e_first[k];
+    if (v == 22) {
+        A.ra[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(~first));
+        A.rb[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(k + 1));
+        return;
+    }
+    const BoxP bp = A.boxes[A.box[first]];
+    const double w = ldexp(bp.L, -v);
+    const double lo = -0.5 * bp.L;
+    double ix, iy, iz;
+    cell_index(A.key[first], v, ix, iy, iz);
+    float hx, lx, hy, ly, hz, lz;
+    split_hilo(lo + (ix + 0.5) * w, hx, lx);
+    split_hilo(lo + (iy + 0.5) * w, hy, ly);
+    split_hilo(lo + (iz + 0.5) * w, hz, lz);
+    const float h = __double2float_ru(0.8660254037844387 * w + A.rmax);
+    A.ra[k] = make_float4(hx, hy, hz, h);
+    A.rb[k] = make_float4(lx, ly, lz, __int_as_float(A.e_skip[k]));
+}
+
+}  // namespace
+
+void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                    cudaStream_t s) {
+    const int n = T.cap_n;
+    if (n <= 0) return;
+    const int nb = ceil_div(n, 256);
+    cudaMemsetAsync(T.mask, 0, sizeof(uint32_t) * n, s);
+    if (C.nbox > 1)
+        k_nodes<true><<<nb, 256, 0, s>>>(T.key, P.box, ctl, n, T.node_a, T.node_b, T.node_v, T.mask);
+    else
+        k_nodes<false><<<nb, 256, 0, s>>>(T.key, P.box, ctl, n, T.node_a, T.node_b, T.node_v,
+                                          T.mask);
+    k_entry_counts<<<nb, 256, 0, s>>>(T.mask, ctl, n, T.start);
+    exclusive_scan_i32(T.start, n, &ctl->n_live, T.scan_part, &ctl->n_entries, s);
+    k_emit<<<nb, 256, 0, s>>>(T.mask, T.start, T.node_a, T.node_b, T.node_v, ctl, n, T.e_first,
+                              T.e_count, T.e_skip, T.e_level, T.leaf_of);
+    k_box_ranges<<<ceil_div(n > C.nbox + 1 ? n : C.nbox + 1, 256), 256, 0, s>>>(
+        P.box, ctl, n, C.nbox, T.box_first);
+    k_box_roots<<<ceil_div(C.nbox, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
+    const int ne = T.cap_e;
+    cudaMemsetAsync(T.e_parent, 0xff, sizeof(int32_t) * ne, s);
+    k_link<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_skip, T.e_level, ctl, ne, T.e_parent, T.e_nchild);
+    cudaMemsetAsync(&ctl->n_cells, 0, sizeof(int), s);
+    k_count_cells<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_level, ctl, ne);
+}
+
+void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
+                           const SimC& C, bool fp64, cudaStream_t s) {
+    const int n = T.cap_n;
+    if (n <= 0) return;
+    cudaMemsetAsync(T.e_arrive, 0, sizeof(int32_t) * T.cap_e, s);
+    GravRecArgs A;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.box = P.box;
+    A.key = T.key; A.boxes = boxes;
+    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_parent = T.e_parent;
+    A.e_nchild = T.e_nchild; A.leaf_of = T.leaf_of; A.e_level = T.e_level;
+    A.e_arrive = T.e_arrive;
+    A.d_a = reinterpret_cast<double4_32a*>(T.d_a);
+    A.d_q0 = reinterpret_cast<double4_32a*>(T.d_q0);
+    A.d_q1 = reinterpret_cast<double4_32a*>(T.d_q1);
+    A.d_c = reinterpret_cast<double4_32a*>(T.d_c);
+    A.ra = T.ra; A.rb = T.rb; A.rq0 = T.rq0; A.rq1 = T.rq1; A.rc_hi = T.rc_hi; A.rc_lo = T.rc_lo;
+    A.ctl = ctl;
+    A.ncap = n;
+    A.crit_scale = C.crit_scale;
+    A.fp32 = !fp64;
+    A.inside = C.theta2 > (1.0 / 3.0);
+    k_moments<<<ceil_div(n, 256), 256, 0, s>>>(A);
+}
+
+void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
+                             const SimC& C, double rmax, cudaStream_t s) {
+    CollRecArgs A;
+    A.box = P.box; A.key = T.key; A.boxes = boxes;
+    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level;
+    A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
+    k_coll_records<<<ceil_div(T.cap_e, 256), 256, 0, s>>>(A);
+}
+
+}  // namespace rb

@@ -1,0 +1,501 @@
+// rb_walk.cu -- Barnes-Hut gravity walk (Sect. 4.2, Eq. 1) and tree
+// collision search (Sect. 5.2, Eq. 3) over the ghost images of Sect. 2.3.
+//
+// Warp-cooperative stackless walk.  Each warp owns 32 consecutive targets in
+// Morton order (spatially close); each lane keeps its own "next entry" in the
+// pre-order entry array, exactly as a per-particle stackless walk would.  The
+// warp always processes the smallest next entry of its lanes (one __reduce_min
+// vote); that entry's record is a broadcast load, and only the lanes whose
+// next entry it is evaluate their own opening test.  Every lane therefore
+// accepts, opens and interacts with exactly the cells of its own walk, so the
+// accepted cell sets equal the oracle's; lanes skip the entries their own
+// walk does not visit.
+//
+// FP32 walk: the target point and every centre of mass are hi/lo float pairs,
+// so (hi_c - hi_p) + (lo_c - lo_p) keeps ~1e-7 relative accuracy even for
+// neighbours a metre apart in a 2 km box.  An opening test whose two sides
+// differ by less than 1e-5 relative is decided again in FP64 on the FP64
+// centre of mass, with the same operation sequence as the oracle.
+#include <cfloat>
+
+#include "rb_internal.cuh"
+
+namespace rb {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct GravArgs {
+    const double *x, *y, *z;
+    const int32_t* box;
+    const float4 *ra, *rb, *rq0, *rq1, *rc_hi, *rc_lo;
+    const double4_32a *d_a, *d_q0, *d_q1, *d_c;
+    const int32_t *e_skip, *leaf_of, *box_root;
+    const BoxP* boxes;
+    Ctl* ctl;
+    WalkOut out;
+    int ncap;
+    int ngx, ngy, ngz;
+    int half_step_offset;
+    double G, theta2, soft2, t0, half_dt;
+    float soft2f;
+};
+
+__device__ __forceinline__ double4_32a ld_d4(const double4_32a* p) { return *p; }
+
+__device__ __forceinline__ double time_of(const Ctl* ctl, double t0, double half_dt, int hs) {
+    const double h = (double)(2 * ctl->step + hs);
+    return __dadd_rn(t0, __dmul_rn(h, half_dt));
+}
+
+// Image offset (gx Lx, gy Ly - gx s, gz Lz), evaluated without contraction.
+__device__ __forceinline__ void image_offset(const BoxP& bp, double s, int gx, int gy, int gz,
+                                             double& ox, double& oy, double& oz) {
+    ox = __dmul_rn((double)gx, bp.Lx);
+    oy = __dsub_rn(__dmul_rn((double)gy, bp.Ly), __dmul_rn((double)gx, s));
+    oz = __dmul_rn((double)gz, bp.Lz);
+}
+
+__device__ __forceinline__ double shear_offset(const BoxP& bp, double t) {
+    return bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
+}
+
+// Opening test in FP64, operation for operation as the oracle evaluates it.
+__device__ __forceinline__ bool mac64(const double4_32a& a, double theta2, double tx, double ty,
+                                      double tz) {
+    const double dx = __dsub_rn(a.x, tx), dy = __dsub_rn(a.y, ty), dz = __dsub_rn(a.z, tz);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return a.w < __dmul_rn(theta2, r2);
+}
+
+// Is the target point inside the closed cube of a cell (FP64, exact sequence)?
+__device__ __forceinline__ bool inside64(const double4_32a& c, double tx, double ty, double tz) {
+    return c.x <= tx && tx <= __dadd_rn(c.x, c.w) && c.y <= ty && ty <= __dadd_rn(c.y, c.w) &&
+           c.z <= tz && tz <= __dadd_rn(c.z, c.w);
+}
+
+template <bool kQuad, bool kInside, bool kPot, bool kSoft>
+__global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (wbase >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int i = wbase + lane;
+    const bool valid = i < n;
+    const int ii = valid ? i : n - 1;
+    const double px = A.x[ii], py = A.y[ii], pz = A.z[ii];
+    const BoxP bp = A.boxes[A.box[ii]];
+    const int root = A.box_root[A.box[ii]];
+    const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
+    const int self_leaf = A.leaf_of[ii];
+    const double t = time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset);
+    const double s = shear_offset(bp, t);
+    double ax = 0.0, ay = 0.0, az = 0.0, pot = 0.0;
+    int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0;
+    for (int gx = -A.ngx; gx <= A.ngx; gx++)
+        for (int gy = -A.ngy; gy <= A.ngy; gy++)
+            for (int gz = -A.ngz; gz <= A.ngz; gz++) {
+                double ox, oy, oz;
+                image_offset(bp, s, gx, gy, gz, ox, oy, oz);
+                const double tx = __dsub_rn(px, ox), ty = __dsub_rn(py, oy), tz = __dsub_rn(pz, oz);
+                const float thx = __double2float_rn(tx), thy = __double2float_rn(ty),
+                            thz = __double2float_rn(tz);
+                const float tlx = __double2float_rn(tx - (double)thx);
+                const float tly = __double2float_rn(ty - (double)thy);
+                const float tlz = __double2float_rn(tz - (double)thz);
+                const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
+                int next = (valid && root >= 0) ? root : kEnd;
+                float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
+                for (;;) {
+                    if (next >= wend) next = kEnd;
+                    const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
+                    if (e == kEnd) break;
+                    const float4 ra = __ldg(&A.ra[e]);
+                    const float4 rb = __ldg(&A.rb[e]);
+                    const bool act = next == e;
+                    const float dx = (ra.x - thx) + (rb.x - tlx);
+                    const float dy = (ra.y - thy) + (rb.y - tly);
+                    const float dz = (ra.z - thz) + (rb.z - tlz);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (__float_as_int(ra.w) < 0) {
+                        // particle leaf: exact term of Eq. 1
+                        if (act) {
+                            if (e != self) {
+                                const float m = -ra.w;
+                                const float inv = rsqrtf(kSoft ? r2 + A.soft2f : r2);
+                                const float f = m * (inv * inv * inv);
+                                fx += f * dx;
+                                fy += f * dy;
+                                fz += f * dz;
+                                if (kPot) fp -= m * inv;
+                                nleaf++;
+                            }
+                            next = e + 1;
+                        }
+                    } else if (act) {
+                        nmac++;
+                        bool acc = ra.w < r2;
+                        if (fabsf(ra.w - r2) <= 1e-5f * r2) {
+                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, tx, ty, tz);
+                            nrecheck++;
+                        }
+                        if (kInside && acc) {
+                            const float4 ch = __ldg(&A.rc_hi[e]);
+                            const float4 cl = __ldg(&A.rc_lo[e]);
+                            const float ux = (thx - ch.x) + (tlx - cl.x);
+                            const float uy = (thy - ch.y) + (tly - cl.y);
+                            const float uz = (thz - ch.z) + (tlz - cl.z);
+                            const float w = ch.w, tol = 1e-5f * ch.w;
+                            const float mx = fminf(fminf(ux, w - ux), fminf(fminf(uy, w - uy), fminf(uz, w - uz)));
+                            if (fabsf(mx) <= tol) {
+                                acc = !inside64(ld_d4(&A.d_c[e]), tx, ty, tz);
+                                nrecheck++;
+                            } else if (mx > 0.f) {
+                                acc = false;
+                            }
+                        }
+                        if (acc) {
+                            const float4 q0 = __ldg(&A.rq0[e]);
+                            const float inv = rsqrtf(r2);
+                            const float inv2 = inv * inv;
+                            const float invs = kSoft ? rsqrtf(r2 + A.soft2f) : inv;
+                            const float f = q0.x * (invs * invs * invs);
+                            fx += f * dx;
+                            fy += f * dy;
+                            fz += f * dz;
+                            if (kPot) fp -= q0.x * invs;
+                            if (kQuad) {
+                                const float4 q1 = __ldg(&A.rq1[e]);
+                                const float qx = q0.y * dx + q1.x * dy + q1.y * dz;
+                                const float qy = q1.x * dx + q0.z * dy + q1.z * dz;
+                                const float qz = q1.y * dx + q1.z * dy + q0.w * dz;
+                                const float dqd = dx * qx + dy * qy + dz * qz;
+                                const float inv5 = inv2 * inv2 * inv;
+                                const float c = 2.5f * dqd * (inv5 * inv2);
+                                fx += c * dx - inv5 * qx;
+                                fy += c * dy - inv5 * qy;
+                                fz += c * dz - inv5 * qz;
+                                if (kPot) fp -= 0.5f * dqd * inv5;
+                            }
+                            ncell++;
+                            next = __float_as_int(rb.w);
+                        } else {
+                            next = e + 1;
+                        }
+                    }
+                }
+                ax += (double)fx;
+                ay += (double)fy;
+                az += (double)fz;
+                pot += (double)fp;
+            }
+    if (valid) {
+        A.out.ax[i] = A.G * ax;
+        A.out.ay[i] = A.G * ay;
+        A.out.az[i] = A.G * az;
+        if (kPot) A.out.phi[i] = A.G * pot;
+        if (A.out.ncell) {
+            A.out.ncell[i] = ncell;
+            A.out.nleaf[i] = nleaf;
+            A.out.nmac[i] = nmac;
+        }
+    }
+    // warp totals of the counters
+    unsigned long long c0 = valid ? ncell : 0, c1 = valid ? nleaf : 0, c2 = valid ? nmac : 0,
+                       c3 = valid ? nrecheck : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_down_sync(kFull, c0, o);
+        c1 += __shfl_down_sync(kFull, c1, o);
+        c2 += __shfl_down_sync(kFull, c2, o);
+        c3 += __shfl_down_sync(kFull, c3, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.ctl->n_cell, c0);
+        atomicAdd(&A.ctl->n_leaf, c1);
+        atomicAdd(&A.ctl->n_mac, c2);
+        atomicAdd(&A.ctl->n_recheck, c3);
+    }
+}
+
+// FP64 walk: the same traversal on FP64 records, every opening test in the
+// oracle's operation sequence.
+template <bool kQuad, bool kInside, bool kPot>
+__global__ void __launch_bounds__(128) k_walk64(GravArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (wbase >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int i = wbase + lane;
+    const bool valid = i < n;
+    const int ii = valid ? i : n - 1;
+    const double px = A.x[ii], py = A.y[ii], pz = A.z[ii];
+    const BoxP bp = A.boxes[A.box[ii]];
+    const int root = A.box_root[A.box[ii]];
+    const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
+    const int self_leaf = A.leaf_of[ii];
+    const double t = time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset);
+    const double s = shear_offset(bp, t);
+    const double soft2 = A.soft2;
+    double ax = 0.0, ay = 0.0, az = 0.0, pot = 0.0;
+    int ncell = 0, nleaf = 0, nmac = 0;
+    for (int gx = -A.ngx; gx <= A.ngx; gx++)
+        for (int gy = -A.ngy; gy <= A.ngy; gy++)
+            for (int gz = -A.ngz; gz <= A.ngz; gz++) {
+                double ox, oy, oz;
+                image_offset(bp, s, gx, gy, gz, ox, oy, oz);
+                const double tx = __dsub_rn(px, ox), ty = __dsub_rn(py, oy), tz = __dsub_rn(pz, oz);
+                const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
+                int next = (valid && root >= 0) ? root : kEnd;
+                for (;;) {
+                    if (next >= wend) next = kEnd;
+                    const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
+                    if (e == kEnd) break;
+                    const double4_32a a = ld_d4(&A.d_a[e]);
+                    const bool act = next == e;
+                    if (__double_as_longlong(a.w) < 0) {
+                        if (act) {
+                            if (e != self) {
+                                const double dx = a.x - tx, dy = a.y - ty, dz = a.z - tz;
+                                const double r2 = dx * dx + dy * dy + dz * dz + soft2;
+                                const double inv = rsqrt(r2);
+                                const double f = -a.w * (inv * inv * inv);
+                                ax += f * dx;
+                                ay += f * dy;
+                                az += f * dz;
+                                if (kPot) pot += a.w * inv;
+                                nleaf++;
+                            }
+                            next = e + 1;
+                        }
+                    } else if (act) {
+                        nmac++;
+                        bool acc = mac64(a, A.theta2, tx, ty, tz);
+                        if (kInside && acc) acc = !inside64(ld_d4(&A.d_c[e]), tx, ty, tz);
+                        if (acc) {
+                            const double4_32a q0 = ld_d4(&A.d_q0[e]);
+                            const double dx = a.x - tx, dy = a.y - ty, dz = a.z - tz;
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            const double invs = rsqrt(r2 + soft2);
+                            const double f = q0.x * (invs * invs * invs);
+                            ax += f * dx;
+                            ay += f * dy;
+                            az += f * dz;
+                            if (kPot) pot -= q0.x * invs;
+                            if (kQuad) {
+                                const double4_32a q1 = ld_d4(&A.d_q1[e]);
+                                const double inv = rsqrt(r2);
+                                const double inv2 = inv * inv;
+                                const double qx = q0.y * dx + q1.x * dy + q1.y * dz;
+                                const double qy = q1.x * dx + q0.z * dy + q1.z * dz;
+                                const double qz = q1.y * dx + q1.z * dy + q0.w * dz;
+                                const double dqd = dx * qx + dy * qy + dz * qz;
+                                const double inv5 = inv2 * inv2 * inv;
+                                const double c = 2.5 * dqd * (inv5 * inv2);
+                                ax += c * dx - inv5 * qx;
+                                ay += c * dy - inv5 * qy;
+                                az += c * dz - inv5 * qz;
+                                if (kPot) pot -= 0.5 * dqd * inv5;
+                            }
+                            ncell++;
+                            next = A.e_skip[e];
+                        } else {
+                            next = e + 1;
+                        }
+                    }
+                }
+            }
+    if (valid) {
+        A.out.ax[i] = A.G * ax;
+        A.out.ay[i] = A.G * ay;
+        A.out.az[i] = A.G * az;
+        if (kPot) A.out.phi[i] = A.G * pot;
+        if (A.out.ncell) {
+            A.out.ncell[i] = ncell;
+            A.out.nleaf[i] = nleaf;
+            A.out.nmac[i] = nmac;
+        }
+    }
+    unsigned long long c0 = valid ? ncell : 0, c1 = valid ? nleaf : 0, c2 = valid ? nmac : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_down_sync(kFull, c0, o);
+        c1 += __shfl_down_sync(kFull, c1, o);
+        c2 += __shfl_down_sync(kFull, c2, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.ctl->n_cell, c0);
+        atomicAdd(&A.ctl->n_leaf, c1);
+        atomicAdd(&A.ctl->n_mac, c2);
+    }
+}
+
+struct CollArgs {
+    const double *x, *y, *z, *r;
+    const int32_t *id, *box;
+    const float4 *ra, *rb;
+    const int32_t *box_root, *e_skip;
+    const BoxP* boxes;
+    Ctl* ctl;
+    uint64_t* pair_key;
+    int pair_cap;
+    int ncap;
+    int ngx, ngy, ngz;
+    int half_step_offset;
+    double t0, half_dt;
+};
+
+// Tree collision search (Sect. 5.2): descend while the distance from the
+// target point to a cell's centre is below R_i + R_max + (sqrt(3)/2) w (Eq. 3,
+// tested in FP32 with a 2e-5 relative margin so that no overlap is pruned);
+// at a leaf j the overlap test of Sect. 5.1 runs in FP64 in the oracle's
+// operation order on the canonical orientation (lower id a, image of b).
+// Only the lower-id particle of a pair records it, so each overlap is found
+// once: the higher-id particle would see it through the opposite image.
+__global__ void __launch_bounds__(128) k_collide(CollArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
+    if (wbase >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int i = wbase + lane;
+    const bool valid = i < n;
+    const int ii = valid ? i : n - 1;
+    const double px = A.x[ii], py = A.y[ii], pz = A.z[ii], pr = A.r[ii];
+    const int pid = A.id[ii];
+    const BoxP bp = A.boxes[A.box[ii]];
+    const int root = A.box_root[A.box[ii]];
+    const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
+    const double t = time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset);
+    const double s = shear_offset(bp, t);
+    const float prf = (float)pr;
+    for (int gx = -A.ngx; gx <= A.ngx; gx++)
+        for (int gy = -A.ngy; gy <= A.ngy; gy++)
+            for (int gz = -A.ngz; gz <= A.ngz; gz++) {
+                double ox, oy, oz;
+                image_offset(bp, s, gx, gy, gz, ox, oy, oz);
+                const int code = (gx + 7) | ((gy + 7) << 4) | ((gz + 7) << 8);
+                const double tx = __dsub_rn(px, ox), ty = __dsub_rn(py, oy), tz = __dsub_rn(pz, oz);
+                const float thx = __double2float_rn(tx), thy = __double2float_rn(ty),
+                            thz = __double2float_rn(tz);
+                const float tlx = __double2float_rn(tx - (double)thx);
+                const float tly = __double2float_rn(ty - (double)thy);
+                const float tlz = __double2float_rn(tz - (double)thz);
+                int next = (valid && root >= 0) ? root : kEnd;
+                for (;;) {
+                    if (next >= wend) next = kEnd;
+                    const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
+                    if (e == kEnd) break;
+                    const float4 ra = __ldg(&A.ra[e]);
+                    const bool act = next == e;
+                    bool hit = false;
+                    uint64_t key = 0;
+                    if (__float_as_int(ra.w) < 0) {
+                        if (act) {
+                            const int j = ~__float_as_int(ra.w);
+                            if (j != i) {
+                                const int jid = A.id[j];
+                                if (pid < jid) {
+                                    const double rx = __dsub_rn(__dadd_rn(A.x[j], ox), px);
+                                    const double ry = __dsub_rn(__dadd_rn(A.y[j], oy), py);
+                                    const double rz = __dsub_rn(__dadd_rn(A.z[j], oz), pz);
+                                    const double r2 = __dadd_rn(
+                                        __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)),
+                                        __dmul_rn(rz, rz));
+                                    const double sr = __dadd_rn(pr, A.r[j]);
+                                    if (r2 < __dmul_rn(sr, sr)) {
+                                        hit = true;
+                                        key = ((uint64_t)pid << 36) | ((uint64_t)jid << 12) |
+                                              (uint64_t)code;
+                                    }
+                                }
+                            }
+                            next = e + 1;
+                        }
+                    } else if (act) {
+                        const float4 rb = __ldg(&A.rb[e]);
+                        const float dx = (ra.x - thx) + (rb.x - tlx);
+                        const float dy = (ra.y - thy) + (rb.y - tly);
+                        const float dz = (ra.z - thz) + (rb.z - tlz);
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        const float lim = (prf + ra.w) * 1.00002f;
+                        next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
+                    }
+                    const unsigned hits = __ballot_sync(kFull, hit);
+                    if (hits) {
+                        int base = 0;
+                        const int leader = __ffs(hits) - 1;
+                        if (lane == leader) base = atomicAdd(&A.ctl->pair_count, __popc(hits));
+                        base = __shfl_sync(kFull, base, leader);
+                        if (hit) {
+                            const int slot = base + __popc(hits & ((1u << lane) - 1u));
+                            if (slot < A.pair_cap) A.pair_key[slot] = key;
+                            else atomicOr(&A.ctl->err, kErrPairOverflow);
+                        }
+                    }
+                }
+            }
+}
+
+}  // namespace
+
+void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                  int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
+                  bool counts, cudaStream_t s) {
+    if (T.cap_n <= 0) return;
+    GravArgs A;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.box = P.box;
+    A.ra = T.ra; A.rb = T.rb; A.rq0 = T.rq0; A.rq1 = T.rq1; A.rc_hi = T.rc_hi; A.rc_lo = T.rc_lo;
+    A.d_a = reinterpret_cast<const double4_32a*>(T.d_a);
+    A.d_q0 = reinterpret_cast<const double4_32a*>(T.d_q0);
+    A.d_q1 = reinterpret_cast<const double4_32a*>(T.d_q1);
+    A.d_c = reinterpret_cast<const double4_32a*>(T.d_c);
+    A.e_skip = T.e_skip; A.leaf_of = T.leaf_of; A.box_root = T.box_root;
+    A.boxes = boxes; A.ctl = ctl;
+    A.out = out;
+    if (!counts) { A.out.ncell = nullptr; A.out.nleaf = nullptr; A.out.nmac = nullptr; }
+    A.ncap = T.cap_n;
+    A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
+    A.half_step_offset = half_step_offset;
+    A.G = C.G; A.theta2 = C.theta2; A.soft2 = C.soft2; A.t0 = C.t0; A.half_dt = C.half_dt;
+    A.soft2f = (float)C.soft2;
+    const bool inside = C.theta2 > (1.0 / 3.0);
+    const bool quad = C.quadrupole != 0;
+    const bool soft = C.soft2 > 0.0;
+    const int grid = ceil_div(T.cap_n, 128);
+#define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, 128, 0, s>>>(A)
+#define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, 128, 0, s>>>(A)
+    if (walk_mode == 0 || potential) {
+        if (quad) {
+            if (inside) { if (potential) RB_W64(true, true, true); else RB_W64(true, true, false); }
+            else { if (potential) RB_W64(true, false, true); else RB_W64(true, false, false); }
+        } else {
+            if (inside) { if (potential) RB_W64(false, true, true); else RB_W64(false, true, false); }
+            else { if (potential) RB_W64(false, false, true); else RB_W64(false, false, false); }
+        }
+    } else {
+        if (quad) {
+            if (inside) { if (soft) RB_W32(true, true, false, true); else RB_W32(true, true, false, false); }
+            else { if (soft) RB_W32(true, false, false, true); else RB_W32(true, false, false, false); }
+        } else {
+            if (inside) { if (soft) RB_W32(false, true, false, true); else RB_W32(false, true, false, false); }
+            else { if (soft) RB_W32(false, false, false, true); else RB_W32(false, false, false, false); }
+        }
+    }
+#undef RB_W32
+#undef RB_W64
+}
+
+void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                      const Pairs& PR, int half_step_offset, cudaStream_t s) {
+    if (T.cap_n <= 0) return;
+    CollArgs A;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r; A.id = P.id; A.box = P.box;
+    A.ra = T.ra; A.rb = T.rb; A.box_root = T.box_root; A.e_skip = T.e_skip; A.boxes = boxes;
+    A.ctl = ctl;
+    A.pair_key = PR.key; A.pair_cap = PR.cap; A.ncap = T.cap_n;
+    A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
+    A.half_step_offset = half_step_offset; A.t0 = C.t0; A.half_dt = C.half_dt;
+    k_collide<<<ceil_div(T.cap_n, 128), 128, 0, s>>>(A);
+}
+
+}  // namespace rb

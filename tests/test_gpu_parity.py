@@ -1,0 +1,224 @@
+"""GPU-vs-oracle parity through the C ABI (librb on cuda:0).
+
+Forces: FP64 walk within 1e-12 of the oracle's tree at the same theta with
+identical per-particle counts of accepted cells and exact particle terms;
+FP32 walk within max relative error 1e-5 (per-particle denominator floored at
+1e-3 of the rms force).  Tree: identical cell sets, moments to rounding.
+Collisions: bit-identical pair sets.  Trajectories: 1e-9 relative after 10
+FP64 steps; bit-identical without gravity."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1110_4876_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rb():
+    from paper_1110_4876_gb300 import build, rb as _rb
+
+    build.build()
+    _rb.load()
+    return _rb
+
+
+def sheet_cfg(rb, L, walk, theta=0.5, **kw):
+    c = dict(G=I.G_SI, omega=I.OMEGA, box=(L, L, L), nghost=(1, 1, 0), boundary=rb.RB_BC_SHEAR,
+             integrator=rb.RB_INT_SEI, theta=theta, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1,
+             walk=walk)
+    c.update(kw)
+    return c
+
+
+def sheet_params(orc, L, theta=0.5, **kw):
+    p = orc.Params(G=I.G_SI, omega=I.OMEGA, L=(L, L, L), nghost=(1, 1, 0), boundary=2, integrator=1,
+                   theta=theta, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+FP32_TOL = 1e-5
+FP64_TOL = 1e-12
+
+
+@pytest.mark.parametrize("L,N,seed", [(100.0, 2400, 1), (160.0, 6000, 7)])
+def test_tree_cells_and_moments(rb, orc, L, N, seed):
+    P = I.sheet(L, N, seed)
+    sim = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP64))
+    sim.set_particles(P)
+    sim.gravity()
+    got = rb.rb_get_tree(sim.h)
+    ref = orc.Tree(P.x, P.y, P.z, P.m, L).cells()
+    gs = {(d, frozenset(m.tolist())): (M, c, Q) for d, m, M, c, Q in got}
+    rs = {(d, frozenset(m.tolist())): (M, c, Q) for d, m, M, c, Q in ref}
+    assert len(gs) == len(got)
+    assert set(gs) == set(rs)
+    # the GPU sums children bottom-up, the oracle sums members in insertion
+    # order: both are within n u (n <= 6000 terms, u = 1.1e-16) of the exact sums
+    for k, (M, c, Q) in rs.items():
+        gM, gc, gQ = gs[k]
+        w = L / 2 ** k[0]
+        assert abs(gM - M) <= 1e-12 * M
+        assert np.max(np.abs(gc - c)) <= 1e-12 * L
+        assert np.max(np.abs(gQ - Q)) <= 1e-10 * M * w * w
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5])
+def test_fp64_walk_matches_oracle_tree(rb, orc, theta):
+    L, N = 100.0, 2400
+    P = I.sheet(L, N, 1)
+    sim = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP64, theta=theta))
+    sim.set_particles(P)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    p = sheet_params(orc, L, theta)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, P.x, P.y, P.z, P.m, counts=True)
+    assert orc.force_errors(a, a_ref)[2] <= FP64_TOL
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
+
+
+@pytest.mark.parametrize("theta,quad", [(0.5, 1), (0.5, 0), (0.3, 1)])
+def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad):
+    L, N = 160.0, 6000
+    P = I.sheet(L, N, 7)
+    sim = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP32, theta=theta, quadrupole=quad))
+    sim.set_particles(P)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    p = sheet_params(orc, L, theta, quadrupole=quad)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, P.x, P.y, P.z, P.m, counts=True)
+    e = orc.force_errors(a, a_ref)
+    assert e[2] <= FP32_TOL, e
+    # the guarded opening test reproduces the oracle's accepted sets
+    assert np.mean(nc == rc) > 0.999 and np.mean(nl == rl) > 0.999
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_plummer_open_inside_rule(rb, orc, walk):
+    """theta = 0.7 > 1/sqrt(3): the target-inside-cell rule is active."""
+    N = 5000
+    P = I.plummer(N, 3)
+    cfg = dict(G=1.0, box=(128.0,) * 3, boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG,
+               theta=0.7, softening=1e-3, dt=1e-3, gravity=1, collisions=0, walk=walk)
+    sim = rb.Sim(**cfg)
+    sim.set_particles(P)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    p = orc.Params(G=1.0, L=(128.0,) * 3, theta=0.7, soft=1e-3, dt=1e-3, gravity=1)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, P.x, P.y, P.z, P.m, counts=True)
+    e = orc.force_errors(a, a_ref)
+    assert e[2] <= (FP64_TOL if walk == 0 else FP32_TOL), e
+    if walk == 0:
+        np.testing.assert_array_equal(nc, rc)
+        np.testing.assert_array_equal(nl, rl)
+
+
+@pytest.mark.parametrize("boundary,seed", [(0, 1), (1, 2), (2, 3)])
+def test_pair_sets_bit_identical(rb, orc, boundary, seed):
+    L, n = 30.0, 1500
+    g = np.random.default_rng(seed)
+    x, y = g.uniform(-L / 2, L / 2, (2, n))
+    z = g.normal(0, 1.0, n)
+    r = g.uniform(0.3, 0.6, n)
+    zero = np.zeros(n)
+    cfg = dict(G=1.0, omega=0.02, box=(L, L, L), nghost=(1, 1, 0), boundary=boundary,
+               integrator=rb.RB_INT_LEAPFROG, gravity=0, collisions=1, dt=0.1, t0=123.4)
+    sim = rb.Sim(**cfg)
+    sim.set_particles((x, y, z, zero, zero, zero, np.ones(n), r))
+    a, b, c = sim.pairs()
+    p = orc.Params(omega=0.02, L=(L, L, L), nghost=(1, 1, 0), boundary=boundary, t0=123.4, dt=0.1)
+    ref = orc.collide_brute(p, 123.4, x, y, z, r, np.arange(n))
+    got = rb.pair_keys(a, b, c)
+    assert len(ref) > 100
+    assert np.array_equal(got, ref)
+
+
+def _arrays(d):
+    return np.stack([d[k] for k in ("x", "y", "z", "vx", "vy", "vz")], axis=1)
+
+
+def test_trajectory_10_steps_fp64(rb, orc):
+    """10 DKD steps of the small sheet (SEI, tree gravity, collisions)."""
+    L, N = 100.0, 2400
+    P = I.sheet(L, N, 1)
+    sim = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP64))
+    sim.set_particles(P)
+    sim.step(10)
+    got = sim.particles()
+    st = orc.State(sheet_params(orc, L), *P.arrays())
+    st.step(10)
+    assert got["id"].tolist() == st.id.tolist()
+    ref = np.stack([st.x, st.y, st.z, st.vx, st.vy, st.vz], axis=1)
+    g = _arrays(got)
+    scale_x = L
+    scale_v = np.max(np.abs(ref[:, 3:]))
+    assert np.max(np.abs(g[:, :3] - ref[:, :3])) <= 1e-9 * scale_x
+    assert np.max(np.abs(g[:, 3:] - ref[:, 3:])) <= 1e-9 * scale_v
+
+
+def test_collisions_only_bit_identical_and_conserving(rb, orc):
+    """Sect. 6.2 set-up (periodic, no gravity, eps = 1): the GPU trajectory is
+    bit-identical to the oracle's and conserves energy and momentum."""
+    g = np.random.default_rng(11)
+    n, L = 3000, 40.0
+    x, y, z = g.uniform(-L / 2, L / 2, (3, n))
+    vx, vy, vz = g.normal(0, 0.5, (3, n))
+    m = g.uniform(0.5, 2.0, n)
+    r = np.full(n, 0.5)
+    cfg = dict(box=(L, L, L), nghost=(1, 1, 1), boundary=rb.RB_BC_PERIODIC, z_periodic=1, eps=1.0,
+               dt=0.02, gravity=0, collisions=1, integrator=rb.RB_INT_LEAPFROG)
+    sim = rb.Sim(**cfg)
+    sim.set_particles((x, y, z, vx, vy, vz, m, r))
+    E0, P0 = sim.energy()
+    sim.step(20)
+    E1, P1 = sim.energy()
+    got = sim.particles()
+    p = orc.Params(L=(L, L, L), nghost=(1, 1, 1), boundary=1, z_periodic=1, eps=1.0, dt=0.02,
+                   gravity=0, collisions=1, integrator=0)
+    st = orc.State(p, x, y, z, vx, vy, vz, m, r)
+    st.step(20)
+    ref = np.stack([st.x, st.y, st.z, st.vx, st.vy, st.vz], axis=1)
+    assert np.array_equal(_arrays(got), ref)
+    assert abs(E1 - E0) <= 1e-13 * abs(E0)
+    assert np.all(np.abs(P1 - P0) <= 1e-13 * np.sum(m * np.abs(vx)))
+    assert sim.stats()["pairs_found"] >= 0
+
+
+def test_open_boundary_removal(rb, orc):
+    g = np.random.default_rng(4)
+    n, L = 500, 10.0
+    x, y, z = g.uniform(-L / 2, L / 2, (3, n))
+    vx, vy, vz = g.normal(0, 20.0, (3, n))
+    zero = np.zeros(n)
+    cfg = dict(G=1.0, box=(L, L, L), boundary=rb.RB_BC_OPEN, dt=0.01, gravity=0, collisions=0,
+               integrator=rb.RB_INT_LEAPFROG)
+    sim = rb.Sim(**cfg)
+    sim.set_particles((x, y, z, vx, vy, vz, np.ones(n), zero))
+    sim.step(5)
+    got = sim.particles()
+    p = orc.Params(L=(L, L, L), boundary=0, dt=0.01, gravity=0, collisions=0)
+    st = orc.State(p, x, y, z, vx, vy, vz, np.ones(n), zero)
+    st.step(5)
+    assert 0 < st.n < n
+    assert got["id"].tolist() == st.id.tolist()
+    assert np.array_equal(got["x"], st.x)
+
+
+def test_ensemble_equals_single_boxes(rb, orc):
+    """Boxes advanced together give the same result as each box alone."""
+    boxes = [(60.0, 900, 21), (35.0, 300, 22), (80.0, 1500, 23)]
+    cfg = sheet_cfg(rb, 60.0, rb.RB_WALK_FP64)
+    ens = rb.Sim(nbox=len(boxes), **cfg)
+    for b, (L, N, seed) in enumerate(boxes):
+        ens.set_box(b, (L, L, L))
+        ens.set_particles(I.sheet(L, N, seed), box=b)
+    ens.step(3)
+    for b, (L, N, seed) in enumerate(boxes):
+        one = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP64))
+        one.set_particles(I.sheet(L, N, seed))
+        one.step(3)
+        ge, go = ens.particles(b), one.particles()
+        assert ge["id"].tolist() == go["id"].tolist()
+        assert np.max(np.abs(_arrays(ge) - _arrays(go))) <= 1e-12 * L
