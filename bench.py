@@ -210,6 +210,8 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     wms = statistics.mean(walk_ms)
+    if not wms > 0.0:
+        raise RuntimeError("the gravity walk stage time was not recorded")
     achieved = statistics.mean(walk_flops) / (wms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_walk32 (gravity walk)", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
@@ -345,9 +347,14 @@ def main():
     ap.add_argument("--walk", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--cpu-samples", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--particles", type=int, default=N_SHEET,
+                    help="sheet size (default 1M; smaller sizes are for profiling only)")
+    ap.add_argument("--box", type=float, default=L_SHEET, help="sheet side in m (default 2050)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global N_SHEET, L_SHEET
+    N_SHEET, L_SHEET = args.particles, args.box
     if args.impl == "reference":
         run_reference(args)
     else:

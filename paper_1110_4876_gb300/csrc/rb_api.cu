@@ -70,7 +70,9 @@ struct rb_sim {
 namespace {
 
 constexpr int kEnergyParts = 304;
-constexpr int kResolveRounds = 4;
+// The sorted queue of a freshly drawn 1M-particle sheet (~940k pairs) has
+// chains of at most ~24 pairs; what 32 rounds leave is finished in order.
+constexpr int kResolveRounds = 32;
 
 int fail(rb_sim* s, int code, const std::string& msg) {
     if (s) s->err = msg; else g_create_error = msg;
@@ -163,17 +165,23 @@ int alloc_pairs(rb_sim* s, int cap) {
     free_list(s, s->pair_allocs);
     Pairs& R = s->PR;
     int32_t* keep_slot = R.slot_of_id;
-    int32_t* keep_minp = R.minp;
     R.cap = cap;
     int rc = RB_OK;
-    rc |= dalloc(s, &R.key, cap, s->pair_allocs);
-    rc |= dalloc(s, &R.key_alt, cap, s->pair_allocs);
-    rc |= dalloc(s, &R.val, cap, s->pair_allocs);
-    rc |= dalloc(s, &R.val_alt, cap, s->pair_allocs);
-    rc |= dalloc(s, &R.done, cap, s->pair_allocs);
-    rc |= dalloc(s, &R.hist, radix_hist_words(cap), s->pair_allocs);
+    auto& L = s->pair_allocs;
+    rc |= dalloc(s, &R.key, cap, L);
+    rc |= dalloc(s, &R.key_alt, cap, L);
+    rc |= dalloc(s, &R.val, cap, L);
+    rc |= dalloc(s, &R.val_alt, cap, L);
+    rc |= dalloc(s, &R.ekey, 2 * (size_t)cap, L);
+    rc |= dalloc(s, &R.ekey_alt, 2 * (size_t)cap, L);
+    rc |= dalloc(s, &R.eval, 2 * (size_t)cap, L);
+    rc |= dalloc(s, &R.eval_alt, 2 * (size_t)cap, L);
+    rc |= dalloc(s, &R.prev_a, cap, L);
+    rc |= dalloc(s, &R.prev_b, cap, L);
+    rc |= dalloc(s, &R.rdone, cap, L);
+    rc |= dalloc(s, &R.hist, radix_hist_words(cap), L);
+    rc |= dalloc(s, &R.ehist, radix_hist_words(2 * cap), L);
     R.slot_of_id = keep_slot;
-    R.minp = keep_minp;
     return rc ? RB_ERR_CUDA : RB_OK;
 }
 
@@ -228,7 +236,6 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.box_first, s->nbox + 1, L);
         rc |= dalloc(s, &T.box_root, s->nbox, L);
         rc |= dalloc(s, &s->PR.slot_of_id, cap, L);
-        rc |= dalloc(s, &s->PR.minp, cap, L);
         rc |= dalloc(s, &s->acc_x, cap, L); rc |= dalloc(s, &s->acc_y, cap, L);
         rc |= dalloc(s, &s->acc_z, cap, L); rc |= dalloc(s, &s->phi, cap, L);
         rc |= dalloc(s, &s->cnt_cell, cap, L); rc |= dalloc(s, &s->cnt_leaf, cap, L);
@@ -308,7 +315,9 @@ WalkOut walk_out(rb_sim* s) {
 
 // Stage marker: an event record node in the step graph when profiling.
 void mark(rb_sim* s, int k) {
-    if (s->profiling) cudaEventRecord(s->ev_stage[k], s->stream);
+    // External: a real event record node (inside a capture a plain record is
+    // only an ordering marker)
+    if (s->profiling) cudaEventRecordWithFlags(s->ev_stage[k], s->stream, cudaEventRecordExternal);
 }
 
 // The launches of one step starting from particle set p; returns the set

@@ -57,11 +57,11 @@ struct Ctl {
     int n_entries;             // tree entries (cells + leaves) of the last build
     int n_cells;
     int pair_count;            // pairs found by the last search (may exceed capacity)
-    int pair_n;                // min(pair_count, capacity)
+    int pair_n;                // pairs to resolve (0 when the search overflowed)
+    int pair_ends;             // 2 * pair_n
     int pending;               // pairs not yet resolved
     int resolved;              // pairs that were approaching and were resolved
     int err;                   // error bits (kErr*)
-    int pad;
     unsigned long long n_cell, n_leaf, n_mac, n_recheck;
 };
 constexpr int kErrNonFinite = 1;
@@ -93,10 +93,12 @@ struct Tree {
 struct Pairs {
     uint64_t *key, *key_alt;
     uint32_t *val, *val_alt;   // unused payload for the sort
-    int32_t* minp;             // per particle slot: lowest pending pair
-    uint8_t* done;
+    uint64_t *ekey, *ekey_alt; // pair ends: particle slot (sort key)
+    uint32_t *eval, *eval_alt; // pair ends: 2 * pair + side
+    int32_t *prev_a, *prev_b;  // previous pair (queue order) of particle a / b, or -1
+    int32_t* rdone;            // round in which a pair was resolved, -1 while pending
     int32_t* slot_of_id;       // global id -> slot in the current set
-    uint32_t* hist;
+    uint32_t *hist, *ehist;
     int cap;
 };
 

@@ -164,6 +164,7 @@ __global__ void k_pairs_prep(Ctl* ctl, int cap) {
     const int c = ctl->pair_count;
     const int n = c <= cap ? c : 0;
     ctl->pair_n = n;
+    ctl->pair_ends = 2 * n;
     ctl->pending = n;
     ctl->resolved = 0;
 }
@@ -172,8 +173,8 @@ struct ResolveArgs {
     PSet P;
     const uint64_t* key;
     const int32_t* slot_of_id;
-    int32_t* minp;
-    uint8_t* done;
+    const int32_t *prev_a, *prev_b;
+    int32_t* rdone;
     Ctl* ctl;
     const BoxP* boxes;
     int hs;
@@ -223,46 +224,56 @@ __device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C,
     return true;
 }
 
-// Conflict-free rounds: a pending pair is resolved in a round when it is the
-// lowest pending pair of both its particles.  Pairs resolved together touch
-// disjoint particles, and every pair sees the results of all earlier pairs
-// that share a particle with it: the outcome equals resolving the sorted
-// queue one pair at a time.
-__global__ void __launch_bounds__(256) k_res_reset(ResolveArgs A) {
+// Pair ends for the predecessor links: (particle slot, 2 * pair + side).
+__global__ void __launch_bounds__(256) k_pair_ends(ResolveArgs A, uint64_t* __restrict__ ekey,
+                                                   uint32_t* __restrict__ eval) {
     const int n = A.ctl->pair_n;
-    if (A.ctl->pending == 0) return;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (A.done[k]) continue;
         int a, b;
         pair_slots(A, A.key[k], a, b);
-        A.minp[a] = INT_MAX;
-        A.minp[b] = INT_MAX;
+        ekey[2 * k] = (uint64_t)a;
+        ekey[2 * k + 1] = (uint64_t)b;
+        eval[2 * k] = 2u * k;
+        eval[2 * k + 1] = 2u * k + 1u;
     }
 }
 
-__global__ void __launch_bounds__(256) k_res_claim(ResolveArgs A) {
-    const int n = A.ctl->pair_n;
-    if (A.ctl->pending == 0) return;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (A.done[k]) continue;
-        int a, b;
-        pair_slots(A, A.key[k], a, b);
-        atomicMin(&A.minp[a], k);
-        atomicMin(&A.minp[b], k);
+// After a stable sort of the ends by particle, consecutive ends of the same
+// particle are consecutive pairs of that particle in queue order.
+__global__ void __launch_bounds__(256) k_pair_prev(const uint64_t* __restrict__ ekey,
+                                                   const uint32_t* __restrict__ eval,
+                                                   const Ctl* __restrict__ ctl,
+                                                   int32_t* __restrict__ prev_a,
+                                                   int32_t* __restrict__ prev_b,
+                                                   int32_t* __restrict__ rdone) {
+    const int m = ctl->pair_ends;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+        const uint32_t v = eval[e];
+        const int k = (int)(v >> 1);
+        const int prev = (e > 0 && ekey[e - 1] == ekey[e]) ? (int)(eval[e - 1] >> 1) : -1;
+        if (v & 1u) prev_b[k] = prev; else prev_a[k] = prev;
+        if (!(v & 1u)) rdone[k] = -1;
     }
 }
 
-__global__ void __launch_bounds__(256) k_res_apply(ResolveArgs A, SimC C) {
-    const int n = A.ctl->pair_n;
+// Round r: a pending pair is resolved when the previous pair of each of its
+// particles was resolved in an earlier round.  Pairs resolved in the same
+// round share no particle, and every pair sees the results of all earlier
+// pairs that share a particle with it, so the outcome equals resolving the
+// sorted queue one pair at a time (the longest chain of the queue sets the
+// number of rounds; the tail finishes whatever the rounds leave).
+__global__ void __launch_bounds__(256) k_res_round(ResolveArgs A, SimC C, int r) {
     if (A.ctl->pending == 0) return;
+    const int n = A.ctl->pair_n;
     int nd = 0, nr = 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (A.done[k]) continue;
-        int a, b;
-        pair_slots(A, A.key[k], a, b);
-        if (A.minp[a] == k && A.minp[b] == k) {
+        if (A.rdone[k] >= 0) continue;
+        const int pa = A.prev_a[k], pb = A.prev_b[k];
+        const bool ready_a = pa < 0 || (unsigned)A.rdone[pa] < (unsigned)r;
+        const bool ready_b = pb < 0 || (unsigned)A.rdone[pb] < (unsigned)r;
+        if (ready_a && ready_b) {
             nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
-            A.done[k] = 1;
+            A.rdone[k] = r;
             nd++;
         }
     }
@@ -271,14 +282,14 @@ __global__ void __launch_bounds__(256) k_res_apply(ResolveArgs A, SimC C) {
 }
 
 // Whatever the rounds left: one thread, in queue order.
-__global__ void k_res_tail(ResolveArgs A, SimC C) {
+__global__ void k_res_tail(ResolveArgs A, SimC C, int r) {
     if (A.ctl->pending == 0) return;
     const int n = A.ctl->pair_n;
     int nr = 0;
     for (int k = 0; k < n; k++) {
-        if (A.done[k]) continue;
+        if (A.rdone[k] >= 0) continue;
         nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
-        A.done[k] = 1;
+        A.rdone[k] = r;
     }
     A.ctl->resolved += nr;
     A.ctl->pending = 0;
@@ -372,16 +383,19 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s) {
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
                    int half_step_offset, int rounds, cudaStream_t s) {
     ResolveArgs A;
-    A.P = P; A.key = PR.key; A.slot_of_id = PR.slot_of_id; A.minp = PR.minp; A.done = PR.done;
+    A.P = P; A.key = PR.key; A.slot_of_id = PR.slot_of_id;
+    A.prev_a = PR.prev_a; A.prev_b = PR.prev_b; A.rdone = PR.rdone;
     A.ctl = ctl; A.boxes = boxes; A.hs = half_step_offset;
-    cudaMemsetAsync(PR.done, 0, (size_t)PR.cap, s);
-    const int grid = std::min(ceil_div(PR.cap, 256), 2 * 152);
-    for (int r = 0; r < rounds; r++) {
-        k_res_reset<<<grid, 256, 0, s>>>(A);
-        k_res_claim<<<grid, 256, 0, s>>>(A);
-        k_res_apply<<<grid, 256, 0, s>>>(A, C);
-    }
-    k_res_tail<<<1, 1, 0, s>>>(A, C);
+    const int grid = std::min(ceil_div(PR.cap, 256), 4 * 152);
+    k_pair_ends<<<grid, 256, 0, s>>>(A, PR.ekey, PR.eval);
+    // particle slots are < 2^24: three 8-bit passes, stable in queue order
+    const int which = radix_sort(PR.ekey, PR.eval, PR.ekey_alt, PR.eval_alt, 2 * PR.cap,
+                                 &ctl->pair_ends, 24, nullptr, 0, PR.ehist, s);
+    k_pair_prev<<<2 * grid, 256, 0, s>>>(which ? PR.ekey_alt : PR.ekey,
+                                         which ? PR.eval_alt : PR.eval, ctl, PR.prev_a, PR.prev_b,
+                                         PR.rdone);
+    for (int r = 0; r < rounds; r++) k_res_round<<<grid, 256, 0, s>>>(A, C, r);
+    k_res_tail<<<1, 1, 0, s>>>(A, C, rounds);
 }
 
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,

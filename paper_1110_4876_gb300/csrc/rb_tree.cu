@@ -237,6 +237,21 @@ struct GravRecArgs {
     bool fp32, inside;
 };
 
+// Mass and position of a child entry: a particle leaf is read from the
+// particle arrays (written by an earlier kernel), a cell from the records
+// that another thread of this kernel published (L2, not L1).
+__device__ __forceinline__ void child_mass_pos(const GravRecArgs& A, int c, double& m, double& x,
+                                               double& y, double& z) {
+    if (A.e_level[c] == 22) {
+        const int j = A.e_first[c];
+        m = A.m[j]; x = A.x[j]; y = A.y[j]; z = A.z[j];
+    } else {
+        const double4_32a a = ldcg_d4(&A.d_a[c]);
+        m = ldcg_d4(&A.d_q0[c]).x;
+        x = a.x; y = a.y; z = a.z;
+    }
+}
+
 // Leaf records, then bottom-up cell moments: the last child to finish
 // computes its parent (atomic arrival count, no waiting).  A cell's moments
 // come from its children: M = sum M_c, centre of mass = sum M_c com_c / M,
@@ -259,24 +274,26 @@ __global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
             A.rb[e] = make_float4(lx, ly, lz, __int_as_float(e + 1));
         }
     }
+    bool wrote_cell = false;
     for (;;) {
         const int k = A.e_parent[e];
         if (k < 0) return;
-        __threadfence();
+        // a cell written by this thread is published before its arrival is
+        // counted; a leaf publishes nothing (its parent reads the particle)
+        if (wrote_cell) __threadfence();
         const int prev = atomicAdd(&A.e_arrive[k], 1);
         if (prev != A.e_nchild[k] - 1) return;
         __threadfence();
         // all children of k are final: compute k
         const int end = A.e_skip[k];
         double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        for (int c = k + 1; c < end; c = __ldcg(&A.e_skip[c])) {
-            const double4_32a a = ldcg_d4(&A.d_a[c]);
-            const bool leaf = ldcg_i8(&A.e_level[c]) == 22;
-            const double mc = leaf ? -a.w : ldcg_d4(&A.d_q0[c]).x;
+        for (int c = k + 1; c < end; c = A.e_skip[c]) {
+            double mc, px, py, pz;
+            child_mass_pos(A, c, mc, px, py, pz);
             M += mc;
-            sx += mc * a.x;
-            sy += mc * a.y;
-            sz += mc * a.z;
+            sx += mc * px;
+            sy += mc * py;
+            sz += mc * pz;
         }
         const int v = A.e_level[k];
         const int first = A.e_first[k];
@@ -292,16 +309,13 @@ __global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
             cx = lo + (ix + 0.5) * w; cy = lo + (iy + 0.5) * w; cz = lo + (iz + 0.5) * w;
         }
         double q[6] = {0, 0, 0, 0, 0, 0};
-        for (int c = k + 1; c < end; c = __ldcg(&A.e_skip[c])) {
-            const double4_32a a = ldcg_d4(&A.d_a[c]);
-            const bool leaf = ldcg_i8(&A.e_level[c]) == 22;
+        for (int c = k + 1; c < end; c = A.e_skip[c]) {
             double mc;
-            if (leaf) {
-                mc = -a.w;
-            } else {
+            double4_32a a;
+            child_mass_pos(A, c, mc, a.x, a.y, a.z);
+            if (A.e_level[c] != 22) {
                 const double4_32a q0 = ldcg_d4(&A.d_q0[c]);
                 const double4_32a q1 = ldcg_d4(&A.d_q1[c]);
-                mc = q0.x;
                 q[0] += q0.y; q[1] += q0.z; q[2] += q0.w;
                 q[3] += q1.x; q[4] += q1.y; q[5] += q1.z;
             }
@@ -341,7 +355,7 @@ __global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
                 A.rc_lo[k] = make_float4(lx, ly, lz, 0.f);
             }
         }
-        __threadfence();
+        wrote_cell = true;
         e = k;
     }
 }

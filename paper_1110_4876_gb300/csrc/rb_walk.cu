@@ -68,6 +68,23 @@ __device__ __forceinline__ bool mac64(const double4_32a& a, double theta2, doubl
     return a.w < __dmul_rn(theta2, r2);
 }
 
+// 1/sqrt(x) from the hardware estimate plus one Newton step
+// y' = y (3/2 - x y^2 / 2), which roughly halves its relative error.
+__device__ __forceinline__ float rsqrt_nr(float x) {
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+
+// Compensated (Kahan) accumulation: in a sheet the net force is often a
+// small remainder of much larger cancelling terms, and plain FP32 sums lose
+// ~1e-5 of it; the running compensation c keeps the lost low-order bits.
+__device__ __forceinline__ void kadd(float& s, float& c, float t) {
+    const float y = t - c;
+    const float u = s + y;
+    c = (u - s) - y;
+    s = u;
+}
+
 // Is the target point inside the closed cube of a cell (FP64, exact sequence)?
 __device__ __forceinline__ bool inside64(const double4_32a& c, double tx, double ty, double tz) {
     return c.x <= tx && tx <= __dadd_rn(c.x, c.w) && c.y <= ty && ty <= __dadd_rn(c.y, c.w) &&
@@ -105,7 +122,8 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                 const float tlz = __double2float_rn(tz - (double)thz);
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
-                float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
+                float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // per-image sums
+                float cx = 0.f, cy = 0.f, cz = 0.f;              // their compensations
                 for (;;) {
                     if (next >= wend) next = kEnd;
                     const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
@@ -122,17 +140,19 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                         if (act) {
                             if (e != self) {
                                 const float m = -ra.w;
-                                const float inv = rsqrtf(kSoft ? r2 + A.soft2f : r2);
+                                const float inv = rsqrt_nr(kSoft ? r2 + A.soft2f : r2);
                                 const float f = m * (inv * inv * inv);
-                                fx += f * dx;
-                                fy += f * dy;
-                                fz += f * dz;
+                                kadd(fx, cx, f * dx);
+                                kadd(fy, cy, f * dy);
+                                kadd(fz, cz, f * dz);
                                 if (kPot) fp -= m * inv;
                                 nleaf++;
                             }
                             next = e + 1;
                         }
                     } else if (act) {
+                        const float4 q0 = __ldg(&A.rq0[e]);
+                        const float4 q1 = __ldg(&A.rq1[e]);
                         nmac++;
                         bool acc = ra.w < r2;
                         if (fabsf(ra.w - r2) <= 1e-5f * r2) {
@@ -155,28 +175,27 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                             }
                         }
                         if (acc) {
-                            const float4 q0 = __ldg(&A.rq0[e]);
-                            const float inv = rsqrtf(r2);
+                            const float inv = rsqrt_nr(r2);
                             const float inv2 = inv * inv;
-                            const float invs = kSoft ? rsqrtf(r2 + A.soft2f) : inv;
+                            const float invs = kSoft ? rsqrt_nr(r2 + A.soft2f) : inv;
                             const float f = q0.x * (invs * invs * invs);
-                            fx += f * dx;
-                            fy += f * dy;
-                            fz += f * dz;
+                            float tx_ = f * dx, ty_ = f * dy, tz_ = f * dz;
                             if (kPot) fp -= q0.x * invs;
                             if (kQuad) {
-                                const float4 q1 = __ldg(&A.rq1[e]);
                                 const float qx = q0.y * dx + q1.x * dy + q1.y * dz;
                                 const float qy = q1.x * dx + q0.z * dy + q1.z * dz;
                                 const float qz = q1.y * dx + q1.z * dy + q0.w * dz;
                                 const float dqd = dx * qx + dy * qy + dz * qz;
                                 const float inv5 = inv2 * inv2 * inv;
                                 const float c = 2.5f * dqd * (inv5 * inv2);
-                                fx += c * dx - inv5 * qx;
-                                fy += c * dy - inv5 * qy;
-                                fz += c * dz - inv5 * qz;
+                                tx_ += c * dx - inv5 * qx;
+                                ty_ += c * dy - inv5 * qy;
+                                tz_ += c * dz - inv5 * qz;
                                 if (kPot) fp -= 0.5f * dqd * inv5;
                             }
+                            kadd(fx, cx, tx_);
+                            kadd(fy, cy, ty_);
+                            kadd(fz, cz, tz_);
                             ncell++;
                             next = __float_as_int(rb.w);
                         } else {
@@ -184,9 +203,9 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                         }
                     }
                 }
-                ax += (double)fx;
-                ay += (double)fy;
-                az += (double)fz;
+                ax += (double)fx - (double)cx;
+                ay += (double)fy - (double)cy;
+                az += (double)fz - (double)cz;
                 pot += (double)fp;
             }
     if (valid) {
