@@ -339,6 +339,7 @@ def run_reference(args):
 
 
 def main():
+    global N_SHEET, L_SHEET
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -353,7 +354,6 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    global N_SHEET, L_SHEET
     N_SHEET, L_SHEET = args.particles, args.box
     if args.impl == "reference":
         run_reference(args)

@@ -55,7 +55,9 @@ def test_sheet_1m_forces_sampled(rb, orc, sheet1m):
     sim64 = rb.Sim(**cfg(rb, L, walk=0))
     sim64.set_particles(P)
     a64, (nc, nl, nm) = sim64.gravity(counts=True)
-    assert orc.force_errors(a64[sel], a_ref)[2] <= 1e-12
+    # same accepted sets, different summation order: ~700 terms x u x a net
+    # force up to ~100 times smaller than its terms -> ~1e-11; bound 1e-10
+    assert orc.force_errors(a64[sel], a_ref)[2] <= 1e-10
     np.testing.assert_array_equal(nc[sel], rc)
     np.testing.assert_array_equal(nl[sel], rl)
 
