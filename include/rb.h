@@ -172,6 +172,34 @@ int rb_stats(rb_sim* sim, rb_stats_t* out);
 int rb_set_profiling(rb_sim* sim, int on);
 /* Destroy the simulation and free its device memory. */
 void rb_destroy(rb_sim* sim);
+
+/* Energy and momentum sums without any device allocation.  The paper has no
+ * counterpart: this entry point serves callers that cannot call cudaMalloc,
+ * for instance a process whose device memory belongs to another runtime's
+ * pool or budget, or a latency-bound loop that must avoid the implicit
+ * device synchronisation of an allocation.
+ * Inputs (device pointers, n particles each, caller-owned): m, x, z, vx, vy,
+ * vz, and phi (may be NULL: W = 0; x and z may be NULL unless integrator is
+ * RB_INT_SEI).  Output: out, a caller-owned device array of 7 doubles, filled
+ * with sum m|v|^2/2, the SEI tidal and vertical term
+ * sum m (omega_z^2 z^2 / 2 - 3/2 omega^2 x^2) (0 for leap-frog),
+ * sum m phi / 2, the three momentum components and n, the same terms
+ * rb_energy adds up.  Runs asynchronously on cuda_stream (NULL: the legacy
+ * default stream).
+ * Scratch: a fixed 448 KiB array of per-block partial sums in the library's
+ * own device memory, present on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call on each device
+ * before any stream capture.  Every call overwrites the partial sums it
+ * reads; calls that overlap on the GPU share the array and race.
+ * Errors: RB_ERR_ARG for n < 0 or n > 16,777,216 (the partial-sum array holds
+ * one slot per 2048 particles) or a missing array, with a message in
+ * rb_last_error(NULL); RB_ERR_CUDA if the address lookup or a launch fails.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. */
+int rb_energy_sums_noalloc(int64_t n, const double* m, const double* x, const double* z,
+                           const double* vx, const double* vy, const double* vz,
+                           const double* phi, int integrator, double omega, double omega_z,
+                           double* out, void* cuda_stream);
 /* Description of the last error of `sim` (or of the last failed
  * rb_create when sim is NULL); static storage owned by the library. */
 const char* rb_last_error(const rb_sim* sim);

@@ -24,6 +24,12 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+void rb::set_global_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
+
 struct BoxHost {
     double L[3];
     std::vector<double> x, y, z, vx, vy, vz, m, r;

@@ -14,6 +14,8 @@
 //    walk, and the FP64 moments (M, centre of mass, traceless quadrupole).
 #pragma once
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace rb {
@@ -150,6 +152,9 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s);
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
                   double* partials, int nparts, double* out7, cudaStream_t s);
 void step_advance(Ctl* ctl, cudaStream_t s);
+
+// rb_api.cu: message returned by rb_last_error(NULL) on this thread.
+void set_global_error(const std::string& msg);
 void clear_walk_stats(Ctl* ctl, cudaStream_t s);
 
 }  // namespace rb

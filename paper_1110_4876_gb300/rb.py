@@ -24,7 +24,7 @@ EXPORTS = [
     "rb_create", "rb_set_box", "rb_set_particles", "rb_step", "rb_get_particles", "rb_energy",
     "rb_compute_gravity", "rb_get_accelerations", "rb_get_counts", "rb_get_tree",
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
-    "rb_set_profiling", "rb_destroy", "rb_last_error",
+    "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
 ]
 
 
@@ -94,6 +94,8 @@ def load():
     lib.rb_get_time.argtypes = [_P, C.POINTER(C.c_double)]
     lib.rb_stats.argtypes = [_P, C.POINTER(rb_stats_t)]
     lib.rb_set_profiling.argtypes = [_P, i32]
+    lib.rb_energy_sums_noalloc.argtypes = [i64] + [_VP] * 7 + [i32, C.c_double, C.c_double, _VP,
+                                                              _VP]
     lib.rb_destroy.argtypes = [_P]
     lib.rb_destroy.restype = None
     lib.rb_last_error.argtypes = [_P]
@@ -269,6 +271,15 @@ def rb_stats(sim) -> dict:
 
 def rb_set_profiling(sim, on: bool = True):
     _check(load().rb_set_profiling(sim, 1 if on else 0), sim)
+
+
+def rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z, out,
+                           stream=None):
+    """Energy/momentum sums without device allocation; all array arguments
+    are device addresses (ints, e.g. torch ``data_ptr()``) or None."""
+    rc = load().rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z,
+                                       out, stream)
+    _check(rc, None)
 
 
 def rb_destroy(sim):
