@@ -185,6 +185,9 @@ int alloc_pairs(rb_sim* s, int cap) {
     rc |= dalloc(s, &R.prev_a, cap, L);
     rc |= dalloc(s, &R.prev_b, cap, L);
     rc |= dalloc(s, &R.rdone, cap, L);
+    rc |= dalloc(s, &R.list0, cap, L);
+    rc |= dalloc(s, &R.list1, cap, L);
+    rc |= dalloc(s, &R.rcnt, 64, L);
     rc |= dalloc(s, &R.hist, radix_hist_words(cap), L);
     rc |= dalloc(s, &R.ehist, radix_hist_words(2 * cap), L);
     R.slot_of_id = keep_slot;
@@ -241,6 +244,7 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.d_q1, ecap, L); rc |= dalloc(s, &T.d_c, ecap, L);
         rc |= dalloc(s, &T.box_first, s->nbox + 1, L);
         rc |= dalloc(s, &T.box_root, s->nbox, L);
+        rc |= dalloc(s, &T.lvl, 96, L);
         rc |= dalloc(s, &s->PR.slot_of_id, cap, L);
         rc |= dalloc(s, &s->acc_x, cap, L); rc |= dalloc(s, &s->acc_y, cap, L);
         rc |= dalloc(s, &s->acc_z, cap, L); rc |= dalloc(s, &s->phi, cap, L);

@@ -48,6 +48,35 @@ __global__ void __launch_bounds__(kThreads) k_rs_up(const uint64_t* __restrict__
     hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// One block per digit: exclusive scan of that digit's per-tile counts (a
+// contiguous row of the digit-major histogram) and the digit's total.
+__global__ void __launch_bounds__(256) k_digit_rows(uint32_t* __restrict__ hist, int nblocks,
+                                                    uint32_t* __restrict__ dtot) {
+    __shared__ uint32_t wsum[8];
+    uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
+    const int per = (nblocks + 255) / 256;
+    const int b = threadIdx.x * per, e = min(b + per, nblocks);
+    uint32_t s = 0;
+    for (int i = b; i < e; i++) s += row[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t v = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    uint32_t run = v - s;
+    for (int q = 0; q < w; q++) run += wsum[q];
+    for (int i = b; i < e; i++) {
+        const uint32_t c = row[i];
+        row[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == 255) dtot[blockIdx.x] = run;
+}
+
 // Exclusive scan of `total` words in place by one block; the sum of all
 // words goes to *sum when sum is non-null.
 template <typename T>
@@ -94,15 +123,33 @@ __global__ void __launch_bounds__(kThreads) k_rs_down(const uint64_t* __restrict
                                                       uint32_t* __restrict__ vout,
                                                       const int32_t* __restrict__ box,
                                                       const int* d_n, int ncap, int shift,
-                                                      const uint32_t* __restrict__ hist, int nblocks) {
+                                                      const uint32_t* __restrict__ hist,
+                                                      const uint32_t* __restrict__ dtot,
+                                                      int nblocks) {
     __shared__ uint32_t wcnt[kThreads / 32][kBins];
     __shared__ uint32_t boff[kBins];
+    __shared__ uint32_t wsum[kThreads / 32];
     const int n = read_n(d_n, ncap);
     const int base = blockIdx.x * kTile;
     if (base >= n) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < (kThreads / 32) * kBins; d += kThreads) (&wcnt[0][0])[d] = 0;
-    boff[threadIdx.x] = hist[threadIdx.x * nblocks + blockIdx.x];
+    {
+        // start of digit d = (keys of all smaller digits) + (keys of digit d in
+        // earlier tiles); the first is an exclusive scan of the digit totals
+        const uint32_t tot = dtot[threadIdx.x];
+        uint32_t v = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; w++) before += wsum[w];
+        boff[threadIdx.x] = before + v - tot + hist[threadIdx.x * nblocks + blockIdx.x];
+    }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     uint64_t k[kItems];
@@ -219,7 +266,10 @@ __global__ void __launch_bounds__(256) k_scan_down(int32_t* __restrict__ a, int 
 
 }  // namespace
 
-size_t radix_hist_words(int ncap) { return (size_t)kBins * (size_t)ceil_div(ncap > 0 ? ncap : 1, kTile); }
+// Digit-major per-tile histogram plus 256 digit totals.
+size_t radix_hist_words(int ncap) {
+    return (size_t)kBins * (size_t)ceil_div(ncap > 0 ? ncap : 1, kTile) + kBins;
+}
 
 size_t scan_part_words(int ncap) { return (size_t)ceil_div((long long)ncap + 1, kScanTile) + 1; }
 
@@ -232,27 +282,31 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap,
                cudaStream_t s) {
     if (ncap <= 0) return 0;
     const int nblocks = ceil_div(ncap, kTile);
-    const int total = kBins * nblocks;
+    uint32_t* dtot = hist + (size_t)kBins * nblocks;
     int cur = 0;
     uint64_t* K[2] = {k0, k1};
     uint32_t* V[2] = {v0, v1};
-    for (int sh = 0; sh < key_bits; sh += 8) {
-        k_rs_up<false><<<nblocks, kThreads, 0, s>>>(K[cur], V[cur], nullptr, d_n, ncap, sh, hist,
-                                                    nblocks);
-        k_scan_block<uint32_t><<<1, kScanThreads, 0, s>>>(hist, total, nullptr);
-        k_rs_down<false><<<nblocks, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
-                                                      nullptr, d_n, ncap, sh, hist, nblocks);
-        cur ^= 1;
-    }
-    if (box_digits) {
-        for (int sh = 0; sh < box_bits; sh += 8) {
+    const int passes_key = ceil_div(key_bits, 8);
+    const int passes_box = box_digits ? ceil_div(box_bits, 8) : 0;
+    for (int p = 0; p < passes_key + passes_box; p++) {
+        const bool boxp = p >= passes_key;
+        const int sh = boxp ? 8 * (p - passes_key) : 8 * p;
+        if (boxp)
             k_rs_up<true><<<nblocks, kThreads, 0, s>>>(K[cur], V[cur], box_digits, d_n, ncap, sh,
                                                        hist, nblocks);
-            k_scan_block<uint32_t><<<1, kScanThreads, 0, s>>>(hist, total, nullptr);
+        else
+            k_rs_up<false><<<nblocks, kThreads, 0, s>>>(K[cur], V[cur], nullptr, d_n, ncap, sh,
+                                                        hist, nblocks);
+        k_digit_rows<<<kBins, 256, 0, s>>>(hist, nblocks, dtot);
+        if (boxp)
             k_rs_down<true><<<nblocks, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
-                                                         box_digits, d_n, ncap, sh, hist, nblocks);
-            cur ^= 1;
-        }
+                                                         box_digits, d_n, ncap, sh, hist, dtot,
+                                                         nblocks);
+        else
+            k_rs_down<false><<<nblocks, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
+                                                          nullptr, d_n, ncap, sh, hist, dtot,
+                                                          nblocks);
+        cur ^= 1;
     }
     return cur;
 }

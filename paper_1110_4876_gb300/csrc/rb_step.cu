@@ -261,20 +261,41 @@ __global__ void __launch_bounds__(256) k_pair_prev(const uint64_t* __restrict__ 
 // round share no particle, and every pair sees the results of all earlier
 // pairs that share a particle with it, so the outcome equals resolving the
 // sorted queue one pair at a time (the longest chain of the queue sets the
-// number of rounds; the tail finishes whatever the rounds leave).
-__global__ void __launch_bounds__(256) k_res_round(ResolveArgs A, SimC C, int r) {
-    if (A.ctl->pending == 0) return;
-    const int n = A.ctl->pair_n;
+// number of rounds; the tail finishes whatever the rounds leave).  Each round
+// reads only the pairs still pending (round 0: all) and appends the ones that
+// stay pending to the next round's list.
+__global__ void __launch_bounds__(256) k_res_round(ResolveArgs A, SimC C, int r,
+                                                   const int32_t* __restrict__ list_in,
+                                                   int32_t* __restrict__ list_out,
+                                                   int32_t* __restrict__ rcnt) {
+    const int n = r == 0 ? A.ctl->pair_n : rcnt[r];
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
     int nd = 0, nr = 0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (A.rdone[k] >= 0) continue;
-        const int pa = A.prev_a[k], pb = A.prev_b[k];
-        const bool ready_a = pa < 0 || (unsigned)A.rdone[pa] < (unsigned)r;
-        const bool ready_b = pb < 0 || (unsigned)A.rdone[pb] < (unsigned)r;
-        if (ready_a && ready_b) {
-            nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
-            A.rdone[k] = r;
-            nd++;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int t = base + threadIdx.x;
+        bool keep = false;
+        int k = 0;
+        if (t < n) {
+            k = r == 0 ? t : list_in[t];
+            const int pa = A.prev_a[k], pb = A.prev_b[k];
+            const bool ready_a = pa < 0 || (unsigned)A.rdone[pa] < (unsigned)r;
+            const bool ready_b = pb < 0 || (unsigned)A.rdone[pb] < (unsigned)r;
+            if (ready_a && ready_b) {
+                nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
+                A.rdone[k] = r;
+                nd++;
+            } else {
+                keep = true;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int pos = 0;
+            if (lane == leader) pos = atomicAdd(&rcnt[r + 1], __popc(m));
+            pos = __shfl_sync(0xffffffffu, pos, leader);
+            if (keep) list_out[pos + __popc(m & ((1u << lane) - 1u))] = k;
         }
     }
     if (nd) atomicSub(&A.ctl->pending, nd);
@@ -394,7 +415,10 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
     k_pair_prev<<<2 * grid, 256, 0, s>>>(which ? PR.ekey_alt : PR.ekey,
                                          which ? PR.eval_alt : PR.eval, ctl, PR.prev_a, PR.prev_b,
                                          PR.rdone);
-    for (int r = 0; r < rounds; r++) k_res_round<<<grid, 256, 0, s>>>(A, C, r);
+    cudaMemsetAsync(PR.rcnt, 0, sizeof(int32_t) * 64, s);
+    for (int r = 0; r < rounds && r < 63; r++)
+        k_res_round<<<grid, 256, 0, s>>>(A, C, r, (r & 1) ? PR.list0 : PR.list1,
+                                         (r & 1) ? PR.list1 : PR.list0, PR.rcnt);
     k_res_tail<<<1, 1, 0, s>>>(A, C, rounds);
 }
 

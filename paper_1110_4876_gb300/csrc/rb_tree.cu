@@ -17,6 +17,7 @@
 // with one leaf entry per particle: entry order is (first particle, depth),
 // and a per-particle bitmask of the depths of cells starting there gives
 // every entry's position after one scan.
+#include <algorithm>
 #include <cfloat>
 
 #include "rb_internal.cuh"
@@ -157,26 +158,6 @@ __global__ void k_box_roots(const int32_t* __restrict__ box_first,
     box_root[b] = box_first[b] < box_first[b + 1] ? start[box_first[b]] : -1;
 }
 
-// Parent links and child counts: a cell's children are entry k + 1 and then
-// each child's skip until the cell's own skip.
-__global__ void __launch_bounds__(256) k_link(const int32_t* __restrict__ e_skip,
-                                              const int8_t* __restrict__ e_level,
-                                              const Ctl* __restrict__ ctl, int ecap,
-                                              int32_t* __restrict__ e_parent,
-                                              int32_t* __restrict__ e_nchild) {
-    const int E = min(ctl->n_entries, ecap);
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= E || e_level[k] == 22) return;
-    const int end = e_skip[k];
-    int c = k + 1, nc = 0;
-    while (c < end) {
-        e_parent[c] = k;
-        nc++;
-        c = e_skip[c];
-    }
-    e_nchild[k] = nc;
-}
-
 __global__ void __launch_bounds__(256) k_count_cells(const int8_t* __restrict__ e_level,
                                                      Ctl* __restrict__ ctl, int ecap) {
     const int E = min(ctl->n_entries, ecap);
@@ -194,18 +175,6 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
     x = (x ^ (x >> 32)) & 0x1fffffull;
     return (uint32_t)x;
-}
-
-// Loads that bypass L1: moments written by other blocks of this kernel are
-// read only after their writers' fence + arrival count.
-__device__ __forceinline__ double4_32a ldcg_d4(const double4_32a* p) {
-    const double2* q = reinterpret_cast<const double2*>(p);
-    const double2 a = __ldcg(q), b = __ldcg(q + 1);
-    return make_double4_32a(a.x, a.y, b.x, b.y);
-}
-
-__device__ __forceinline__ int ldcg_i8(const int8_t* p) {
-    return (int)__ldcg(reinterpret_cast<const signed char*>(p));
 }
 
 __device__ __forceinline__ void split_hilo(double v, float& hi, float& lo) {
@@ -238,53 +207,95 @@ struct GravRecArgs {
 };
 
 // Mass and position of a child entry: a particle leaf is read from the
-// particle arrays (written by an earlier kernel), a cell from the records
-// that another thread of this kernel published (L2, not L1).
+// particle arrays, a cell from the records an earlier (deeper) level wrote.
 __device__ __forceinline__ void child_mass_pos(const GravRecArgs& A, int c, double& m, double& x,
                                                double& y, double& z) {
     if (A.e_level[c] == 22) {
         const int j = A.e_first[c];
         m = A.m[j]; x = A.x[j]; y = A.y[j]; z = A.z[j];
     } else {
-        const double4_32a a = ldcg_d4(&A.d_a[c]);
-        m = ldcg_d4(&A.d_q0[c]).x;
+        const double4_32a a = A.d_a[c];
+        m = A.d_q0[c].x;
         x = a.x; y = a.y; z = a.z;
     }
 }
 
-// Leaf records, then bottom-up cell moments: the last child to finish
-// computes its parent (atomic arrival count, no waiting).  A cell's moments
-// come from its children: M = sum M_c, centre of mass = sum M_c com_c / M,
-// Q = sum [Q_c + M_c (3 d d^T - |d|^2 I)], d = com_c - com (the traceless
-// quadrupole about the centre of mass; parallel-axis theorem).
-__global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
+// Leaf records (FP64 and FP32) of every particle.
+__global__ void __launch_bounds__(256) k_leaf_records(GravRecArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    int e = A.leaf_of[p];
-    {
-        const double x = A.x[p], y = A.y[p], z = A.z[p], m = A.m[p];
-        A.d_a[e] = make_double4_32a(x, y, z, -m);
-        if (A.fp32) {
-            float hx, lx, hy, ly, hz, lz;
-            split_hilo(x, hx, lx);
-            split_hilo(y, hy, ly);
-            split_hilo(z, hz, lz);
-            A.ra[e] = make_float4(hx, hy, hz, -(float)m);
-            A.rb[e] = make_float4(lx, ly, lz, __int_as_float(e + 1));
-        }
+    const int e = A.leaf_of[p];
+    const double x = A.x[p], y = A.y[p], z = A.z[p], m = A.m[p];
+    A.d_a[e] = make_double4_32a(x, y, z, -m);
+    if (A.fp32) {
+        float hx, lx, hy, ly, hz, lz;
+        split_hilo(x, hx, lx);
+        split_hilo(y, hy, ly);
+        split_hilo(z, hz, lz);
+        A.ra[e] = make_float4(hx, hy, hz, -(float)m);
+        A.rb[e] = make_float4(lx, ly, lz, __int_as_float(e + 1));
     }
-    bool wrote_cell = false;
-    for (;;) {
-        const int k = A.e_parent[e];
-        if (k < 0) return;
-        // a cell written by this thread is published before its arrival is
-        // counted; a leaf publishes nothing (its parent reads the particle)
-        if (wrote_cell) __threadfence();
-        const int prev = atomicAdd(&A.e_arrive[k], 1);
-        if (prev != A.e_nchild[k] - 1) return;
-        __threadfence();
-        // all children of k are final: compute k
+}
+
+// Cells per depth: counts (block histograms, one atomic per depth and
+// block), offsets, then the lists.  lvl[0..22]: counts, lvl[32..54]: offsets,
+// lvl[64..86]: fill cursors.
+__global__ void __launch_bounds__(256) k_level_count(const int8_t* __restrict__ e_level,
+                                                     const Ctl* __restrict__ ctl, int ecap,
+                                                     int32_t* __restrict__ lvl) {
+    __shared__ int h[23];
+    if (threadIdx.x < 23) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int E = min(ctl->n_entries, ecap);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < E) {
+        const int v = e_level[k];
+        if (v < 22) atomicAdd(&h[v], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 22 && h[threadIdx.x]) atomicAdd(&lvl[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_level_offsets(int32_t* lvl) {
+    int s = 0;
+    for (int d = 0; d < 22; d++) {
+        lvl[32 + d] = s;
+        lvl[64 + d] = s;
+        s += lvl[d];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_level_fill(const int8_t* __restrict__ e_level,
+                                                    const Ctl* __restrict__ ctl, int ecap,
+                                                    int32_t* __restrict__ lvl,
+                                                    int32_t* __restrict__ list) {
+    __shared__ int h[23], base[23];
+    if (threadIdx.x < 23) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int E = min(ctl->n_entries, ecap);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = 22, mine = 0;
+    if (k < E) {
+        v = e_level[k];
+        if (v < 22) mine = atomicAdd(&h[v], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 22 && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&lvl[64 + threadIdx.x], h[threadIdx.x]);
+    __syncthreads();
+    if (v < 22) list[base[v] + mine] = k;
+}
+
+// The cells of one depth.  A cell's moments come from its children (deeper
+// cells, done by earlier launches, or particles): M = sum M_c, centre of
+// mass = sum M_c com_c / M, Q = sum [Q_c + M_c (3 d d^T - |d|^2 I)],
+// d = com_c - com (the traceless quadrupole about the centre of mass, by the
+// parallel-axis theorem).
+__global__ void __launch_bounds__(256) k_moments_level(GravRecArgs A, const int32_t* __restrict__ lvl,
+                                                       const int32_t* __restrict__ list, int depth) {
+    const int cnt = lvl[depth], off = lvl[32 + depth];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int k = list[off + t];
         const int end = A.e_skip[k];
         double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         for (int c = k + 1; c < end; c = A.e_skip[c]) {
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
             sy += mc * py;
             sz += mc * pz;
         }
-        const int v = A.e_level[k];
+        const int v = depth;
         const int first = A.e_first[k];
         const BoxP bp = A.boxes[A.box[first]];
         const double w = ldexp(bp.L, -v);
@@ -314,8 +325,8 @@ __global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
             double4_32a a;
             child_mass_pos(A, c, mc, a.x, a.y, a.z);
             if (A.e_level[c] != 22) {
-                const double4_32a q0 = ldcg_d4(&A.d_q0[c]);
-                const double4_32a q1 = ldcg_d4(&A.d_q1[c]);
+                const double4_32a q0 = A.d_q0[c];
+                const double4_32a q1 = A.d_q1[c];
                 q[0] += q0.y; q[1] += q0.z; q[2] += q0.w;
                 q[3] += q1.x; q[4] += q1.y; q[5] += q1.z;
             }
@@ -355,12 +366,11 @@ __global__ void __launch_bounds__(256) k_moments(GravRecArgs A) {
                 A.rc_lo[k] = make_float4(lx, ly, lz, 0.f);
             }
         }
-        wrote_cell = true;
-        e = k;
     }
 }
 
 struct CollRecArgs {
+    const double *x, *y, *z, *r;
     const int32_t* box;
     const uint64_t* key;
     const BoxP* boxes;
@@ -374,7 +384,8 @@ struct CollRecArgs {
 
 // Collision-search records (Sect. 5.2): per cell its geometric centre
 // (hi/lo) and the opening radius (sqrt(3)/2) w + R_max of Eq. 3, rounded up;
-// per leaf the particle slot.
+// per leaf the particle's position (hi/lo), slot and radius (the search
+// leaves skip implicitly to the next entry).
 __global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
     const int E = min(A.ctl->n_entries, A.ecap);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,8 +393,12 @@ __global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
     const int v = A.e_level[k];
     const int first = A.e_first[k];
     if (v == 22) {
-        A.ra[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(~first));
-        A.rb[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(k + 1));
+        float hx, lx, hy, ly, hz, lz;
+        split_hilo(A.x[first], hx, lx);
+        split_hilo(A.y[first], hy, ly);
+        split_hilo(A.z[first], hz, lz);
+        A.ra[k] = make_float4(hx, hy, hz, __int_as_float(~first));
+        A.rb[k] = make_float4(lx, ly, lz, (float)A.r[first]);
         return;
     }
     const BoxP bp = A.boxes[A.box[first]];
@@ -421,8 +436,6 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
         P.box, ctl, n, C.nbox, T.box_first);
     k_box_roots<<<ceil_div(C.nbox, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
     const int ne = T.cap_e;
-    cudaMemsetAsync(T.e_parent, 0xff, sizeof(int32_t) * ne, s);
-    k_link<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_skip, T.e_level, ctl, ne, T.e_parent, T.e_nchild);
     cudaMemsetAsync(&ctl->n_cells, 0, sizeof(int), s);
     k_count_cells<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_level, ctl, ne);
 }
@@ -431,29 +444,34 @@ void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* b
                            const SimC& C, bool fp64, cudaStream_t s) {
     const int n = T.cap_n;
     if (n <= 0) return;
-    cudaMemsetAsync(T.e_arrive, 0, sizeof(int32_t) * T.cap_e, s);
     GravRecArgs A;
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.box = P.box;
     A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_parent = T.e_parent;
     A.e_nchild = T.e_nchild; A.leaf_of = T.leaf_of; A.e_level = T.e_level;
     A.e_arrive = T.e_arrive;
-    A.d_a = reinterpret_cast<double4_32a*>(T.d_a);
-    A.d_q0 = reinterpret_cast<double4_32a*>(T.d_q0);
-    A.d_q1 = reinterpret_cast<double4_32a*>(T.d_q1);
-    A.d_c = reinterpret_cast<double4_32a*>(T.d_c);
+    A.d_a = T.d_a; A.d_q0 = T.d_q0; A.d_q1 = T.d_q1; A.d_c = T.d_c;
     A.ra = T.ra; A.rb = T.rb; A.rq0 = T.rq0; A.rq1 = T.rq1; A.rc_hi = T.rc_hi; A.rc_lo = T.rc_lo;
     A.ctl = ctl;
     A.ncap = n;
     A.crit_scale = C.crit_scale;
     A.fp32 = !fp64;
     A.inside = C.theta2 > (1.0 / 3.0);
-    k_moments<<<ceil_div(n, 256), 256, 0, s>>>(A);
+    k_leaf_records<<<ceil_div(n, 256), 256, 0, s>>>(A);
+    cudaMemsetAsync(T.lvl, 0, sizeof(int32_t) * 96, s);
+    const int ne = T.cap_e;
+    k_level_count<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_level, ctl, ne, T.lvl);
+    k_level_offsets<<<1, 1, 0, s>>>(T.lvl);
+    k_level_fill<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_level, ctl, ne, T.lvl, T.e_arrive);
+    const int grid = std::min(ceil_div(n, 256), 4 * 152);
+    for (int d = kMaxDepth; d >= 0; d--)
+        k_moments_level<<<grid, 256, 0, s>>>(A, T.lvl, T.e_arrive, d);
 }
 
 void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
                              const SimC& C, double rmax, cudaStream_t s) {
     CollRecArgs A;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
     A.box = P.box; A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
