@@ -88,6 +88,7 @@ struct Tree {
     float4 *rc_hi, *rc_lo;          // FP32 cell corner (hi/lo) + width, inside test
     double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
     int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
+    int32_t* lvl;                   // per-depth cell counts / offsets / cursors (96)
     int cap_n, cap_e;
 };
 
@@ -99,12 +100,46 @@ struct Pairs {
     uint32_t *eval, *eval_alt; // pair ends: 2 * pair + side
     int32_t *prev_a, *prev_b;  // previous pair (queue order) of particle a / b, or -1
     int32_t* rdone;            // round in which a pair was resolved, -1 while pending
+    int32_t *list0, *list1;    // pending pairs entering a round (ping-pong)
+    int32_t* rcnt;             // rcnt[r]: pairs pending at the start of round r (64)
     int32_t* slot_of_id;       // global id -> slot in the current set
     uint32_t *hist, *ehist;
     int cap;
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+#ifdef __CUDACC__
+// Time after 2 * step + hs drift halves: t0 + h * (dt / 2).
+__device__ __forceinline__ double time_of(const Ctl* ctl, double t0, double half_dt, int hs) {
+    const double h = (double)(2 * ctl->step + hs);
+    return __dadd_rn(t0, __dmul_rn(h, half_dt));
+}
+
+// Ghost image offset (gx Lx, gy Ly - gx s, gz Lz), evaluated without
+// contraction (Sect. 2.3; shear reading: s = fmod(1.5 Omega Lx t, Ly)).
+__device__ __forceinline__ void image_offset(const BoxP& bp, double s, int gx, int gy, int gz,
+                                             double& ox, double& oy, double& oz) {
+    ox = __dmul_rn((double)gx, bp.Lx);
+    oy = __dsub_rn(__dmul_rn((double)gy, bp.Ly), __dmul_rn((double)gx, s));
+    oz = __dmul_rn((double)gz, bp.Lz);
+}
+
+__device__ __forceinline__ double shear_offset(const BoxP& bp, double t) {
+    return bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
+}
+
+// Morton key -> integer cell index of depth v along each axis.
+__device__ __forceinline__ uint32_t morton_compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+#endif
 
 // ---- launch wrappers (implemented in the .cu files) ----
 // rb_sort.cu

@@ -39,25 +39,27 @@ struct GravArgs {
     int half_step_offset;
     double G, theta2, soft2, t0, half_dt;
     float soft2f;
+    // recording of accepted cells in the band w/R > theta_lo (learned mode)
+    uint64_t* req;
+    int* req_count;
+    int req_cap;
+    float band_scale;   // (theta_lo / theta)^2: band iff (w/theta)^2 > band_scale R^2
+    uint32_t thresh;    // keep a request when its hash < thresh (0xffffffff: all)
+    uint32_t seed;
 };
 
 __device__ __forceinline__ double4_32a ld_d4(const double4_32a* p) { return *p; }
 
-__device__ __forceinline__ double time_of(const Ctl* ctl, double t0, double half_dt, int hs) {
-    const double h = (double)(2 * ctl->step + hs);
-    return __dadd_rn(t0, __dmul_rn(h, half_dt));
-}
-
-// Image offset (gx Lx, gy Ly - gx s, gz Lz), evaluated without contraction.
-__device__ __forceinline__ void image_offset(const BoxP& bp, double s, int gx, int gy, int gz,
-                                             double& ox, double& oy, double& oz) {
-    ox = __dmul_rn((double)gx, bp.Lx);
-    oy = __dsub_rn(__dmul_rn((double)gy, bp.Ly), __dmul_rn((double)gx, s));
-    oz = __dmul_rn((double)gz, bp.Lz);
-}
-
-__device__ __forceinline__ double shear_offset(const BoxP& bp, double t) {
-    return bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
+// Counter-based hash of a (target, cell, image) request for subsampling.
+__device__ __forceinline__ uint32_t req_hash(uint32_t slot, uint32_t entry, uint32_t code,
+                                             uint32_t seed) {
+    uint32_t h = slot * 0x9E3779B1u ^ (entry + 0x7F4A7C15u) * 0x85EBCA77u ^ code * 0xC2B2AE3Du ^ seed;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
 }
 
 // Opening test in FP64, operation for operation as the oracle evaluates it.
@@ -76,8 +78,10 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 }
 
 // Compensated (Kahan) accumulation: in a sheet the net force is often a
-// small remainder of much larger cancelling terms, and plain FP32 sums lose
-// ~1e-5 of it; the running compensation c keeps the lost low-order bits.
+// small remainder of much larger cancelling terms, and a plain FP32 running
+// sum loses ~1e-5 of it.  The walk sums terms plainly over at most 16 warp
+// iterations and adds those short partial sums into Kahan sums, whose
+// running compensation c keeps the lost low-order bits.
 __device__ __forceinline__ void kadd(float& s, float& c, float t) {
     const float y = t - c;
     const float u = s + y;
@@ -91,7 +95,7 @@ __device__ __forceinline__ bool inside64(const double4_32a& c, double tx, double
            c.z <= tz && tz <= __dadd_rn(c.z, c.w);
 }
 
-template <bool kQuad, bool kInside, bool kPot, bool kSoft>
+template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false>
 __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
@@ -122,10 +126,17 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                 const float tlz = __double2float_rn(tz - (double)thz);
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
-                float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // per-image sums
-                float cx = 0.f, cy = 0.f, cz = 0.f;              // their compensations
+                float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // sums of the last <= 16 iterations
+                float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // image sums + compensation
+                int it = 0;
                 for (;;) {
                     if (next >= wend) next = kEnd;
+                    if ((++it & 15) == 0) {   // warp-uniform flush into the compensated sums
+                        kadd(sx, cx, fx);
+                        kadd(sy, cy, fy);
+                        kadd(sz, cz, fz);
+                        fx = fy = fz = 0.f;
+                    }
                     const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
                     if (e == kEnd) break;
                     const float4 ra = __ldg(&A.ra[e]);
@@ -142,9 +153,9 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                                 const float m = -ra.w;
                                 const float inv = rsqrt_nr(kSoft ? r2 + A.soft2f : r2);
                                 const float f = m * (inv * inv * inv);
-                                kadd(fx, cx, f * dx);
-                                kadd(fy, cy, f * dy);
-                                kadd(fz, cz, f * dz);
+                                fx += f * dx;
+                                fy += f * dy;
+                                fz += f * dz;
                                 if (kPot) fp -= m * inv;
                                 nleaf++;
                             }
@@ -193,9 +204,9 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                                 tz_ += c * dz - inv5 * qz;
                                 if (kPot) fp -= 0.5f * dqd * inv5;
                             }
-                            kadd(fx, cx, tx_);
-                            kadd(fy, cy, ty_);
-                            kadd(fz, cz, tz_);
+                            fx += tx_;
+                            fy += ty_;
+                            fz += tz_;
                             ncell++;
                             next = __float_as_int(rb.w);
                         } else {
@@ -203,9 +214,12 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                         }
                     }
                 }
-                ax += (double)fx - (double)cx;
-                ay += (double)fy - (double)cy;
-                az += (double)fz - (double)cz;
+                kadd(sx, cx, fx);
+                kadd(sy, cy, fy);
+                kadd(sz, cz, fz);
+                ax += (double)sx - (double)cx;
+                ay += (double)sy - (double)cy;
+                az += (double)sz - (double)cz;
                 pot += (double)fp;
             }
     if (valid) {
@@ -364,13 +378,27 @@ struct CollArgs {
     double t0, half_dt;
 };
 
+// Overlap test of Sect. 5.1 on the canonical orientation (a = lower id, b
+// seen through image offset o), operation for operation as the oracle.
+__device__ __forceinline__ bool overlap64(double xa, double ya, double za, double ra, double xb,
+                                          double yb, double zb, double rb, double ox, double oy,
+                                          double oz) {
+    const double rx = __dsub_rn(__dadd_rn(xb, ox), xa);
+    const double ry = __dsub_rn(__dadd_rn(yb, oy), ya);
+    const double rz = __dsub_rn(__dadd_rn(zb, oz), za);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+    const double sr = __dadd_rn(ra, rb);
+    return r2 < __dmul_rn(sr, sr);
+}
+
 // Tree collision search (Sect. 5.2): descend while the distance from the
 // target point to a cell's centre is below R_i + R_max + (sqrt(3)/2) w (Eq. 3,
-// tested in FP32 with a 2e-5 relative margin so that no overlap is pruned);
-// at a leaf j the overlap test of Sect. 5.1 runs in FP64 in the oracle's
-// operation order on the canonical orientation (lower id a, image of b).
-// Only the lower-id particle of a pair records it, so each overlap is found
-// once: the higher-id particle would see it through the opposite image.
+// tested in FP32 with a 2e-5 relative margin so that no overlap is pruned).
+// Each unordered pair is examined once, from its lower slot (the other
+// particle reaches it through the opposite image).  A leaf is first screened
+// in FP32 (hi/lo positions, 1e-4 margin, so no overlap is lost); survivors get
+// the exact FP64 test in the oracle's operation order on the canonical
+// orientation (lower id a, image of b as seen from a).
 __global__ void __launch_bounds__(128) k_collide(CollArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
@@ -411,20 +439,30 @@ __global__ void __launch_bounds__(128) k_collide(CollArgs A) {
                     if (__float_as_int(ra.w) < 0) {
                         if (act) {
                             const int j = ~__float_as_int(ra.w);
-                            if (j != i) {
-                                const int jid = A.id[j];
-                                if (pid < jid) {
-                                    const double rx = __dsub_rn(__dadd_rn(A.x[j], ox), px);
-                                    const double ry = __dsub_rn(__dadd_rn(A.y[j], oy), py);
-                                    const double rz = __dsub_rn(__dadd_rn(A.z[j], oz), pz);
-                                    const double r2 = __dadd_rn(
-                                        __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)),
-                                        __dmul_rn(rz, rz));
-                                    const double sr = __dadd_rn(pr, A.r[j]);
-                                    if (r2 < __dmul_rn(sr, sr)) {
-                                        hit = true;
+                            if (j > i) {
+                                const float4 rb = __ldg(&A.rb[e]);
+                                const float dx = (ra.x - thx) + (rb.x - tlx);
+                                const float dy = (ra.y - thy) + (rb.y - tly);
+                                const float dz = (ra.z - thz) + (rb.z - tlz);
+                                const float d2 = dx * dx + dy * dy + dz * dz;
+                                const float sr = prf + rb.w;
+                                if (d2 < sr * sr * 1.0001f) {
+                                    const int jid = A.id[j];
+                                    if (pid < jid) {
+                                        hit = overlap64(px, py, pz, pr, A.x[j], A.y[j], A.z[j],
+                                                        A.r[j], ox, oy, oz);
                                         key = ((uint64_t)pid << 36) | ((uint64_t)jid << 12) |
                                               (uint64_t)code;
+                                    } else {
+                                        // j is the lower id: this particle is its image -g
+                                        double nx, ny, nz;
+                                        image_offset(bp, s, -gx, -gy, -gz, nx, ny, nz);
+                                        hit = overlap64(A.x[j], A.y[j], A.z[j], A.r[j], px, py, pz,
+                                                        pr, nx, ny, nz);
+                                        const int ncode =
+                                            (-gx + 7) | ((-gy + 7) << 4) | ((-gz + 7) << 8);
+                                        key = ((uint64_t)jid << 36) | ((uint64_t)pid << 12) |
+                                              (uint64_t)ncode;
                                     }
                                 }
                             }
