@@ -311,6 +311,65 @@ def cpu_baseline(sim, cfg, P, args):
     return base, fe
 
 
+def run_ensemble(args):
+    """256 shearing boxes of uneven N advanced together (every stage one
+    launch over all boxes, one CUDA graph per step) against the same boxes as
+    256 single-box simulations stepped one after another.  Prints one JSON
+    line (not the headline metric)."""
+    import torch
+
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    boxes = I.ensemble_boxes(256)
+    parts = [(Lb, I.sheet(Lb, nb, seed + 7919)) for nb, Lb, seed in boxes]
+    ntot = sum(P.n for _, P in parts)
+
+    def cfg(L):
+        c = sheet_config(rb, args.walk)
+        c["box"] = (L, L, L)
+        return c
+
+    ens = rb.Sim(nbox=len(parts), stream=stream.cuda_stream, **cfg(parts[0][0]))
+    for b, (Lb, P) in enumerate(parts):
+        ens.set_box(b, (Lb, Lb, Lb))
+        ens.set_particles(P, box=b)
+    tuned = rb.rb_autotune(ens.h)
+    ens.step(args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ens.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batched = e0.elapsed_time(e1) / 1e3
+    singles = []
+    for Lb, P in parts:
+        s = rb.Sim(stream=stream.cuda_stream, **cfg(Lb))
+        s.set_particles(P)
+        s.step(1)
+        singles.append(s)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s in singles:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_looped = e0.elapsed_time(e1) / 1e3
+    line = {"metric": "particle-steps/s (256-box shearing-sheet ensemble)", "unit": UNIT,
+            "value": ntot * args.steps / t_batched, "looped_single_boxes": ntot * args.steps / t_looped,
+            "speedup": t_looped / t_batched, "particles": ntot, "boxes": len(parts),
+            "steps": args.steps, "warmup": args.warmup, "walk_block, search_block": tuned,
+            "dtype": "f32" if args.walk == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "256 shearing boxes, N_b log-uniform [500, 20000], surface "
+                                   "density log-uniform [200, 1000] kg/m^2, theta=0.5, SEI, eps=0.5"}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -351,12 +410,16 @@ def main():
     ap.add_argument("--particles", type=int, default=N_SHEET,
                     help="sheet size (default 1M; smaller sizes are for profiling only)")
     ap.add_argument("--box", type=float, default=L_SHEET, help="sheet side in m (default 2050)")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="measure the 256-box ensemble (batched vs looped) instead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     N_SHEET, L_SHEET = args.particles, args.box
     if args.impl == "reference":
         run_reference(args)
+    elif args.ensemble:
+        run_ensemble(args)
     else:
         run_ours(args)
 

@@ -81,6 +81,8 @@ typedef struct rb_stats_t {
     int64_t fp64_rechecks;    /* FP32 opening tests decided again in FP64 (guard band) */
     int64_t pair_capacity;    /* current pair buffer capacity */
     int64_t kernels_per_step; /* kernel launches in one captured step graph */
+    int64_t walk_block;       /* threads per block of the gravity walk */
+    int64_t search_block;     /* threads per block of the collision search */
     double  t;                /* simulation time */
     double  ms_last_step;     /* device time of the last step (events), ms */
     /* device time of each stage of the last step when profiling is on (ms):
@@ -170,8 +172,56 @@ int rb_stats(rb_sim* sim, rb_stats_t* out);
 /* on = 1: record CUDA events between the stages of every step (event nodes
  * inside the step graph) so rb_stats reports per-stage device times. */
 int rb_set_profiling(rb_sim* sim, int on);
+/* Time the gravity walk and the collision search at 64, 128 and 256 threads
+ * per block on the current positions (best of 3 after a warm-up each) and
+ * keep the fastest; results are cached per (particle-count bucket, theta,
+ * walk mode, batched) for the process, and use_cache = 1 takes a cached
+ * choice without timing.  Positions and velocities are not changed. */
+int rb_autotune(rb_sim* sim, int use_cache);
 /* Destroy the simulation and free its device memory. */
 void rb_destroy(rb_sim* sim);
+
+/* Learned far-field correction.  Not in the paper: a network
+ * 12 -> 64 -> 64 -> 64 -> 3 (GELU, tanh form) predicts, for a target point p
+ * and an accepted cell (Sect. 4.2), the residual between the cell's exact
+ * force (Eq. 1 over its particles) and its multipole force, in units of
+ * G M / R^2 (R = |p - com|).  Inputs: r_hat (3), w/R, log10 N_c,
+ * (com - centre)/w (3), and with Qh = Q/(M w^2): r_hat.Qh.r_hat, |Qh r_hat|,
+ * tr(Qh^2), det(Qh).  Weights: 9347 floats, W1 (12x64), b1, W2 (64x64), b2,
+ * W3 (64x64), b3, W4 (64x3), b4, each W row-major input x output; the
+ * kernels run them as BF16 on tensor cores with FP32 accumulation. */
+#define RB_MLP_PARAMS 9347
+/* Load the weights (host array) and the fallback angle theta_fb in
+ * (0, cfg.theta]: with walk = RB_WALK_FP32_LEARNED the walk runs at
+ * cfg.theta and adds the predicted residual of every accepted cell with
+ * w/R > theta_fb.  Errors: RB_ERR_ARG (count or angle), RB_ERR_NONFINITE. */
+int rb_load_mlp(rb_sim* sim, const float* w, int64_t nw, double theta_fallback);
+/* Training samples from the current positions of every box: a tree walk at
+ * theta_hi records the accepted cells with w/R > theta_lo, each kept with
+ * probability prob (a counter-based hash of the request and seed); for each
+ * the 12 inputs (X, host, cap x 12) and the residual (Y, cap x 3) are
+ * computed in FP64.  meta (cap x 5, may be NULL): target id, image code,
+ * cell depth, lowest particle id in the cell, particles in the cell.
+ * *n_out = samples written (min(found, cap)). */
+int rb_mlp_samples(rb_sim* sim, double theta_hi, double theta_lo, double prob, uint64_t seed,
+                   int64_t cap, int64_t* n_out, float* X, float* Y, int64_t* meta);
+/* Train on n samples (host X n x 12, Y n x 3) with Adam (lr, beta 0.9 /
+ * 0.999, eps 1e-8) on the mean squared error, minibatches of `batch` rows
+ * in an order shuffled per epoch from `seed`.  Inputs and outputs are
+ * standardised per column for training: w_init (host, 9347) is the start in
+ * standardised units; w_out (host, 9347) is the result with the scales
+ * folded back into W1, b1, W4, b4 (raw units, ready for rb_load_mlp);
+ * loss_hist (host, epochs; may be NULL) is each epoch's mean loss, the
+ * standardised loss times the mean output variance.  No simulation needed;
+ * NULL stream: the call makes its own. */
+int rb_mlp_train(const float* X, const float* Y, int64_t n, int epochs, int batch, double lr,
+                 uint64_t seed, const float* w_init, float* w_out, float* loss_hist,
+                 void* cuda_stream);
+/* Gradient (host, 9347) and mean squared error of the whole set (n rows)
+ * under weights w, as the training kernels compute them (BF16 operands,
+ * FP32 accumulation). */
+int rb_mlp_grad(const float* w, const float* X, const float* Y, int64_t n, float* grad, float* loss,
+                void* cuda_stream);
 
 /* Energy and momentum sums without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc,

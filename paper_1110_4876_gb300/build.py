@@ -20,7 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "librb.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["rb_sort.cu", "rb_tree.cu", "rb_walk.cu", "rb_step.cu", "rb_api.cu", "rb_noalloc.cu"]
+SOURCES = ["rb_sort.cu", "rb_tree.cu", "rb_walk.cu", "rb_step.cu", "rb_api.cu", "rb_noalloc.cu",
+           "rb_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

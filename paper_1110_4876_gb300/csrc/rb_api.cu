@@ -11,6 +11,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <random>
 #include <string>
 #include <utility>
 #include <vector>
@@ -71,6 +74,17 @@ struct rb_sim {
     float last_ms = 0.f;
     float stage_ms[12] = {};
     Ctl hctl{};
+    // learned far-field correction
+    float* mlp_w = nullptr;      // padded FP32 weights
+    void* mlp_wbf = nullptr;     // padded BF16 weights
+    bool mlp_loaded = false;
+    double theta_fb = 0.5;
+    uint64_t* req = nullptr;     // requests of the learned walk
+    int req_cap = 0;
+    std::vector<void*> mlp_allocs, req_allocs;
+    // launch shapes (threads per block) of the gravity walk and the search
+    int walk_block = 128, search_block = 128;
+    bool tuned = false;
 };
 
 namespace {
@@ -323,6 +337,19 @@ WalkOut walk_out(rb_sim* s) {
     return o;
 }
 
+// Arguments of the request kernels for the tree built on set c.
+mlp::ReqArgs req_args(rb_sim* s, int c, int hs, const uint64_t* req, int cap) {
+    mlp::ReqArgs A;
+    const PSet& P = s->P[c];
+    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.id = P.id; A.box = P.box;
+    A.boxes = s->d_boxes; A.ctl = s->ctl; A.key = s->T.key;
+    A.e_first = s->T.e_first; A.e_count = s->T.e_count; A.e_level = s->T.e_level;
+    A.d_a = s->T.d_a; A.d_q0 = s->T.d_q0; A.d_q1 = s->T.d_q1;
+    A.req = req; A.req_count = &s->ctl->req_count; A.req_cap = cap;
+    A.G = s->C.G; A.t0 = s->C.t0; A.half_dt = s->C.half_dt; A.hs = hs;
+    return A;
+}
+
 // Stage marker: an event record node in the step graph when profiling.
 void mark(rb_sim* s, int k) {
     // External: a real event record node (inside a capture a plain record is
@@ -350,8 +377,21 @@ int record_step(rb_sim* s, int p) {
         mark(s, 3);
         build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st);
         mark(s, 4);
-        gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk, 1, walk_out(s), false, true,
-                     st);
+        if (s->cfg.walk == RB_WALK_FP32_LEARNED) {
+            // walk at theta recording the accepted cells with w/R > theta_fb,
+            // then add the network's residual for each of them
+            cudaMemsetAsync(&s->ctl->req_count, 0, sizeof(int), st);
+            const WalkRecord rec{s->req, &s->ctl->req_count, s->req_cap,
+                                 (float)((s->theta_fb / s->cfg.theta) * (s->theta_fb / s->cfg.theta)),
+                                 0xffffffffu, 0u};
+            gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, RB_WALK_FP32, 1, walk_out(s), false,
+                         true, st, &rec, s->walk_block);
+            mlp::correct_async(req_args(s, c, 1, s->req, s->req_cap), s->mlp_wbf, s->mlp_w, s->acc_x,
+                               s->acc_y, s->acc_z, st);
+        } else {
+            gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk, 1, walk_out(s), false,
+                         true, st, nullptr, s->walk_block);
+        }
         mark(s, 5);
         drift_keys(s->P[c], s->T, s->ctl, s->d_boxes, s->C, s->ncap, 1, 2, s->acc_x, s->acc_y,
                    s->acc_z, true, st);
@@ -369,7 +409,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 8);
         build_collision_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
         mark(s, 9);
-        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st);
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block);
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st);
         mark(s, 11);
@@ -382,8 +422,29 @@ int record_step(rb_sim* s, int p) {
     return c;
 }
 
+// Requests of the learned walk: at most this many per particle.
+constexpr int kReqPerParticle = 256;
+
+// Request buffer of the learned walk (kReqPerParticle per particle).
+int ensure_requests(rb_sim* s) {
+    if (!s->mlp_loaded) return fail(s, RB_ERR_STATE, "the learned walk needs rb_load_mlp first");
+    const long long want = (long long)kReqPerParticle * s->ncap;
+    if (want > 0x7fffffffll) return fail(s, RB_ERR_ARG, "too many particles for the learned walk");
+    if (s->req_cap < want) {
+        drop_graphs(s);
+        free_list(s, s->req_allocs);
+        if (dalloc(s, &s->req, (size_t)want, s->req_allocs)) return RB_ERR_CUDA;
+        s->req_cap = (int)want;
+    }
+    return RB_OK;
+}
+
 int capture_graphs(rb_sim* s) {
     drop_graphs(s);
+    if (s->cfg.walk == RB_WALK_FP32_LEARNED) {
+        int rc = ensure_requests(s);
+        if (rc) return rc;
+    }
     for (int p = 0; p < 2; p++) {
         cudaGraph_t g = nullptr;
         RB_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
@@ -427,7 +488,8 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve) {
     for (int attempt = 0; attempt < 2; attempt++) {
         RB_CUDA(s, cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream));
         if (clear_err(s)) return RB_ERR_CUDA;
-        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream);
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
+                         s->search_block);
         sort_pairs(s->PR, s->ctl, s->stream);
         if (read_ctl(s)) return RB_ERR_CUDA;
         if (s->hctl.pair_count <= s->PR.cap) {
@@ -465,12 +527,28 @@ int rebuild_now(rb_sim* s) {
 }
 
 int gravity_now(rb_sim* s, bool potential) {
+    const bool learned = !potential && s->cfg.walk == RB_WALK_FP32_LEARNED;
+    if (learned) {
+        int rc = ensure_requests(s);
+        if (rc) return rc;
+    }
     rebuild_now(s);
     const bool fp64 = potential || s->cfg.walk == RB_WALK_FP64;
     build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
     clear_walk_stats(s->ctl, s->stream);
-    gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64 ? RB_WALK_FP64 : s->cfg.walk, 0,
-                 walk_out(s), potential, true, s->stream);
+    if (learned) {
+        cudaMemsetAsync(&s->ctl->req_count, 0, sizeof(int), s->stream);
+        const WalkRecord rec{s->req, &s->ctl->req_count, s->req_cap,
+                             (float)((s->theta_fb / s->cfg.theta) * (s->theta_fb / s->cfg.theta)),
+                             0xffffffffu, 0u};
+        gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, RB_WALK_FP32, 0, walk_out(s), false,
+                     true, s->stream, &rec, s->walk_block);
+        mlp::correct_async(req_args(s, s->cur, 0, s->req, s->req_cap), s->mlp_wbf, s->mlp_w, s->acc_x,
+                           s->acc_y, s->acc_z, s->stream);
+    } else {
+        gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64 ? RB_WALK_FP64 : s->cfg.walk, 0,
+                     walk_out(s), potential, true, s->stream, nullptr, s->walk_block);
+    }
     s->acc_set = s->cur;
     RB_CUDA(s, cudaGetLastError());
     return read_ctl(s);
@@ -518,7 +596,6 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
     if (c.boundary < 0 || c.boundary > 2) return fail(nullptr, RB_ERR_ARG, "unknown boundary");
     if (c.integrator < 0 || c.integrator > 1) return fail(nullptr, RB_ERR_ARG, "unknown integrator");
     if (c.walk < 0 || c.walk > 2) return fail(nullptr, RB_ERR_ARG, "unknown walk mode");
-    if (c.walk == RB_WALK_FP32_LEARNED) return fail(nullptr, RB_ERR_ARG, "learned walk needs rb_load_mlp (not built)");
     if (c.integrator == RB_INT_SEI && !(c.omega > 0.0)) return fail(nullptr, RB_ERR_ARG, "SEI needs omega > 0");
     if (c.boundary == RB_BC_SHEAR && !(c.omega > 0.0)) return fail(nullptr, RB_ERR_ARG, "shear boundaries need omega > 0");
     if (c.nghost[2] > 0 && !c.z_periodic) return fail(nullptr, RB_ERR_ARG, "ghost boxes in z need z_periodic");
@@ -599,6 +676,8 @@ int rb_step(rb_sim* s, int64_t nsteps) {
         s->cur = s->gafter[p];
         s->acc_set = s->cfg.gravity ? (s->cfg.collisions ? 1 - s->cur : s->cur) : -1;
         if (s->hctl.err & kErrNonFinite) return fail(s, RB_ERR_NONFINITE, "a position became non-finite");
+        if (s->cfg.walk == RB_WALK_FP32_LEARNED && s->hctl.req_count > s->req_cap)
+            return fail(s, RB_ERR_CAPACITY, "learned-correction requests exceeded 256 per particle");
         if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
             // the step ended before resolution: search again with a larger buffer
             if ((rc = collide_with_retry(s, s->cur, 0, true))) return rc;
@@ -804,7 +883,115 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     out->t = s->cfg.t0 + (double)(2 * c.step) * (0.5 * s->cfg.dt);
     out->ms_last_step = s->last_ms;
     out->kernels_per_step = s->kernels_per_step;
+    out->walk_block = s->walk_block;
+    out->search_block = s->search_block;
     for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
+    return RB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Launch shapes chosen by rb_autotune, per (particle-count bucket, theta in
+// thousandths, walk mode, batched boxes), shared by every simulation of the
+// process.
+struct TuneKey {
+    int nbucket, theta_milli, walk, batched;
+    bool operator<(const TuneKey& o) const {
+        if (nbucket != o.nbucket) return nbucket < o.nbucket;
+        if (theta_milli != o.theta_milli) return theta_milli < o.theta_milli;
+        if (walk != o.walk) return walk < o.walk;
+        return batched < o.batched;
+    }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::mutex g_tune_mutex;
+
+TuneKey tune_key(const rb_sim* s) {
+    int b = 0;
+    while ((1LL << b) < (long long)std::max(s->ntot, 1)) b++;
+    return TuneKey{b, (int)std::lround(s->cfg.theta * 1000.0), s->cfg.walk, s->nbox > 1 ? 1 : 0};
+}
+
+// Fastest of 3 repetitions (after one warm-up) of a launch sequence.
+template <typename F>
+float time_best(rb_sim* s, F&& launch) {
+    launch();
+    float best = 1e30f;
+    for (int r = 0; r < 3; r++) {
+        cudaEventRecord(s->ev0, s->stream);
+        launch();
+        cudaEventRecord(s->ev1, s->stream);
+        cudaEventSynchronize(s->ev1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+        best = std::min(best, ms);
+    }
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rb_autotune(rb_sim* s, int use_cache) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (s->ntot == 0) return RB_OK;
+    const TuneKey key = tune_key(s);
+    if (use_cache) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            s->walk_block = it->second.first;
+            s->search_block = it->second.second;
+            s->tuned = true;
+            drop_graphs(s);
+            return RB_OK;
+        }
+    }
+    const int cand[3] = {64, 128, 256};
+    int wb = s->walk_block, sb = s->search_block;
+    if (s->cfg.gravity) {
+        rebuild_now(s);
+        const bool fp64 = s->cfg.walk == RB_WALK_FP64;
+        build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
+        float best = 1e30f;
+        for (int b : cand) {
+            const float ms = time_best(s, [&] {
+                gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C,
+                             fp64 ? RB_WALK_FP64 : RB_WALK_FP32, 0, walk_out(s), false, false, s->stream,
+                             nullptr, b);
+            });
+            if (ms < best) { best = ms; wb = b; }
+        }
+        s->acc_set = -1;   // the tuning walks left no consistent acceleration record
+    }
+    if (s->cfg.collisions) {
+        rebuild_now(s);
+        build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+        float best = 1e30f;
+        for (int b : cand) {
+            const float ms = time_best(s, [&] {
+                cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream);
+                collision_search(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->PR, 0, s->stream, b);
+            });
+            if (ms < best) { best = ms; sb = b; }
+        }
+        cudaMemsetAsync(&s->ctl->pair_n, 0, sizeof(int), s->stream);
+    }
+    RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    RB_CUDA(s, cudaGetLastError());
+    s->walk_block = wb;
+    s->search_block = sb;
+    s->tuned = true;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = {wb, sb};
+    }
+    drop_graphs(s);
     return RB_OK;
 }
 
@@ -822,6 +1009,8 @@ void rb_destroy(rb_sim* s) {
     drop_graphs(s);
     free_list(s, s->pair_allocs);
     free_list(s, s->allocs);
+    free_list(s, s->mlp_allocs);
+    free_list(s, s->req_allocs);
     cudaStreamSynchronize(s->stream);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
@@ -833,6 +1022,272 @@ void rb_destroy(rb_sim* s) {
 
 const char* rb_last_error(const rb_sim* s) {
     return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+// ---- learned far-field correction ----
+
+int rb_load_mlp(rb_sim* s, const float* w, int64_t nw, double theta_fallback) {
+    if (!s || !w || nw != RB_MLP_PARAMS) return fail(s, RB_ERR_ARG, "expected 9347 weights");
+    if (!(theta_fallback > 0.0) || theta_fallback > s->cfg.theta)
+        return fail(s, RB_ERR_ARG, "theta_fallback must be in (0, theta]");
+    for (int64_t i = 0; i < nw; i++)
+        if (!std::isfinite(w[i])) return fail(s, RB_ERR_NONFINITE, "non-finite weight");
+    const int np = mlp::padded_size();
+    if (!s->mlp_w) {
+        if (dalloc(s, &s->mlp_w, np, s->mlp_allocs)) return RB_ERR_CUDA;
+        uint16_t* bf = nullptr;
+        if (dalloc(s, &bf, np, s->mlp_allocs)) return RB_ERR_CUDA;
+        s->mlp_wbf = bf;
+    }
+    std::vector<float> pad(np);
+    mlp::to_padded(w, pad.data());
+    RB_CUDA(s, cudaMemcpyAsync(s->mlp_w, pad.data(), sizeof(float) * np, cudaMemcpyHostToDevice, s->stream));
+    mlp::to_bf16_async(s->mlp_w, s->mlp_wbf, s->stream);
+    RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->mlp_loaded = true;
+    s->theta_fb = theta_fallback;
+    drop_graphs(s);
+    return RB_OK;
+}
+
+int rb_mlp_samples(rb_sim* s, double theta_hi, double theta_lo, double prob, uint64_t seed,
+                   int64_t cap, int64_t* n_out, float* X, float* Y, int64_t* meta) {
+    if (!s || !n_out || !(theta_hi > 0.0) || !(theta_lo > 0.0) || !(theta_lo < theta_hi) ||
+        !(prob > 0.0) || cap < 1 || cap > 0x7fffffffll)
+        return fail(s, RB_ERR_ARG, "bad sampling arguments");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (!s->cfg.gravity) return fail(s, RB_ERR_STATE, "gravity is off");
+    *n_out = 0;
+    if (s->ntot == 0) return RB_OK;
+    rebuild_now(s);
+    SimC C2 = s->C;
+    C2.theta = theta_hi;
+    C2.theta2 = theta_hi * theta_hi;
+    C2.crit_scale = 1.0 / (theta_hi * theta_hi);
+    build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, C2, false, s->stream);
+    std::vector<void*> tmp;
+    uint64_t* req = nullptr;
+    float *dX = nullptr, *dY = nullptr;
+    int64_t* dmeta = nullptr;
+    if (dalloc(s, &req, cap, tmp) || dalloc(s, &dX, 12 * cap, tmp) || dalloc(s, &dY, 3 * cap, tmp) ||
+        dalloc(s, &dmeta, 5 * cap, tmp)) {
+        free_list(s, tmp);
+        return RB_ERR_CUDA;
+    }
+    cudaMemsetAsync(&s->ctl->req_count, 0, sizeof(int), s->stream);
+    const uint32_t thresh = prob >= 1.0 ? 0xffffffffu : (uint32_t)(prob * 4294967296.0);
+    const WalkRecord rec{req, &s->ctl->req_count, (int)cap,
+                         (float)((theta_lo / theta_hi) * (theta_lo / theta_hi)), thresh,
+                         (uint32_t)(seed ^ (seed >> 32))};
+    clear_walk_stats(s->ctl, s->stream);
+    gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, C2, RB_WALK_FP32, 0, walk_out(s), false, true,
+                 s->stream, &rec);
+    s->acc_set = s->cur;
+    mlp::label_async(req_args(s, s->cur, 0, req, (int)cap), dX, dY, dmeta, (int)cap, s->stream);
+    rc = read_ctl(s);
+    const int64_t n = std::min<int64_t>(s->hctl.req_count, cap);
+    if (!rc && n > 0) {
+        if (X) cudaMemcpyAsync(X, dX, sizeof(float) * 12 * n, cudaMemcpyDeviceToHost, s->stream);
+        if (Y) cudaMemcpyAsync(Y, dY, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s->stream);
+        if (meta) cudaMemcpyAsync(meta, dmeta, sizeof(int64_t) * 5 * n, cudaMemcpyDeviceToHost, s->stream);
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, RB_ERR_CUDA, "sample copy failed");
+    }
+    free_list(s, tmp);
+    cudaStreamSynchronize(s->stream);
+    *n_out = n;
+    return rc;
+}
+
+}  // extern "C"
+
+// Standalone training and gradient entry points (no simulation).
+namespace {
+
+struct MlpBufs {
+    cudaStream_t s = nullptr;
+    bool own = false;
+    std::vector<void*> ptrs;
+    template <typename T>
+    T* alloc(size_t n) {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), s) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    ~MlpBufs() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+        cudaStreamSynchronize(s);
+        if (own) cudaStreamDestroy(s);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int rb_mlp_grad(const float* w, const float* X, const float* Y, int64_t n, float* grad, float* loss,
+                void* cuda_stream) {
+    if (!w || !X || !Y || n < 1 || n > 0x7fffffffll || !grad) {
+        g_create_error = "rb_mlp_grad: bad arguments";
+        return RB_ERR_ARG;
+    }
+    MlpBufs B;
+    B.s = static_cast<cudaStream_t>(cuda_stream);
+    if (!B.s) {
+        cudaStreamCreateWithFlags(&B.s, cudaStreamNonBlocking);
+        B.own = true;
+    }
+    const int np = mlp::padded_size();
+    float* dw = B.alloc<float>(np);
+    uint16_t* dwb = B.alloc<uint16_t>(np);
+    float* dX = B.alloc<float>(12 * n);
+    float* dY = B.alloc<float>(3 * n);
+    int32_t* didx = B.alloc<int32_t>(n);
+    float* dg = B.alloc<float>(np);
+    float* dl = B.alloc<float>(1);
+    if (!dw || !dwb || !dX || !dY || !didx || !dg || !dl) {
+        g_create_error = "rb_mlp_grad: device allocation failed";
+        return RB_ERR_CUDA;
+    }
+    std::vector<float> pad(np);
+    mlp::to_padded(w, pad.data());
+    std::vector<int32_t> idx(n);
+    for (int64_t i = 0; i < n; i++) idx[i] = (int32_t)i;
+    cudaMemcpyAsync(dw, pad.data(), sizeof(float) * np, cudaMemcpyHostToDevice, B.s);
+    cudaMemcpyAsync(dX, X, sizeof(float) * 12 * n, cudaMemcpyHostToDevice, B.s);
+    cudaMemcpyAsync(dY, Y, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, B.s);
+    cudaMemcpyAsync(didx, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, B.s);
+    cudaMemsetAsync(dl, 0, sizeof(float), B.s);
+    mlp::to_bf16_async(dw, dwb, B.s);
+    if (mlp::grad_async(dwb, dw, dX, dY, didx, (int)n, (int)n, dg, dl, B.s) != cudaSuccess) {
+        g_create_error = "rb_mlp_grad: launch failed";
+        return RB_ERR_CUDA;
+    }
+    float lsum = 0.f;
+    cudaMemcpyAsync(pad.data(), dg, sizeof(float) * np, cudaMemcpyDeviceToHost, B.s);
+    cudaMemcpyAsync(&lsum, dl, sizeof(float), cudaMemcpyDeviceToHost, B.s);
+    if (cudaStreamSynchronize(B.s) != cudaSuccess) {
+        g_create_error = "rb_mlp_grad: CUDA error";
+        return RB_ERR_CUDA;
+    }
+    mlp::from_padded(pad.data(), grad);
+    if (loss) *loss = lsum / (3.0f * (float)n);
+    return RB_OK;
+}
+
+int rb_mlp_train(const float* X, const float* Y, int64_t n, int epochs, int batch, double lr,
+                 uint64_t seed, const float* w_init, float* w_out, float* loss_hist,
+                 void* cuda_stream) {
+    if (!X || !Y || n < 1 || n > 0x7fffffffll || epochs < 1 || batch < 16 || !(lr > 0.0) || !w_init ||
+        !w_out) {
+        g_create_error = "rb_mlp_train: bad arguments";
+        return RB_ERR_ARG;
+    }
+    MlpBufs B;
+    B.s = static_cast<cudaStream_t>(cuda_stream);
+    if (!B.s) {
+        cudaStreamCreateWithFlags(&B.s, cudaStreamNonBlocking);
+        B.own = true;
+    }
+    const int np = mlp::padded_size();
+    float* dw = B.alloc<float>(np);
+    float* dm = B.alloc<float>(np);
+    float* dv = B.alloc<float>(np);
+    uint16_t* dwb = B.alloc<uint16_t>(np);
+    float* dX = B.alloc<float>(12 * n);
+    float* dY = B.alloc<float>(3 * n);
+    int32_t* didx = B.alloc<int32_t>(n);
+    float* dg = B.alloc<float>(np);
+    float* dl = B.alloc<float>(epochs);
+    if (!dw || !dm || !dv || !dwb || !dX || !dY || !didx || !dg || !dl) {
+        g_create_error = "rb_mlp_train: device allocation failed";
+        return RB_ERR_CUDA;
+    }
+    std::vector<float> pad(np);
+    mlp::to_padded(w_init, pad.data());
+    // train on standardised inputs and outputs (zero mean, unit variance per
+    // column); the scales are folded back into W1, b1, W4, b4 at the end, so
+    // w_init is in standardised units and w_out in raw units
+    double mu[15] = {0}, sd[15] = {0};
+    for (int64_t i = 0; i < n; i++) {
+        for (int c = 0; c < 12; c++) mu[c] += X[i * 12 + c];
+        for (int c = 0; c < 3; c++) mu[12 + c] += Y[i * 3 + c];
+    }
+    for (int c = 0; c < 15; c++) mu[c] /= (double)n;
+    for (int64_t i = 0; i < n; i++) {
+        for (int c = 0; c < 12; c++) sd[c] += (X[i * 12 + c] - mu[c]) * (X[i * 12 + c] - mu[c]);
+        for (int c = 0; c < 3; c++) sd[12 + c] += (Y[i * 3 + c] - mu[12 + c]) * (Y[i * 3 + c] - mu[12 + c]);
+    }
+    for (int c = 0; c < 15; c++) sd[c] = sd[c] > 0.0 ? std::sqrt(sd[c] / (double)n) : 1.0;
+    std::vector<float> Xn((size_t)n * 12), Yn((size_t)n * 3);
+    for (int64_t i = 0; i < n; i++) {
+        for (int c = 0; c < 12; c++) Xn[i * 12 + c] = (float)((X[i * 12 + c] - mu[c]) / sd[c]);
+        for (int c = 0; c < 3; c++) Yn[i * 3 + c] = (float)((Y[i * 3 + c] - mu[12 + c]) / sd[12 + c]);
+    }
+    cudaMemcpyAsync(dw, pad.data(), sizeof(float) * np, cudaMemcpyHostToDevice, B.s);
+    cudaMemsetAsync(dm, 0, sizeof(float) * np, B.s);
+    cudaMemsetAsync(dv, 0, sizeof(float) * np, B.s);
+    cudaMemsetAsync(dl, 0, sizeof(float) * epochs, B.s);
+    cudaMemcpyAsync(dX, Xn.data(), sizeof(float) * 12 * n, cudaMemcpyHostToDevice, B.s);
+    cudaMemcpyAsync(dY, Yn.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, B.s);
+    mlp::to_bf16_async(dw, dwb, B.s);
+    std::vector<int32_t> idx(n);
+    std::mt19937_64 rng(seed);
+    int step = 0;
+    for (int ep = 0; ep < epochs; ep++) {
+        for (int64_t i = 0; i < n; i++) idx[i] = (int32_t)i;
+        std::shuffle(idx.begin(), idx.end(), rng);
+        cudaMemcpyAsync(didx, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, B.s);
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int nb = (int)std::min<int64_t>(batch, n - b0);
+            if (mlp::grad_async(dwb, dw, dX, dY, didx + b0, nb, nb, dg, dl + ep, B.s) != cudaSuccess) {
+                g_create_error = "rb_mlp_train: launch failed";
+                return RB_ERR_CUDA;
+            }
+            mlp::adam_async(dw, dm, dv, dg, dwb, (float)lr, ++step, B.s);
+        }
+        // the host permutation buffer is reused next epoch
+        if (cudaStreamSynchronize(B.s) != cudaSuccess) {
+            g_create_error = "rb_mlp_train: CUDA error";
+            return RB_ERR_CUDA;
+        }
+    }
+    std::vector<float> losses(epochs);
+    cudaMemcpyAsync(pad.data(), dw, sizeof(float) * np, cudaMemcpyDeviceToHost, B.s);
+    cudaMemcpyAsync(losses.data(), dl, sizeof(float) * epochs, cudaMemcpyDeviceToHost, B.s);
+    if (cudaStreamSynchronize(B.s) != cudaSuccess) {
+        g_create_error = "rb_mlp_train: CUDA error";
+        return RB_ERR_CUDA;
+    }
+    mlp::from_padded(pad.data(), w_out);
+    // fold the standardisation into the weights: z1 = ((x - mu)/sd) W1 + b1 and
+    // y = (h3 W4 + b4) sd_y + mu_y
+    {
+        float* W1 = w_out;              // 12 x 64
+        float* b1 = w_out + 12 * 64;    // 64
+        for (int o = 0; o < 64; o++) {
+            double b = b1[o];
+            for (int c = 0; c < 12; c++) {
+                b -= mu[c] / sd[c] * W1[c * 64 + o];
+                W1[c * 64 + o] = (float)(W1[c * 64 + o] / sd[c]);
+            }
+            b1[o] = (float)b;
+        }
+        float* W4 = w_out + RB_MLP_PARAMS - 3 - 64 * 3;   // 64 x 3
+        float* b4 = w_out + RB_MLP_PARAMS - 3;
+        for (int c = 0; c < 3; c++) {
+            for (int h = 0; h < 64; h++) W4[h * 3 + c] = (float)(W4[h * 3 + c] * sd[12 + c]);
+            b4[c] = (float)(b4[c] * sd[12 + c] + mu[12 + c]);
+        }
+    }
+    // per-epoch mean loss in raw units (the standardised loss times the
+    // mean output variance)
+    const double var_y = (sd[12] * sd[12] + sd[13] * sd[13] + sd[14] * sd[14]) / 3.0;
+    if (loss_hist)
+        for (int ep = 0; ep < epochs; ep++)
+            loss_hist[ep] = (float)(losses[ep] / (3.0 * (double)n) * var_y);
+    return RB_OK;
 }
 
 }  // extern "C"

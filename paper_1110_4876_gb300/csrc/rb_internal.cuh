@@ -64,6 +64,8 @@ struct Ctl {
     int pending;               // pairs not yet resolved
     int resolved;              // pairs that were approaching and were resolved
     int err;                   // error bits (kErr*)
+    int req_count;             // learned-correction requests recorded by the last walk
+    int pad_;
     unsigned long long n_cell, n_leaf, n_mac, n_recheck;
 };
 constexpr int kErrNonFinite = 1;
@@ -169,11 +171,24 @@ struct WalkOut {
     double *ax, *ay, *az, *phi;   // per sorted slot
     int32_t *ncell, *nleaf, *nmac;
 };
+// Optional recording of accepted cells with w/R > theta_lo (learned mode):
+// requests (slot << 40) | (image code << 28) | entry, kept when a hash of
+// the request is below thresh.
+struct WalkRecord {
+    uint64_t* req;
+    int* count;
+    int cap;
+    float band_scale;   // (theta_lo / theta)^2
+    uint32_t thresh, seed;
+};
+// Walk and search kernels take their block size (64, 128 or 256 threads)
+// at run time; the autotuner picks it.
+constexpr int kMaxWalkBlock = 256;
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
-                  bool counts, cudaStream_t s);
+                  bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128);
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
-                      const Pairs& PR, int half_step_offset, cudaStream_t s);
+                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128);
 
 // rb_step.cu
 void drift_keys(const PSet& P, const Tree& T, Ctl* ctl, const BoxP* boxes, const SimC& C,
@@ -190,6 +205,37 @@ void step_advance(Ctl* ctl, cudaStream_t s);
 
 // rb_api.cu: message returned by rb_last_error(NULL) on this thread.
 void set_global_error(const std::string& msg);
+
+// rb_mlp.cu: learned far-field correction.
+namespace mlp {
+struct ReqArgs {
+    const double *x, *y, *z, *m;
+    const int32_t *id, *box;
+    const BoxP* boxes;
+    const Ctl* ctl;
+    const uint64_t* key;               // sorted Morton keys of the tree
+    const int32_t *e_first, *e_count;
+    const int8_t* e_level;
+    const double4_32a *d_a, *d_q0, *d_q1;
+    const uint64_t* req;               // requests recorded by the walk
+    const int* req_count;
+    int req_cap;
+    double G, t0, half_dt;
+    int hs;                            // half-step offset of the walk's time
+};
+int padded_size();
+void to_padded(const float* canonical, float* padded);
+void from_padded(const float* padded, float* canonical);
+cudaError_t grad_async(const void* wbf, const float* wf, const float* X, const float* Y,
+                       const int32_t* idx, int n, int n_total, float* grad, float* loss,
+                       cudaStream_t s);
+void adam_async(float* w, float* m, float* v, const float* grad, void* wbf, float lr, int step,
+                cudaStream_t s);
+void to_bf16_async(const float* w, void* wbf, cudaStream_t s);
+void label_async(const ReqArgs& A, float* X, float* Y, int64_t* meta, int max_req, cudaStream_t s);
+void correct_async(const ReqArgs& A, const void* wbf, const float* wf, double* ax, double* ay,
+                   double* az, cudaStream_t s);
+}  // namespace mlp
 void clear_walk_stats(Ctl* ctl, cudaStream_t s);
 
 }  // namespace rb

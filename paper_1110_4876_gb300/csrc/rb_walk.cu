@@ -96,7 +96,7 @@ __device__ __forceinline__ bool inside64(const double4_32a& c, double tx, double
 }
 
 template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false>
-__global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
+__global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
     if (wbase >= n) return;
@@ -104,31 +104,40 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
     const int i = wbase + lane;
     const bool valid = i < n;
     const int ii = valid ? i : n - 1;
-    const double px = A.x[ii], py = A.y[ii], pz = A.z[ii];
-    const BoxP bp = A.boxes[A.box[ii]];
     const int root = A.box_root[A.box[ii]];
     const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
     const int self_leaf = A.leaf_of[ii];
-    const double t = time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset);
-    const double s = shear_offset(bp, t);
-    double ax = 0.0, ay = 0.0, az = 0.0, pot = 0.0;
+    // the FP64 target point of the current image: read only by the rare FP64
+    // re-decisions, so it lives in shared memory rather than in registers
+    __shared__ double tgt[3][kMaxWalkBlock];
+    double pot = 0.0;
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // sums + compensation
     int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0;
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
             for (int gz = -A.ngz; gz <= A.ngz; gz++) {
-                double ox, oy, oz;
-                image_offset(bp, s, gx, gy, gz, ox, oy, oz);
-                const double tx = __dsub_rn(px, ox), ty = __dsub_rn(py, oy), tz = __dsub_rn(pz, oz);
-                const float thx = __double2float_rn(tx), thy = __double2float_rn(ty),
-                            thz = __double2float_rn(tz);
-                const float tlx = __double2float_rn(tx - (double)thx);
-                const float tly = __double2float_rn(ty - (double)thy);
-                const float tlz = __double2float_rn(tz - (double)thz);
+                float thx, thy, thz, tlx, tly, tlz;
+                {
+                    const BoxP bp = A.boxes[A.box[ii]];
+                    const double s = shear_offset(bp, time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset));
+                    double ox, oy, oz;
+                    image_offset(bp, s, gx, gy, gz, ox, oy, oz);
+                    const double tx = __dsub_rn(A.x[ii], ox), ty = __dsub_rn(A.y[ii], oy),
+                                 tz = __dsub_rn(A.z[ii], oz);
+                    tgt[0][threadIdx.x] = tx;
+                    tgt[1][threadIdx.x] = ty;
+                    tgt[2][threadIdx.x] = tz;
+                    thx = __double2float_rn(tx); thy = __double2float_rn(ty); thz = __double2float_rn(tz);
+                    tlx = __double2float_rn(tx - (double)thx);
+                    tly = __double2float_rn(ty - (double)thy);
+                    tlz = __double2float_rn(tz - (double)thz);
+                }
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
                 float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // sums of the last <= 16 iterations
-                float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // image sums + compensation
                 int it = 0;
+                bool rec = false;     // kRecord: this lane accepted a band cell this iteration
+                uint64_t rkey = 0;
                 for (;;) {
                     if (next >= wend) next = kEnd;
                     if ((++it & 15) == 0) {   // warp-uniform flush into the compensated sums
@@ -167,7 +176,8 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                         nmac++;
                         bool acc = ra.w < r2;
                         if (fabsf(ra.w - r2) <= 1e-5f * r2) {
-                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, tx, ty, tz);
+                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, tgt[0][threadIdx.x],
+                                        tgt[1][threadIdx.x], tgt[2][threadIdx.x]);
                             nrecheck++;
                         }
                         if (kInside && acc) {
@@ -179,7 +189,8 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                             const float w = ch.w, tol = 1e-5f * ch.w;
                             const float mx = fminf(fminf(ux, w - ux), fminf(fminf(uy, w - uy), fminf(uz, w - uz)));
                             if (fabsf(mx) <= tol) {
-                                acc = !inside64(ld_d4(&A.d_c[e]), tx, ty, tz);
+                                acc = !inside64(ld_d4(&A.d_c[e]), tgt[0][threadIdx.x],
+                                                tgt[1][threadIdx.x], tgt[2][threadIdx.x]);
                                 nrecheck++;
                             } else if (mx > 0.f) {
                                 acc = false;
@@ -209,23 +220,39 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
                             fz += tz_;
                             ncell++;
                             next = __float_as_int(rb.w);
+                            if (kRecord && ra.w > A.band_scale * r2) {
+                                const uint32_t code = (gx + 7) | ((gy + 7) << 4) | ((gz + 7) << 8);
+                                rec = A.thresh == 0xffffffffu ||
+                                      req_hash((uint32_t)i, (uint32_t)e, code, A.seed) < A.thresh;
+                                if (rec)
+                                    rkey = ((uint64_t)i << 40) | ((uint64_t)code << 28) | (uint64_t)e;
+                            }
                         } else {
                             next = e + 1;
                         }
+                    }
+                    if (kRecord) {
+                        // accepted band cells of this iteration, appended warp by warp
+                        const unsigned m = __ballot_sync(kFull, rec);
+                        if (m) {
+                            const int leader = __ffs(m) - 1;
+                            int pos = 0;
+                            if (lane == leader) pos = atomicAdd(A.req_count, __popc(m));
+                            pos = __shfl_sync(kFull, pos, leader) + __popc(m & ((1u << lane) - 1u));
+                            if (rec && pos < A.req_cap) A.req[pos] = rkey;
+                        }
+                        rec = false;
                     }
                 }
                 kadd(sx, cx, fx);
                 kadd(sy, cy, fy);
                 kadd(sz, cz, fz);
-                ax += (double)sx - (double)cx;
-                ay += (double)sy - (double)cy;
-                az += (double)sz - (double)cz;
                 pot += (double)fp;
             }
     if (valid) {
-        A.out.ax[i] = A.G * ax;
-        A.out.ay[i] = A.G * ay;
-        A.out.az[i] = A.G * az;
+        A.out.ax[i] = A.G * ((double)sx - (double)cx);
+        A.out.ay[i] = A.G * ((double)sy - (double)cy);
+        A.out.az[i] = A.G * ((double)sz - (double)cz);
         if (kPot) A.out.phi[i] = A.G * pot;
         if (A.out.ncell) {
             A.out.ncell[i] = ncell;
@@ -254,7 +281,7 @@ __global__ void __launch_bounds__(128) k_walk32(GravArgs A) {
 // FP64 walk: the same traversal on FP64 records, every opening test in the
 // oracle's operation sequence.
 template <bool kQuad, bool kInside, bool kPot>
-__global__ void __launch_bounds__(128) k_walk64(GravArgs A) {
+__global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
     if (wbase >= n) return;
@@ -399,7 +426,7 @@ __device__ __forceinline__ bool overlap64(double xa, double ya, double za, doubl
 // in FP32 (hi/lo positions, 1e-4 margin, so no overlap is lost); survivors get
 // the exact FP64 test in the oracle's operation order on the canonical
 // orientation (lower id a, image of b as seen from a).
-__global__ void __launch_bounds__(128) k_collide(CollArgs A) {
+__global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
     if (wbase >= n) return;
@@ -497,9 +524,16 @@ __global__ void __launch_bounds__(128) k_collide(CollArgs A) {
 
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
-                  bool counts, cudaStream_t s) {
+                  bool counts, cudaStream_t s, const WalkRecord* rec, int block) {
+    block = (block == 64 || block == 256) ? block : 128;
     if (T.cap_n <= 0) return;
     GravArgs A;
+    A.req = nullptr; A.req_count = nullptr; A.req_cap = 0;
+    A.band_scale = 0.f; A.thresh = 0u; A.seed = 0u;
+    if (rec) {
+        A.req = rec->req; A.req_count = rec->count; A.req_cap = rec->cap;
+        A.band_scale = rec->band_scale; A.thresh = rec->thresh; A.seed = rec->seed;
+    }
     A.x = P.x; A.y = P.y; A.z = P.z; A.box = P.box;
     A.ra = T.ra; A.rb = T.rb; A.rq0 = T.rq0; A.rq1 = T.rq1; A.rc_hi = T.rc_hi; A.rc_lo = T.rc_lo;
     A.d_a = reinterpret_cast<const double4_32a*>(T.d_a);
@@ -518,10 +552,19 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     const bool inside = C.theta2 > (1.0 / 3.0);
     const bool quad = C.quadrupole != 0;
     const bool soft = C.soft2 > 0.0;
-    const int grid = ceil_div(T.cap_n, 128);
-#define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, 128, 0, s>>>(A)
-#define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, 128, 0, s>>>(A)
-    if (walk_mode == 0 || potential) {
+    const int grid = ceil_div(T.cap_n, block);
+#define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, 0, s>>>(A)
+#define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, block, 0, s>>>(A)
+    if (rec) {
+        // FP32 walk that also records accepted band cells (quadrupole on)
+        if (inside) {
+            if (soft) k_walk32<true, true, false, true, true><<<grid, block, 0, s>>>(A);
+            else k_walk32<true, true, false, false, true><<<grid, block, 0, s>>>(A);
+        } else {
+            if (soft) k_walk32<true, false, false, true, true><<<grid, block, 0, s>>>(A);
+            else k_walk32<true, false, false, false, true><<<grid, block, 0, s>>>(A);
+        }
+    } else if (walk_mode == 0 || potential) {
         if (quad) {
             if (inside) { if (potential) RB_W64(true, true, true); else RB_W64(true, true, false); }
             else { if (potential) RB_W64(true, false, true); else RB_W64(true, false, false); }
@@ -543,8 +586,9 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
 }
 
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
-                      const Pairs& PR, int half_step_offset, cudaStream_t s) {
+                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block) {
     if (T.cap_n <= 0) return;
+    block = (block == 64 || block == 256) ? block : 128;
     CollArgs A;
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r; A.id = P.id; A.box = P.box;
     A.ra = T.ra; A.rb = T.rb; A.box_root = T.box_root; A.e_skip = T.e_skip; A.boxes = boxes;
@@ -552,7 +596,7 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.pair_key = PR.key; A.pair_cap = PR.cap; A.ncap = T.cap_n;
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
     A.half_step_offset = half_step_offset; A.t0 = C.t0; A.half_dt = C.half_dt;
-    k_collide<<<ceil_div(T.cap_n, 128), 128, 0, s>>>(A);
+    k_collide<<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
 }
 
 }  // namespace rb

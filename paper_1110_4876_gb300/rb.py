@@ -25,7 +25,9 @@ EXPORTS = [
     "rb_compute_gravity", "rb_get_accelerations", "rb_get_counts", "rb_get_tree",
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
+    "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_autotune",
 ]
+RB_MLP_PARAMS = 9347
 
 
 class RbError(RuntimeError):
@@ -53,7 +55,7 @@ class rb_stats_t(C.Structure):
         ("pairs_found", C.c_int64), ("pairs_resolved", C.c_int64),
         ("cell_interactions", C.c_int64), ("leaf_interactions", C.c_int64),
         ("mac_tests", C.c_int64), ("fp64_rechecks", C.c_int64), ("pair_capacity", C.c_int64),
-        ("kernels_per_step", C.c_int64),
+        ("kernels_per_step", C.c_int64), ("walk_block", C.c_int64), ("search_block", C.c_int64),
         ("t", C.c_double), ("ms_last_step", C.c_double), ("ms_stage", C.c_double * 12),
     ]
 
@@ -94,6 +96,12 @@ def load():
     lib.rb_get_time.argtypes = [_P, C.POINTER(C.c_double)]
     lib.rb_stats.argtypes = [_P, C.POINTER(rb_stats_t)]
     lib.rb_set_profiling.argtypes = [_P, i32]
+    lib.rb_autotune.argtypes = [_P, i32]
+    lib.rb_load_mlp.argtypes = [_P, _VP, i64, C.c_double]
+    lib.rb_mlp_samples.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_uint64, i64,
+                                   C.POINTER(i64), _VP, _VP, _VP]
+    lib.rb_mlp_train.argtypes = [_VP, _VP, i64, i32, i32, C.c_double, C.c_uint64, _VP, _VP, _VP, _VP]
+    lib.rb_mlp_grad.argtypes = [_VP, _VP, _VP, i64, _VP, _VP, _VP]
     lib.rb_energy_sums_noalloc.argtypes = [i64] + [_VP] * 7 + [i32, C.c_double, C.c_double, _VP,
                                                               _VP]
     lib.rb_destroy.argtypes = [_P]
@@ -273,6 +281,13 @@ def rb_set_profiling(sim, on: bool = True):
     _check(load().rb_set_profiling(sim, 1 if on else 0), sim)
 
 
+def rb_autotune(sim, use_cache: bool = True):
+    """Pick the walk/search launch shapes by timing them; returns the choice."""
+    _check(load().rb_autotune(sim, 1 if use_cache else 0), sim)
+    st = rb_stats(sim)
+    return int(st["walk_block"]), int(st["search_block"])
+
+
 def rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z, out,
                            stream=None):
     """Energy/momentum sums without device allocation; all array arguments
@@ -280,6 +295,55 @@ def rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega
     rc = load().rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z,
                                        out, stream)
     _check(rc, None)
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def rb_load_mlp(sim, w, theta_fallback: float):
+    w = _f32(w)
+    _check(load().rb_load_mlp(sim, _ptr(w), len(w), theta_fallback), sim)
+
+
+def rb_mlp_samples(sim, theta_hi: float, theta_lo: float, prob: float, seed: int, cap: int):
+    """Training samples on the current positions: (X (n,12), Y (n,3), meta (n,5))."""
+    X = np.zeros((cap, 12), np.float32)
+    Y = np.zeros((cap, 3), np.float32)
+    meta = np.zeros((cap, 5), np.int64)
+    n = C.c_int64(0)
+    _check(load().rb_mlp_samples(sim, theta_hi, theta_lo, prob, seed, cap, C.byref(n), _ptr(X),
+                                 _ptr(Y), _ptr(meta)), sim)
+    k = n.value
+    return X[:k], Y[:k], meta[:k]
+
+
+def rb_mlp_train(X, Y, w_init, epochs: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+                 stream=None):
+    """Adam training on the GPU; returns (weights, per-epoch mean loss)."""
+    X = _f32(X, (-1, 12))
+    Y = _f32(Y, (-1, 3))
+    w0 = _f32(w_init)
+    out = np.zeros(RB_MLP_PARAMS, np.float32)
+    hist = np.zeros(epochs, np.float32)
+    _check(load().rb_mlp_train(_ptr(X), _ptr(Y), len(X), epochs, batch, lr, seed, _ptr(w0),
+                               _ptr(out), _ptr(hist), stream), None)
+    return out, hist
+
+
+def rb_mlp_grad(w, X, Y, stream=None):
+    """(gradient (9347,), mean squared error) from the GPU training kernels."""
+    X = _f32(X, (-1, 12))
+    Y = _f32(Y, (-1, 3))
+    w = _f32(w)
+    g = np.zeros(RB_MLP_PARAMS, np.float32)
+    loss = C.c_float(0.0)
+    _check(load().rb_mlp_grad(_ptr(w), _ptr(X), _ptr(Y), len(X), _ptr(g), C.byref(loss), stream),
+           None)
+    return g, loss.value
 
 
 def rb_destroy(sim):
