@@ -121,6 +121,9 @@ def load():
     for fn in (lib.orc_collide_brute, lib.orc_collide_tree):
         fn.restype = C.c_int64
         fn.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _I64, C.c_int64, _U64]
+    lib.orc_collide_tree_sel.restype = C.c_int64
+    lib.orc_collide_tree_sel.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _I64, C.c_int64,
+                                         _I64, C.c_int64, _U64]
     lib.orc_resolve.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _D, _D, _D, _I64,
                                 C.c_int64, _U64]
     lib.orc_drift.argtypes = [_PP, C.c_int64, _D, _D, _D, _D, _D, _D]
@@ -247,6 +250,20 @@ def collide_brute(p: Params, t: float, x, y, z, r, ids, cap=None):
 def collide_tree(p: Params, t: float, x, y, z, r, ids, cap=None):
     """Sect. 5.2 (Eq. 3) search: sorted pair keys."""
     return _collide(load().orc_collide_tree, p, t, x, y, z, r, ids, cap or 4 * len(x) + 16)
+
+
+def collide_tree_targets(p: Params, t: float, x, y, z, r, ids, targets, cap=None):
+    """Sect. 5.2 search from the listed targets only (unsorted keys)."""
+    x, y, z, r = map(_d, (x, y, z, r))
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    sel = np.ascontiguousarray(targets, dtype=np.int64)
+    cap = cap or 16 * len(sel) + 16
+    keys = np.zeros(cap, dtype=np.uint64)
+    k = load().orc_collide_tree_sel(C.byref(p.c()), t, len(x), x, y, z, r, ids, len(sel), sel, cap,
+                                    keys)
+    if k > cap:
+        return collide_tree_targets(p, t, x, y, z, r, ids, targets, int(k))
+    return keys[:k].copy()
 
 
 def decode_pairs(keys):

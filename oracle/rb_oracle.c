@@ -690,6 +690,33 @@ int64_t orc_collide_tree(const orc_params* p, double t, int64_t n, const double*
     return pb.k;
 }
 
+/* The same Eq. 3 search run only from the listed targets (pairs that one of
+ * them records as the lower-id member); used to time the search on a
+ * sample.  Returns the number of pairs found (first `cap` stored, unsorted). */
+int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const double* x,
+                             const double* y, const double* z, const double* r, const int64_t* id,
+                             int64_t nt, const int64_t* tsel, int64_t cap, uint64_t* keys) {
+    double off[3 * ORC_MAXIMG], dvy[ORC_MAXIMG];
+    int code[ORC_MAXIMG];
+    int ni = orc_images(p, t, ORC_MAXIMG, off, dvy, code);
+    double* m1 = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t i = 0; i < n; i++) m1[i] = 1.0;
+    orc_tree* tr = orc_tree_build(n, x, y, z, m1, p->L[0]);
+    double rmax = 0.0;
+    for (int64_t i = 0; i < n; i++) rmax = r[i] > rmax ? r[i] : rmax;
+    orc_pairbuf pb = {keys, 0, cap};
+    for (int64_t k = 0; k < nt; k++) {
+        int64_t i = tsel[k];
+        for (int g = 0; g < ni; g++) {
+            double pt[3] = {x[i] - off[3 * g + 0], y[i] - off[3 * g + 1], z[i] - off[3 * g + 2]};
+            if (n > 0) orc_csearch(tr, 0, pt, i, r[i], rmax, r, id, off + 3 * g, code[g], &pb);
+        }
+    }
+    orc_tree_free(tr);
+    free(m1);
+    return pb.k;
+}
+
 /* Resolution of the collision queue (Sect. 5, Eq. 2; reading R8): pairs in
  * ascending key order; a pair is skipped unless the particles approach; the
  * relative normal velocity is multiplied by -eps and momentum is conserved.

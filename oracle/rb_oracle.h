@@ -65,6 +65,9 @@ int64_t orc_collide_brute(const orc_params* p, double t, int64_t n, const double
 int64_t orc_collide_tree(const orc_params* p, double t, int64_t n, const double* x, const double* y,
                          const double* z, const double* r, const int64_t* id, int64_t cap,
                          uint64_t* keys);
+int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const double* x,
+                             const double* y, const double* z, const double* r, const int64_t* id,
+                             int64_t nt, const int64_t* tsel, int64_t cap, uint64_t* keys);
 void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, const double* y,
                  const double* z, double* vx, double* vy, double* vz, const double* m,
                  const int64_t* id, int64_t npairs, const uint64_t* keys);

@@ -131,3 +131,18 @@ def test_sheet_step_runs_and_collides(orc):
     assert st.n == 2400
     assert np.all(np.abs(st.x) <= 50) and np.all(np.abs(st.y) <= 50)
     assert tot > 0
+
+
+def test_target_subset_search_is_a_subset_of_the_full_search(orc):
+    """The sampled search records exactly the pairs whose lower-id member
+    is a listed target."""
+    L = 30.0
+    x, y, z, r = _dense(7, L=L)
+    ids = np.arange(len(x), dtype=np.int64)
+    p = orc.Params(omega=0.02, L=(L, L, L), nghost=(1, 1, 0), boundary=2)
+    full = orc.collide_tree(p, 5.0, x, y, z, r, ids)
+    sel = np.arange(0, len(x), 3)
+    part = np.sort(orc.collide_tree_targets(p, 5.0, x, y, z, r, ids, sel))
+    a, _, _ = orc.decode_pairs(full)
+    assert part.tolist() == full[np.isin(a, sel)].tolist()
+    assert np.sort(orc.collide_tree_targets(p, 5.0, x, y, z, r, ids, ids)).tolist() == full.tolist()
