@@ -44,17 +44,36 @@ FLOP_CELL, FLOP_LEAF, FLOP_MAC = 60, 20, 10
 
 
 def workload_name(walk: str) -> str:
+    tree = ("theta=0.8 quadrupole + learned residual for w/R > 0.5 (BF16 MLP)" if walk == "learned"
+            else f"theta=0.5 quadrupole, {walk} walk")
     return (f"shearing sheet N={N_SHEET:,} box {L_SHEET:g}x{L_SHEET:g} m, 1 ghost ring, SEI, "
-            f"theta=0.5 quadrupole, {walk} walk, collisions eps=0.5")
+            f"{tree}, collisions eps=0.5")
 
 
 def sheet_config(rb, walk):
     from paper_1110_4876_gb300 import inputs as I
 
+    mode = {"fp32": rb.RB_WALK_FP32, "fp64": rb.RB_WALK_FP64, "learned": rb.RB_WALK_FP32_LEARNED}[walk]
     return dict(G=I.G_SI, omega=I.OMEGA, box=(L_SHEET,) * 3, nghost=(1, 1, 0),
-                boundary=rb.RB_BC_SHEAR, integrator=rb.RB_INT_SEI, theta=0.5, eps=0.5,
-                dt=I.DT_SHEET, gravity=1, collisions=1,
-                walk=rb.RB_WALK_FP32 if walk == "fp32" else rb.RB_WALK_FP64)
+                boundary=rb.RB_BC_SHEAR, integrator=rb.RB_INT_SEI,
+                theta=0.8 if walk == "learned" else 0.5, eps=0.5, dt=I.DT_SHEET, gravity=1,
+                collisions=1, walk=mode)
+
+
+_WEIGHTS = {}
+
+
+def make_sim(rb, cfg, stream=None, nbox=1):
+    """A simulation; in the learned mode the network is trained once per
+    process (librb's own kernels) and loaded."""
+    sim = rb.Sim(nbox=nbox, stream=stream, **cfg)
+    if cfg["walk"] == rb.RB_WALK_FP32_LEARNED:
+        if "w" not in _WEIGHTS:
+            from paper_1110_4876_gb300 import learned
+
+            _WEIGHTS["w"], _WEIGHTS["loss"] = learned.train_default()
+        rb.rb_load_mlp(sim.h, _WEIGHTS["w"], 0.5)
+    return sim
 
 
 def measured_peaks():
@@ -117,6 +136,23 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(t_ms: float, dist, device) -> float:
+    """The slowest rank's time (all ranks call this)."""
+    if not dist:
+        return t_ms
+    import torch
+
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, n_per_rank: int, steps: int, t_ms: float) -> float:
+    """Particle-steps/s of all ranks together (each rank advances its own
+    n_per_rank particles for `steps` steps; t_ms is the slowest rank)."""
+    return world * n_per_rank * steps / (t_ms / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -140,8 +176,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     cfg = sheet_config(rb, args.walk)
     P = I.sheet(L_SHEET, N_SHEET, SEED + rank)
-    sim = rb.Sim(stream=stream.cuda_stream, **cfg)
+    sim = make_sim(rb, cfg, stream.cuda_stream)
     sim.set_particles(P)
+    tuned = rb.rb_autotune(sim.h)
     rb.rb_set_profiling(sim.h, True)
     sim.step(args.warmup)
 
@@ -172,18 +209,14 @@ def run_ours(args):
             pairs.append(st["pairs_found"])
         e1.record(stream)
         barrier()
-    t_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     clocks = clk.summary()
-    value = world * N_SHEET * args.steps / (t_ms / 1e3)
+    value = whole_job_value(world, N_SHEET, args.steps, t_ms)
 
     # ---- end to end through the C ABI with host buffers ----
     ke = max(1, min(args.steps, 3))
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in P.arrays()]
-    sim_e = rb.Sim(stream=stream.cuda_stream, **cfg)
+    sim_e = make_sim(rb, cfg, stream.cuda_stream)
     sim_e.set_particles(tuple(host))
     sim_e.step(1)  # capture the step graphs outside the timed region
     state = tuple(host)
@@ -222,14 +255,18 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.walk == "fp32" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.walk == "fp64" else "f32",
         "data": "synthetic (seeded shearing-sheet generator; no dataset or weights)",
         "config": {"workload": workload_name(args.walk), "particles_per_gpu": N_SHEET,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "precision": "walk FP32 on hi/lo cell-relative offsets; positions, kick/drift, "
-                                "moments, collisions FP64" if args.walk == "fp32" else "all FP64",
+                   "precision": ("all FP64" if args.walk == "fp64" else
+                                 "walk FP32 on hi/lo cell-relative offsets; positions, kick/drift, "
+                                 "moments, collisions FP64" +
+                                 ("; MLP BF16 weights, FP32 accumulate" if args.walk == "learned"
+                                  else "")),
                    "l2": "no flush: working set (2 x 72 MB particle sets + ~0.4 GB tree) > 129 MB L2",
-                   "pairs_per_step": statistics.mean(pairs)},
+                   "pairs_per_step": statistics.mean(pairs),
+                   "threads_per_block_walk_search": list(tuned)},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
     }
@@ -255,8 +292,10 @@ def walk_traffic():
 
 
 def oracle_sample(P, samples: int, seed: int = 0):
-    """Time the oracle's step on the full workload with the gravity walk run
-    on a sample of targets; returns (seconds per particle-step, details)."""
+    """Time the oracle's step on the workload: drifts and tree builds on all
+    N particles, the gravity walk and the collision search from a random
+    sample of targets, scaled per particle; returns (seconds per
+    particle-step, details, threads, params, sample)."""
     import oracle
     from paper_1110_4876_gb300 import inputs as I
 
@@ -274,17 +313,18 @@ def oracle_sample(P, samples: int, seed: int = 0):
     tree.gravity(p, oracle.time_at(p, 1), targets=sel)
     t_walk = time.perf_counter() - t
     del tree
+    # the search builds its own tree (the collision tree of the step) and
+    # runs from the sampled targets only
     t = time.perf_counter()
-    keys = oracle.collide_tree(p, oracle.time_at(p, 2), s[0], s[1], s[2], P.r, np.arange(n))
+    keys = oracle.collide_tree_targets(p, oracle.time_at(p, 2), s[0], s[1], s[2], P.r, np.arange(n),
+                                       sel)
     t_coll = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.resolve(p, oracle.time_at(p, 2), s[0], s[1], s[2], s[3], s[4], s[5], P.m, np.arange(n), keys)
-    t_res = time.perf_counter() - t
-    per = (2 * t_drift + t_build + t_coll + t_res) / n + t_walk / samples
-    detail = (f"full step on N={n:,} except the gravity walk, which ran on {samples} random "
-              f"targets (all 9 images) and is scaled per particle: drift x2 {2 * t_drift:.2f} s, "
-              f"tree build {t_build:.2f} s, walk sample {t_walk:.2f} s, collision tree search "
-              f"{t_coll:.2f} s ({len(keys)} pairs), resolution {t_res:.2f} s")
+    t_search = max(t_coll - t_build, 0.0)
+    per = (2 * t_drift + 2 * t_build) / n + (t_walk + t_search) / samples
+    detail = (f"N={n:,}: drift x2 {2 * t_drift:.2f} s and two tree builds {2 * t_build:.2f} s on "
+              f"all particles; gravity walk {t_walk:.2f} s and collision search "
+              f"{t_search:.2f} s ({len(keys)} pairs) from {samples} random targets, scaled per "
+              f"particle; resolution not timed (under 1% of the oracle step)")
     return per, detail, oracle.nthreads(), p, sel
 
 
@@ -297,7 +337,7 @@ def cpu_baseline(sim, cfg, P, args):
     per, detail, cores, p, _ = oracle_sample(P, args.cpu_samples)
     base = {"value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": detail}
     # force error of the benchmarked walk at the initial state
-    sim_f = rb.Sim(**cfg)
+    sim_f = make_sim(rb, cfg)
     sim_f.set_particles(P)
     a_gpu = sim_f.gravity()
     sel = np.random.default_rng(1).choice(P.n, 256, replace=False)
@@ -345,6 +385,16 @@ def run_ensemble(args):
     e1.record(stream)
     torch.cuda.synchronize()
     t_batched = e0.elapsed_time(e1) / 1e3
+    # per-stage split of the batched step, from a separate profiled pass
+    rb.rb_set_profiling(ens.h, True)
+    stage_sum, pairs = {}, 0
+    for _ in range(args.steps):
+        ens.step(1)
+        st = ens.stats()
+        pairs += st["pairs_found"]
+        for k, v in st["ms_stage"].items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    rb.rb_set_profiling(ens.h, False)
     singles = []
     for Lb, P in parts:
         s = rb.Sim(stream=stream.cuda_stream, **cfg(Lb))
@@ -363,7 +413,9 @@ def run_ensemble(args):
             "value": ntot * args.steps / t_batched, "looped_single_boxes": ntot * args.steps / t_looped,
             "speedup": t_looped / t_batched, "particles": ntot, "boxes": len(parts),
             "steps": args.steps, "warmup": args.warmup, "walk_block, search_block": tuned,
-            "dtype": "f32" if args.walk == "fp32" else "f64", "data": "synthetic",
+            "pairs_per_step": pairs / args.steps,
+            "stage_ms_per_step (profiled pass)": {k: v / args.steps for k, v in stage_sum.items()},
+            "dtype": "f64" if args.walk == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "256 shearing boxes, N_b log-uniform [500, 20000], surface "
                                    "density log-uniform [200, 1000] kg/m^2, theta=0.5, SEI, eps=0.5"}}
     print(json.dumps(line), flush=True)
@@ -404,7 +456,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--walk", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--walk", choices=["fp32", "fp64", "learned"], default="fp32",
+                    help="fp32 / fp64 walk at theta 0.5, or the learned correction at theta 0.8")
     ap.add_argument("--cpu-samples", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--particles", type=int, default=N_SHEET,

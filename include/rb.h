@@ -164,6 +164,11 @@ int rb_detect_collisions(rb_sim* sim);
  * code = (gx+7) | (gy+7) << 4 | (gz+7) << 8 (host arrays). */
 int rb_get_pairs(rb_sim* sim, int box, int64_t cap, int64_t* n, int64_t* id_a, int64_t* id_b,
                  int32_t* code);
+/* Test hook: set the collision pair buffer to `cap` pairs (>= 1).  A search
+ * that finds more pairs than fit resolves nothing; the step then grows the
+ * buffer and searches again before any velocity changes, so results do not
+ * depend on cap. */
+int rb_set_pair_capacity(rb_sim* sim, int64_t cap);
 /* Set / read the simulation time (restarts the step counter at t). */
 int rb_set_time(rb_sim* sim, double t);
 int rb_get_time(rb_sim* sim, double* t);

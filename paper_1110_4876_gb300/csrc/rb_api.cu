@@ -844,6 +844,14 @@ int rb_energy(rb_sim* s, int box, double* E, double P[3]) {
     return RB_OK;
 }
 
+int rb_set_pair_capacity(rb_sim* s, int64_t cap) {
+    if (!s || cap < 1 || cap > 0x3fffffffll) return fail(s, RB_ERR_ARG, "bad pair capacity");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    drop_graphs(s);
+    return alloc_pairs(s, (int)cap);
+}
+
 int rb_set_time(rb_sim* s, double t) {
     if (!s || !std::isfinite(t)) return fail(s, RB_ERR_ARG, "bad time");
     s->cfg.t0 = t;

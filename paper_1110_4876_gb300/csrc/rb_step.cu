@@ -302,18 +302,57 @@ __global__ void __launch_bounds__(256) k_res_round(ResolveArgs A, SimC C, int r,
     if (nr) atomicAdd(&A.ctl->resolved, nr);
 }
 
-// Whatever the rounds left: one thread, in queue order.
-__global__ void k_res_tail(ResolveArgs A, SimC C, int r) {
+// What the grid-wide rounds left: one block keeps running rounds (same rule,
+// block barriers instead of launches) on the shrinking pending list.  The
+// lowest pending pair is always ready, so every round resolves at least one
+// pair; after kTailRounds rounds any remainder is resolved by one thread in
+// queue order.
+constexpr int kTailRounds = 4096;
+
+__global__ void __launch_bounds__(1024) k_res_tail(ResolveArgs A, SimC C, int r0, int32_t* list_a,
+                                                   int32_t* list_b, const int32_t* __restrict__ rcnt) {
+    __shared__ int cnt_next, nres;
     if (A.ctl->pending == 0) return;
-    const int n = A.ctl->pair_n;
-    int nr = 0;
-    for (int k = 0; k < n; k++) {
-        if (A.rdone[k] >= 0) continue;
-        nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
-        A.rdone[k] = r;
+    int n = rcnt[r0];
+    int32_t* in = list_a;
+    int32_t* out = list_b;
+    if (threadIdx.x == 0) nres = 0;
+    int r = r0;
+    for (; n > 0 && r < r0 + kTailRounds; r++) {
+        if (threadIdx.x == 0) cnt_next = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int k = in[t];
+            const int pa = A.prev_a[k], pb = A.prev_b[k];
+            const bool ready_a = pa < 0 || (unsigned)A.rdone[pa] < (unsigned)r;
+            const bool ready_b = pb < 0 || (unsigned)A.rdone[pb] < (unsigned)r;
+            if (ready_a && ready_b) {
+                if (resolve_one(A, C, A.key[k])) atomicAdd(&nres, 1);
+                A.rdone[k] = r;
+            } else {
+                out[atomicAdd(&cnt_next, 1)] = k;
+            }
+        }
+        __syncthreads();
+        n = cnt_next;
+        int32_t* tmp = in;
+        in = out;
+        out = tmp;
+        __syncthreads();
     }
-    A.ctl->resolved += nr;
-    A.ctl->pending = 0;
+    if (threadIdx.x == 0) {
+        int nr = nres;
+        if (n > 0 || r0 == 0) {
+            const int np = A.ctl->pair_n;
+            for (int k = 0; k < np; k++) {
+                if (A.rdone[k] >= 0) continue;
+                nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
+                A.rdone[k] = r;
+            }
+        }
+        A.ctl->resolved += nr;
+        A.ctl->pending = 0;
+    }
 }
 
 __global__ void k_step_advance(Ctl* ctl) { ctl->step += 1; }
@@ -419,7 +458,12 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
     for (int r = 0; r < rounds && r < 63; r++)
         k_res_round<<<grid, 256, 0, s>>>(A, C, r, (r & 1) ? PR.list0 : PR.list1,
                                          (r & 1) ? PR.list1 : PR.list0, PR.rcnt);
-    k_res_tail<<<1, 1, 0, s>>>(A, C, rounds);
+    const int last = std::min(rounds, 63);
+    // round r writes its survivors to list0 (r even) or list1 (r odd)
+    int32_t* left = (last & 1) ? PR.list0 : PR.list1;
+    int32_t* spare = (last & 1) ? PR.list1 : PR.list0;
+    // with no grid-wide round before it (r0 == 0) the tail resolves in order
+    k_res_tail<<<1, 1024, 0, s>>>(A, C, last, left, spare, PR.rcnt);
 }
 
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,

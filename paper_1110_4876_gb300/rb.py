@@ -26,6 +26,7 @@ EXPORTS = [
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
     "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_autotune",
+    "rb_set_pair_capacity",
 ]
 RB_MLP_PARAMS = 9347
 
@@ -97,6 +98,7 @@ def load():
     lib.rb_stats.argtypes = [_P, C.POINTER(rb_stats_t)]
     lib.rb_set_profiling.argtypes = [_P, i32]
     lib.rb_autotune.argtypes = [_P, i32]
+    lib.rb_set_pair_capacity.argtypes = [_P, i64]
     lib.rb_load_mlp.argtypes = [_P, _VP, i64, C.c_double]
     lib.rb_mlp_samples.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_uint64, i64,
                                    C.POINTER(i64), _VP, _VP, _VP]
@@ -257,6 +259,10 @@ def rb_get_pairs(sim, box: int = 0):
     c = np.zeros(max(k, 1), dtype=np.int32)
     _check(lib.rb_get_pairs(sim, box, k, C.byref(n), _ptr(a), _ptr(b), _ptr(c)), sim)
     return a[:k], b[:k], c[:k]
+
+
+def rb_set_pair_capacity(sim, cap: int):
+    _check(load().rb_set_pair_capacity(sim, cap), sim)
 
 
 def rb_set_time(sim, t: float):
