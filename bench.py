@@ -41,6 +41,7 @@ SMS = 152
 FP32_LANES_PER_SM = 128
 # algorithmic FP32 flops per interaction (FMA = 2, add/mul = 1, rsqrt = 0)
 FLOP_CELL, FLOP_LEAF, FLOP_MAC = 60, 20, 10
+FLOP_MLP = 2 * (12 * 64 + 2 * 64 * 64 + 64 * 3)
 
 
 def workload_name(walk: str) -> str:
@@ -191,7 +192,7 @@ def run_ours(args):
     # ---- device-resident throughput (inputs already in HBM) ----
     walk_ms, walk_flops, stage_sum = [], [], {}
     launches = 0
-    pairs = []
+    pairs, corr = [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -207,6 +208,7 @@ def run_ours(args):
                 stage_sum[k] = stage_sum.get(k, 0.0) + v
             launches += st["kernels_per_step"]
             pairs.append(st["pairs_found"])
+            corr.append(st["corrections"])
         e1.record(stream)
         barrier()
     t_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
@@ -246,12 +248,20 @@ def run_ours(args):
     if not wms > 0.0:
         raise RuntimeError("the gravity walk stage time was not recorded")
     achieved = statistics.mean(walk_flops) / (wms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_walk32 (gravity walk)", "achieved": achieved,
+    kname = ("k_walk32_learn (gravity walk with the in-walk MLP; FP32 flops only)"
+             if args.walk == "learned" else "k_walk32 (gravity walk)")
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": walk_traffic(), "peak_source":
                     f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
                     "(MEASURED_PEAKS.json sm_max_mhz)",
                 "flops_per_launch": statistics.mean(walk_flops), "ms_per_launch": wms}
+    if args.walk == "learned":
+        # tensor-core work of the network: 2 (12 64 + 2 64 64 + 64 3) flops per corrected cell
+        mlp = FLOP_MLP * statistics.mean(corr)
+        roofline["mlp"] = {"corrections_per_launch": statistics.mean(corr), "flops_per_launch": mlp,
+                           "tflops": mlp / (wms / 1e3) / 1e12, "path": "mma.sync m16n8k16 BF16"}
+        roofline["traffic"] = None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,

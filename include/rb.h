@@ -90,6 +90,7 @@ typedef struct rb_stats_t {
      * 5 kick+drift+keys, 6 sort+gather, 7 tree, 8 collision records,
      * 9 collision search, 10 pair sort, 11 resolution */
     double  ms_stage[12];
+    int64_t corrections;      /* learned walk: band cells corrected by the network in the last walk */
 } rb_stats_t;
 
 typedef struct rb_sim rb_sim; /* opaque, owned by the library */
@@ -199,7 +200,10 @@ void rb_destroy(rb_sim* sim);
 /* Load the weights (host array) and the fallback angle theta_fb in
  * (0, cfg.theta]: with walk = RB_WALK_FP32_LEARNED the walk runs at
  * cfg.theta and adds the predicted residual of every accepted cell with
- * w/R > theta_fb.  Errors: RB_ERR_ARG (count or angle), RB_ERR_NONFINITE. */
+ * w/R > theta_fb.  The network runs inside the walk on each warp's queued
+ * band cells (inputs computed in FP32 from the walk records), so there is
+ * no per-particle limit on corrected cells; rb_stats reports how many there
+ * were.  Errors: RB_ERR_ARG (count or angle), RB_ERR_NONFINITE. */
 int rb_load_mlp(rb_sim* sim, const float* w, int64_t nw, double theta_fallback);
 /* Training samples from the current positions of every box: a tree walk at
  * theta_hi records the accepted cells with w/R > theta_lo, each kept with

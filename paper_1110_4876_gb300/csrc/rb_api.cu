@@ -20,6 +20,7 @@
 
 #include "rb.h"
 #include "rb_internal.cuh"
+#include "rb_mlp.cuh"
 
 using namespace rb;
 
@@ -77,11 +78,10 @@ struct rb_sim {
     // learned far-field correction
     float* mlp_w = nullptr;      // padded FP32 weights
     void* mlp_wbf = nullptr;     // padded BF16 weights
+    mlp::Packed* mlp_pk = nullptr;  // inference layout read by the learned walk
     bool mlp_loaded = false;
     double theta_fb = 0.5;
-    uint64_t* req = nullptr;     // requests of the learned walk
-    int req_cap = 0;
-    std::vector<void*> mlp_allocs, req_allocs;
+    std::vector<void*> mlp_allocs;
     // launch shapes (threads per block) of the gravity walk and the search
     int walk_block = 128, search_block = 128;
     bool tuned = false;
@@ -337,6 +337,12 @@ WalkOut walk_out(rb_sim* s) {
     return o;
 }
 
+// Learned-walk arguments: inference weights and the band w/R > theta_fb.
+WalkLearn learn_args(const rb_sim* s) {
+    const double r = s->theta_fb / s->cfg.theta;
+    return WalkLearn{s->mlp_pk, (float)(r * r)};
+}
+
 // Arguments of the request kernels for the tree built on set c.
 mlp::ReqArgs req_args(rb_sim* s, int c, int hs, const uint64_t* req, int cap) {
     mlp::ReqArgs A;
@@ -378,16 +384,12 @@ int record_step(rb_sim* s, int p) {
         build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st);
         mark(s, 4);
         if (s->cfg.walk == RB_WALK_FP32_LEARNED) {
-            // walk at theta recording the accepted cells with w/R > theta_fb,
-            // then add the network's residual for each of them
+            // walk at theta; accepted cells with w/R > theta_fb get the
+            // network's residual inside the walk
             cudaMemsetAsync(&s->ctl->req_count, 0, sizeof(int), st);
-            const WalkRecord rec{s->req, &s->ctl->req_count, s->req_cap,
-                                 (float)((s->theta_fb / s->cfg.theta) * (s->theta_fb / s->cfg.theta)),
-                                 0xffffffffu, 0u};
+            const WalkLearn L = learn_args(s);
             gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, RB_WALK_FP32, 1, walk_out(s), false,
-                         true, st, &rec, s->walk_block);
-            mlp::correct_async(req_args(s, c, 1, s->req, s->req_cap), s->mlp_wbf, s->mlp_w, s->acc_x,
-                               s->acc_y, s->acc_z, st);
+                         true, st, nullptr, s->walk_block, &L);
         } else {
             gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk, 1, walk_out(s), false,
                          true, st, nullptr, s->walk_block);
@@ -422,29 +424,10 @@ int record_step(rb_sim* s, int p) {
     return c;
 }
 
-// Requests of the learned walk: at most this many per particle.
-constexpr int kReqPerParticle = 256;
-
-// Request buffer of the learned walk (kReqPerParticle per particle).
-int ensure_requests(rb_sim* s) {
-    if (!s->mlp_loaded) return fail(s, RB_ERR_STATE, "the learned walk needs rb_load_mlp first");
-    const long long want = (long long)kReqPerParticle * s->ncap;
-    if (want > 0x7fffffffll) return fail(s, RB_ERR_ARG, "too many particles for the learned walk");
-    if (s->req_cap < want) {
-        drop_graphs(s);
-        free_list(s, s->req_allocs);
-        if (dalloc(s, &s->req, (size_t)want, s->req_allocs)) return RB_ERR_CUDA;
-        s->req_cap = (int)want;
-    }
-    return RB_OK;
-}
-
 int capture_graphs(rb_sim* s) {
     drop_graphs(s);
-    if (s->cfg.walk == RB_WALK_FP32_LEARNED) {
-        int rc = ensure_requests(s);
-        if (rc) return rc;
-    }
+    if (s->cfg.walk == RB_WALK_FP32_LEARNED && !s->mlp_loaded)
+        return fail(s, RB_ERR_STATE, "the learned walk needs rb_load_mlp first");
     for (int p = 0; p < 2; p++) {
         cudaGraph_t g = nullptr;
         RB_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
@@ -528,23 +511,16 @@ int rebuild_now(rb_sim* s) {
 
 int gravity_now(rb_sim* s, bool potential) {
     const bool learned = !potential && s->cfg.walk == RB_WALK_FP32_LEARNED;
-    if (learned) {
-        int rc = ensure_requests(s);
-        if (rc) return rc;
-    }
+    if (learned && !s->mlp_loaded) return fail(s, RB_ERR_STATE, "the learned walk needs rb_load_mlp first");
     rebuild_now(s);
     const bool fp64 = potential || s->cfg.walk == RB_WALK_FP64;
     build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
     clear_walk_stats(s->ctl, s->stream);
     if (learned) {
         cudaMemsetAsync(&s->ctl->req_count, 0, sizeof(int), s->stream);
-        const WalkRecord rec{s->req, &s->ctl->req_count, s->req_cap,
-                             (float)((s->theta_fb / s->cfg.theta) * (s->theta_fb / s->cfg.theta)),
-                             0xffffffffu, 0u};
+        const WalkLearn L = learn_args(s);
         gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, RB_WALK_FP32, 0, walk_out(s), false,
-                     true, s->stream, &rec, s->walk_block);
-        mlp::correct_async(req_args(s, s->cur, 0, s->req, s->req_cap), s->mlp_wbf, s->mlp_w, s->acc_x,
-                           s->acc_y, s->acc_z, s->stream);
+                     true, s->stream, nullptr, s->walk_block, &L);
     } else {
         gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64 ? RB_WALK_FP64 : s->cfg.walk, 0,
                      walk_out(s), potential, true, s->stream, nullptr, s->walk_block);
@@ -676,8 +652,6 @@ int rb_step(rb_sim* s, int64_t nsteps) {
         s->cur = s->gafter[p];
         s->acc_set = s->cfg.gravity ? (s->cfg.collisions ? 1 - s->cur : s->cur) : -1;
         if (s->hctl.err & kErrNonFinite) return fail(s, RB_ERR_NONFINITE, "a position became non-finite");
-        if (s->cfg.walk == RB_WALK_FP32_LEARNED && s->hctl.req_count > s->req_cap)
-            return fail(s, RB_ERR_CAPACITY, "learned-correction requests exceeded 256 per particle");
         if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
             // the step ended before resolution: search again with a larger buffer
             if ((rc = collide_with_retry(s, s->cur, 0, true))) return rc;
@@ -894,6 +868,7 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     out->walk_block = s->walk_block;
     out->search_block = s->search_block;
     for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
+    out->corrections = s->cfg.walk == RB_WALK_FP32_LEARNED ? c.req_count : 0;
     return RB_OK;
 }
 
@@ -966,12 +941,14 @@ int rb_autotune(rb_sim* s, int use_cache) {
         rebuild_now(s);
         const bool fp64 = s->cfg.walk == RB_WALK_FP64;
         build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
+        const bool learned = s->cfg.walk == RB_WALK_FP32_LEARNED && s->mlp_loaded;
+        const WalkLearn L = learn_args(s);
         float best = 1e30f;
         for (int b : cand) {
             const float ms = time_best(s, [&] {
                 gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C,
                              fp64 ? RB_WALK_FP64 : RB_WALK_FP32, 0, walk_out(s), false, false, s->stream,
-                             nullptr, b);
+                             nullptr, b, learned ? &L : nullptr);
             });
             if (ms < best) { best = ms; wb = b; }
         }
@@ -1018,7 +995,6 @@ void rb_destroy(rb_sim* s) {
     free_list(s, s->pair_allocs);
     free_list(s, s->allocs);
     free_list(s, s->mlp_allocs);
-    free_list(s, s->req_allocs);
     cudaStreamSynchronize(s->stream);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
@@ -1046,11 +1022,13 @@ int rb_load_mlp(rb_sim* s, const float* w, int64_t nw, double theta_fallback) {
         uint16_t* bf = nullptr;
         if (dalloc(s, &bf, np, s->mlp_allocs)) return RB_ERR_CUDA;
         s->mlp_wbf = bf;
+        if (dalloc(s, &s->mlp_pk, 1, s->mlp_allocs)) return RB_ERR_CUDA;
     }
     std::vector<float> pad(np);
     mlp::to_padded(w, pad.data());
     RB_CUDA(s, cudaMemcpyAsync(s->mlp_w, pad.data(), sizeof(float) * np, cudaMemcpyHostToDevice, s->stream));
     mlp::to_bf16_async(s->mlp_w, s->mlp_wbf, s->stream);
+    mlp::pack_async(s->mlp_w, s->mlp_pk, s->stream);
     RB_CUDA(s, cudaStreamSynchronize(s->stream));
     s->mlp_loaded = true;
     s->theta_fb = theta_fallback;

@@ -181,12 +181,21 @@ struct WalkRecord {
     float band_scale;   // (theta_lo / theta)^2
     uint32_t thresh, seed;
 };
+// Learned walk (walk mode 2): accepted cells with w/R > theta_lo get the
+// network's residual added inside the walk; the number of corrected cells is
+// added to ctl->req_count.
+namespace mlp { struct Packed; }
+struct WalkLearn {
+    const mlp::Packed* w;   // inference weights (device)
+    float band_scale;       // (theta_lo / theta)^2
+};
 // Walk and search kernels take their block size (64, 128 or 256 threads)
 // at run time; the autotuner picks it.
 constexpr int kMaxWalkBlock = 256;
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
-                  bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128);
+                  bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128,
+                  const WalkLearn* learn = nullptr);
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                       const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128);
 
@@ -233,8 +242,6 @@ void adam_async(float* w, float* m, float* v, const float* grad, void* wbf, floa
                 cudaStream_t s);
 void to_bf16_async(const float* w, void* wbf, cudaStream_t s);
 void label_async(const ReqArgs& A, float* X, float* Y, int64_t* meta, int max_req, cudaStream_t s);
-void correct_async(const ReqArgs& A, const void* wbf, const float* wf, double* ax, double* ay,
-                   double* az, cudaStream_t s);
 }  // namespace mlp
 void clear_walk_stats(Ctl* ctl, cudaStream_t s);
 

@@ -4,6 +4,10 @@
 // multipole force (Sect. 4.2), in units of G M / R^2, so the walk can open
 // cells at a wider theta and add the predicted residual.
 //
+// This file holds the training side (residual labels, the tensor-core
+// gradient kernel, Adam) and the packing of trained weights for inference;
+// inference itself runs inside the gravity walk (rb_walk.cu).
+//
 // Tensor cores: every layer of the forward and backward pass is a BF16
 // mma.sync.m16n8k16 with FP32 accumulation on 16-row tiles per warp.  The
 // hidden activations stay in registers between forward layers (the FP32
@@ -16,8 +20,6 @@
 // b4 8 -- 9928 values; the C ABI exchanges the unpadded 9347 values in the
 // order W1 (12x64), b1, W2, b2, W3, b3, W4 (64x3), b4 (row-major, input x
 // output).
-#include <cuda_bf16.h>
-
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -25,40 +27,13 @@
 #include <vector>
 
 #include "rb_internal.cuh"
+#include "rb_mlp.cuh"
 
 namespace rb {
 namespace mlp {
 namespace {
 
-constexpr int kW1 = 0, kB1 = kW1 + 16 * 64, kW2 = kB1 + 64, kB2 = kW2 + 64 * 64;
-constexpr int kW3 = kB2 + 64, kB3 = kW3 + 64 * 64, kW4 = kB3 + 64, kB4 = kW4 + 64 * 8;
-constexpr int kPad = kB4 + 8;   // 9928
-constexpr int kWarps = 4;       // warps per block (16 rows each)
-constexpr float kGeluC = 0.7978845608028654f;   // sqrt(2 / pi)
-
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ uint32_t pack2h(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    __nv_bfloat162 v;
-    v.x = lo;
-    v.y = hi;
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ float gelu(float z) {
-    return 0.5f * z * (1.f + tanhf(kGeluC * (z + 0.044715f * z * z * z)));
-}
+constexpr int kWarps = 4;       // warps per block of the training kernel (16 rows each)
 
 __device__ __forceinline__ float gelu_grad(float z) {
     const float t = tanhf(kGeluC * (z + 0.044715f * z * z * z));
@@ -66,15 +41,7 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // Fragment loads from row-major BF16 matrices in shared memory (lane l:
-// g = l / 4, q = l % 4).
-// A tile (16 x 16) at (r0, c0) of M (ld columns).
-__device__ __forceinline__ void ldA(uint32_t (&a)[4], const __nv_bfloat16* M, int ld, int r0, int c0,
-                                    int g, int q) {
-    a[0] = *reinterpret_cast<const uint32_t*>(&M[(r0 + g) * ld + c0 + 2 * q]);
-    a[1] = *reinterpret_cast<const uint32_t*>(&M[(r0 + g + 8) * ld + c0 + 2 * q]);
-    a[2] = *reinterpret_cast<const uint32_t*>(&M[(r0 + g) * ld + c0 + 8 + 2 * q]);
-    a[3] = *reinterpret_cast<const uint32_t*>(&M[(r0 + g + 8) * ld + c0 + 8 + 2 * q]);
-}
+// g = l / 4, q = l % 4); ldA is shared with the inference path.
 // A tile of M^T: A[m][k] = M[k][m], m in [r0, r0+16), k in [c0, c0+16).
 __device__ __forceinline__ void ldAT(uint32_t (&a)[4], const __nv_bfloat16* M, int ld, int r0, int c0,
                                      int g, int q) {
@@ -497,54 +464,36 @@ __global__ void __launch_bounds__(256) k_mlp_label(ReqArgs A, float* __restrict_
     }
 }
 
-// Learned correction: for every recorded (target, cell) request, the
-// network's residual times G M / R^2 is added to the target's acceleration.
-// Each warp runs 16 requests through the tensor-core MLP.
-__global__ void __launch_bounds__(kWarps * 32) k_mlp_correct(ReqArgs A,
-                                                             const __nv_bfloat16* __restrict__ wbf,
-                                                             const float* __restrict__ wf,
-                                                             double* __restrict__ ax,
-                                                             double* __restrict__ ay,
-                                                             double* __restrict__ az) {
-    __shared__ SW w;
-    __shared__ __nv_bfloat16 Xs[kWarps][16 * 16];
-    __shared__ float Ys[kWarps][16 * 8];
-    load_weights(w, wbf, wf);
-    __syncthreads();
-    const int nreq = min(*A.req_count, A.req_cap);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    const int ntiles = (nreq + 15) / 16;
-    for (int tile = blockIdx.x * kWarps + warp; tile < ntiles; tile += gridDim.x * kWarps) {
-        const int r = tile * 16 + lane;
-        const bool valid = lane < 16 && r < nreq;
-        int slot = 0;
-        double unit = 0.0;
-        if (lane < 16) {
-            float f[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (valid) {
-                CellView v;
-                req_view(A, A.req[r], v);
-                double R2;
-                req_features(A, v, f, R2);
-                slot = v.slot;
-                unit = A.G * v.M / R2;
-            }
-            for (int c = 0; c < 16; c++) Xs[warp][lane * 16 + c] = __float2bfloat16_rn(c < 12 ? f[c] : 0.f);
+// Inference layout (Packed) of the padded FP32 weights: one thread per B
+// fragment entry, then the biases.
+__global__ void k_mlp_pack(const float* __restrict__ w, Packed* __restrict__ P) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int n1 = 8 * 32, n2 = 32 * 32, n4 = 4 * 32;
+    if (i < n1 + 2 * n2 + n4) {
+        int k = i, off, ld, nt;
+        uint2* dst;
+        if (k < n1) {
+            off = kW1; ld = 64; nt = 8; dst = &P->B1[0][0][0];
+        } else if ((k -= n1) < n2) {
+            off = kW2; ld = 64; nt = 8; dst = &P->B2[0][0][0];
+        } else if ((k -= n2) < n2) {
+            off = kW3; ld = 64; nt = 8; dst = &P->B3[0][0][0];
+        } else {
+            k -= n2;
+            off = kW4; ld = 8; nt = 1; dst = &P->B4[0][0][0];
         }
-        __syncwarp();
-        float out[4];
-        forward(w, Xs[warp], out, nullptr, nullptr);
-        Ys[warp][g * 8 + 2 * q] = out[0];
-        Ys[warp][g * 8 + 2 * q + 1] = out[1];
-        Ys[warp][(g + 8) * 8 + 2 * q] = out[2];
-        Ys[warp][(g + 8) * 8 + 2 * q + 1] = out[3];
-        __syncwarp();
-        if (valid) {
-            atomicAdd(&ax[slot], unit * (double)Ys[warp][lane * 8 + 0]);
-            atomicAdd(&ay[slot], unit * (double)Ys[warp][lane * 8 + 1]);
-            atomicAdd(&az[slot], unit * (double)Ys[warp][lane * 8 + 2]);
-        }
-        __syncwarp();
+        const int lane = k & 31, tile = k >> 5, t = tile / nt, j = tile % nt;
+        const int g = lane >> 2, q = lane & 3, r = 16 * t + 2 * q, c = 8 * j + g;
+        const float* W = w + off;
+        uint2 b;
+        b.x = pack2(W[r * ld + c], W[(r + 1) * ld + c]);
+        b.y = pack2(W[(r + 8) * ld + c], W[(r + 9) * ld + c]);
+        dst[k] = b;
+    } else if ((i -= n1 + 2 * n2 + n4) < 200) {
+        if (i < 64) P->b1[i] = w[kB1 + i];
+        else if (i < 128) P->b2[i - 64] = w[kB2 + i - 64];
+        else if (i < 192) P->b3[i - 128] = w[kB3 + i - 128];
+        else P->b4[i - 192] = w[kB4 + i - 192];
     }
 }
 
@@ -555,10 +504,9 @@ void label_async(const ReqArgs& A, float* X, float* Y, int64_t* meta, int max_re
     k_mlp_label<<<blocks, 256, 0, s>>>(A, X, Y, meta);
 }
 
-void correct_async(const ReqArgs& A, const void* wbf, const float* wf, double* ax, double* ay,
-                   double* az, cudaStream_t s) {
-    k_mlp_correct<<<4 * 152, kWarps * 32, 0, s>>>(A, static_cast<const __nv_bfloat16*>(wbf), wf, ax,
-                                                  ay, az);
+void pack_async(const float* w, Packed* packed, cudaStream_t s) {
+    constexpr int n = 8 * 32 + 2 * 32 * 32 + 4 * 32 + 200;
+    k_mlp_pack<<<(n + 255) / 256, 256, 0, s>>>(w, packed);
 }
 
 // ---- host helpers ----

@@ -19,6 +19,7 @@
 #include <cfloat>
 
 #include "rb_internal.cuh"
+#include "rb_mlp.cuh"
 
 namespace rb {
 namespace {
@@ -46,6 +47,9 @@ struct GravArgs {
     float band_scale;   // (theta_lo / theta)^2: band iff (w/theta)^2 > band_scale R^2
     uint32_t thresh;    // keep a request when its hash < thresh (0xffffffff: all)
     uint32_t seed;
+    // learned walk: cell particle counts (an input of the network) and weights
+    const int32_t* e_count;
+    const mlp::Packed* wpk;
 };
 
 __device__ __forceinline__ double4_32a ld_d4(const double4_32a* p) { return *p; }
@@ -95,8 +99,43 @@ __device__ __forceinline__ bool inside64(const double4_32a& c, double tx, double
            c.z <= tz && tz <= __dadd_rn(c.z, c.w);
 }
 
-template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false>
-__global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
+// Per-warp queue of the learned walk: accepted band cells waiting for the
+// network, which runs on 16 of them at a time (one m16 tile).
+struct LearnQ {
+    __nv_bfloat16 X[48][16];   // network inputs (columns 12..15 zero)
+    float unit[48];            // M / R^2 (G is applied with the walk's sums)
+    int own[48];               // lane whose sums receive the output
+    float Y[16][4];            // outputs of the tile being applied
+};
+
+// Rows r0 .. r0 + 15 of the queue through the network; unit * output is
+// added to the owning lanes' partial sums.  Warp-synchronous.
+__device__ __forceinline__ void learn_flush(LearnQ& Q, const mlp::Packed& w, int r0, int lane,
+                                            float& fx, float& fy, float& fz) {
+    __syncwarp();
+    float out[4];
+    mlp::forward_packed(w, &Q.X[r0][0], out);
+    const int g = lane >> 2, q = lane & 3;
+    if (q < 2) {
+        Q.Y[g][2 * q] = out[0];
+        Q.Y[g][2 * q + 1] = out[1];
+        Q.Y[g + 8][2 * q] = out[2];
+        Q.Y[g + 8][2 * q + 1] = out[3];
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int k = 0; k < 16; k++)
+        if (Q.own[r0 + k] == lane) {
+            const float u = Q.unit[r0 + k];
+            fx += u * Q.Y[k][0];
+            fy += u * Q.Y[k][1];
+            fz += u * Q.Y[k][2];
+        }
+    __syncwarp();
+}
+
+template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord, bool kLearn>
+__device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp::Packed* W) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
     if (wbase >= n) return;
@@ -112,7 +151,8 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
     __shared__ double tgt[3][kMaxWalkBlock];
     double pot = 0.0;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // sums + compensation
-    int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0;
+    int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0, ncorr = 0;
+    int qn = 0;   // kLearn: rows waiting in this warp's queue (warp-uniform)
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
             for (int gz = -A.ngz; gz <= A.ngz; gz++) {
@@ -138,6 +178,8 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
                 int it = 0;
                 bool rec = false;     // kRecord: this lane accepted a band cell this iteration
                 uint64_t rkey = 0;
+                bool want = false;    // kLearn: this lane accepted a band cell this iteration
+                float fin[12], funit = 0.f;
                 for (;;) {
                     if (next >= wend) next = kEnd;
                     if ((++it & 15) == 0) {   // warp-uniform flush into the compensated sums
@@ -220,6 +262,34 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
                             fz += tz_;
                             ncell++;
                             next = __float_as_int(rb.w);
+                            if (kLearn && ra.w > A.band_scale * r2) {
+                                // network inputs (the oracle's definition, in FP32 from the
+                                // walk records): r = p - com = -d
+                                const float4 ch = __ldg(&A.rc_hi[e]);
+                                const float4 cl = __ldg(&A.rc_lo[e]);
+                                const float w = ch.w, rw = 1.f / w;
+                                const float hx = -dx * inv, hy = -dy * inv, hz = -dz * inv;
+                                const float sc = rw * rw / q0.x;
+                                const float qxx = q0.y * sc, qyy = q0.z * sc, qzz = q0.w * sc;
+                                const float qxy = q1.x * sc, qxz = q1.y * sc, qyz = q1.z * sc;
+                                const float ux = qxx * hx + qxy * hy + qxz * hz;
+                                const float uy = qxy * hx + qyy * hy + qyz * hz;
+                                const float uz = qxz * hx + qyz * hy + qzz * hz;
+                                fin[0] = hx; fin[1] = hy; fin[2] = hz;
+                                fin[3] = w * inv;
+                                fin[4] = __log2f((float)__ldg(&A.e_count[e])) * 0.30102999566f;
+                                fin[5] = ((ra.x - ch.x) + (rb.x - cl.x)) * rw - 0.5f;
+                                fin[6] = ((ra.y - ch.y) + (rb.y - cl.y)) * rw - 0.5f;
+                                fin[7] = ((ra.z - ch.z) + (rb.z - cl.z)) * rw - 0.5f;
+                                fin[8] = hx * ux + hy * uy + hz * uz;
+                                fin[9] = sqrtf(ux * ux + uy * uy + uz * uz);
+                                fin[10] = qxx * qxx + qyy * qyy + qzz * qzz +
+                                          2.f * (qxy * qxy + qxz * qxz + qyz * qyz);
+                                fin[11] = qxx * (qyy * qzz - qyz * qyz) - qxy * (qxy * qzz - qyz * qxz) +
+                                          qxz * (qxy * qyz - qyy * qxz);
+                                funit = q0.x * inv2;
+                                want = true;
+                            }
                             if (kRecord && ra.w > A.band_scale * r2) {
                                 const uint32_t code = (gx + 7) | ((gy + 7) << 4) | ((gz + 7) << 8);
                                 rec = A.thresh == 0xffffffffu ||
@@ -243,12 +313,56 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
                         }
                         rec = false;
                     }
+                    if (kLearn) {
+                        // band cells of this iteration join the warp's queue; full
+                        // tiles of 16 go through the network
+                        const unsigned m = __ballot_sync(kFull, want);
+                        if (m) {
+                            if (want) {
+                                const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                                uint4 lo, hi;
+                                lo.x = mlp::pack2(fin[0], fin[1]);
+                                lo.y = mlp::pack2(fin[2], fin[3]);
+                                lo.z = mlp::pack2(fin[4], fin[5]);
+                                lo.w = mlp::pack2(fin[6], fin[7]);
+                                hi.x = mlp::pack2(fin[8], fin[9]);
+                                hi.y = mlp::pack2(fin[10], fin[11]);
+                                hi.z = 0u;
+                                hi.w = 0u;
+                                reinterpret_cast<uint4*>(&LQ->X[pos][0])[0] = lo;
+                                reinterpret_cast<uint4*>(&LQ->X[pos][0])[1] = hi;
+                                LQ->unit[pos] = funit;
+                                LQ->own[pos] = lane;
+                                ncorr++;
+                            }
+                            qn += __popc(m);
+                            while (qn >= 16) {
+                                qn -= 16;
+                                learn_flush(*LQ, *W, qn, lane, fx, fy, fz);
+                            }
+                        }
+                        want = false;
+                    }
                 }
                 kadd(sx, cx, fx);
                 kadd(sy, cy, fy);
                 kadd(sz, cz, fz);
                 pot += (double)fp;
             }
+    if (kLearn && qn > 0) {
+        // the last partial tile: empty rows have zero inputs and no owner
+        if (lane >= qn && lane < 16) {
+            reinterpret_cast<uint4*>(&LQ->X[lane][0])[0] = make_uint4(0u, 0u, 0u, 0u);
+            reinterpret_cast<uint4*>(&LQ->X[lane][0])[1] = make_uint4(0u, 0u, 0u, 0u);
+            LQ->unit[lane] = 0.f;
+            LQ->own[lane] = -1;
+        }
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        learn_flush(*LQ, *W, 0, lane, fx, fy, fz);
+        kadd(sx, cx, fx);
+        kadd(sy, cy, fy);
+        kadd(sz, cz, fz);
+    }
     if (valid) {
         A.out.ax[i] = A.G * ((double)sx - (double)cx);
         A.out.ay[i] = A.G * ((double)sy - (double)cy);
@@ -276,6 +390,32 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
         atomicAdd(&A.ctl->n_mac, c2);
         atomicAdd(&A.ctl->n_recheck, c3);
     }
+    if (kLearn) {
+        int c4 = ncorr;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c4 += __shfl_down_sync(kFull, c4, o);
+        if (lane == 0) atomicAdd(&A.ctl->req_count, c4);
+    }
+}
+
+template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false>
+__global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
+    walk32<kQuad, kInside, kPot, kSoft, kRecord, false>(A, nullptr, nullptr);
+}
+
+// Learned walk: the network's weights and one queue per warp in shared
+// memory; up to 128 registers per thread for the MMA fragments.
+template <bool kInside, bool kSoft>
+__global__ void __launch_bounds__(kMaxWalkBlock, 2) k_walk32_learn(GravArgs A) {
+    __shared__ __align__(16) mlp::Packed w;
+    __shared__ __align__(16) LearnQ q[kMaxWalkBlock / 32];
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(A.wpk);
+        uint4* dst = reinterpret_cast<uint4*>(&w);
+        for (int k = threadIdx.x; k < (int)(sizeof(mlp::Packed) / 16); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    walk32<true, kInside, false, kSoft, false, true>(A, &q[threadIdx.x >> 5], &w);
 }
 
 // FP64 walk: the same traversal on FP64 records, every opening test in the
@@ -524,10 +664,13 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
 
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
-                  bool counts, cudaStream_t s, const WalkRecord* rec, int block) {
+                  bool counts, cudaStream_t s, const WalkRecord* rec, int block,
+                  const WalkLearn* learn) {
     block = (block == 64 || block == 256) ? block : 128;
     if (T.cap_n <= 0) return;
     GravArgs A;
+    A.e_count = T.e_count;
+    A.wpk = learn ? learn->w : nullptr;
     A.req = nullptr; A.req_count = nullptr; A.req_cap = 0;
     A.band_scale = 0.f; A.thresh = 0u; A.seed = 0u;
     if (rec) {
@@ -555,7 +698,17 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     const int grid = ceil_div(T.cap_n, block);
 #define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, 0, s>>>(A)
 #define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, block, 0, s>>>(A)
-    if (rec) {
+    if (learn && !potential) {
+        // FP32 walk with the learned correction of band cells (quadrupole on)
+        A.band_scale = learn->band_scale;
+        if (inside) {
+            if (soft) k_walk32_learn<true, true><<<grid, block, 0, s>>>(A);
+            else k_walk32_learn<true, false><<<grid, block, 0, s>>>(A);
+        } else {
+            if (soft) k_walk32_learn<false, true><<<grid, block, 0, s>>>(A);
+            else k_walk32_learn<false, false><<<grid, block, 0, s>>>(A);
+        }
+    } else if (rec) {
         // FP32 walk that also records accepted band cells (quadrupole on)
         if (inside) {
             if (soft) k_walk32<true, true, false, true, true><<<grid, block, 0, s>>>(A);
