@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "librb_oracle.so")
 BC_OPEN, BC_PERIODIC, BC_SHEAR = 0, 1, 2
 INT_LEAPFROG, INT_SEI = 0, 1
 GRAV_NONE, GRAV_TREE, GRAV_DIRECT = 0, 1, 2
-COLL_NONE, COLL_TREE, COLL_BRUTE = 0, 1, 2
+COLL_NONE, COLL_TREE, COLL_BRUTE, COLL_SWEEP = 0, 1, 2, 3
 CENTRAL_CODE = 7 | (7 << 4) | (7 << 8)
 
 
@@ -121,6 +121,10 @@ def load():
     for fn in (lib.orc_collide_brute, lib.orc_collide_tree):
         fn.restype = C.c_int64
         fn.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _I64, C.c_int64, _U64]
+    for fn in (lib.orc_collide_line_brute, lib.orc_collide_sweep):
+        fn.restype = C.c_int64
+        fn.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _D, _D, _D, _I64, C.c_int64,
+                       _U64]
     lib.orc_collide_tree_sel.restype = C.c_int64
     lib.orc_collide_tree_sel.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _I64, C.c_int64,
                                          _I64, C.c_int64, _U64]
@@ -250,6 +254,28 @@ def collide_brute(p: Params, t: float, x, y, z, r, ids, cap=None):
 def collide_tree(p: Params, t: float, x, y, z, r, ids, cap=None):
     """Sect. 5.2 (Eq. 3) search: sorted pair keys."""
     return _collide(load().orc_collide_tree, p, t, x, y, z, r, ids, cap or 4 * len(x) + 16)
+
+
+def collide_line_brute(p: Params, t: float, x, y, z, vx, vy, vz, r, ids, cap=None):
+    """Sect. 5.3 straight-line criterion over every pair and image (sorted keys)."""
+    return _collide_v(load().orc_collide_line_brute, p, t, x, y, z, vx, vy, vz, r, ids,
+                      cap or 4 * len(x) + 16)
+
+
+def collide_sweep(p: Params, t: float, x, y, z, vx, vy, vz, r, ids, cap=None):
+    """Sect. 5.3 plane sweep along x (sorted keys)."""
+    return _collide_v(load().orc_collide_sweep, p, t, x, y, z, vx, vy, vz, r, ids,
+                      cap or 4 * len(x) + 16)
+
+
+def _collide_v(fn, p, t, x, y, z, vx, vy, vz, r, ids, cap):
+    x, y, z, vx, vy, vz, r = map(_d, (x, y, z, vx, vy, vz, r))
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    keys = np.zeros(max(cap, 1), dtype=np.uint64)
+    k = fn(C.byref(p.c()), t, len(x), x, y, z, vx, vy, vz, r, ids, cap, keys)
+    if k > cap:
+        return _collide_v(fn, p, t, x, y, z, vx, vy, vz, r, ids, int(k))
+    return keys[:k].copy()
 
 
 def collide_tree_targets(p: Params, t: float, x, y, z, r, ids, targets, cap=None):

@@ -29,6 +29,19 @@
  *  R8  Sect. 5: collisions are found when particles overlap at the end of the
  *      step and resolved in ascending (id_a, id_b, image) order instead of a
  *      random shuffle, so that results are reproducible.
+ *  S1  Sect. 5.3 approximates trajectories by straight lines between the
+ *      positions before and after the drift: at detection time t (the end of
+ *      the step) particle i moves on x_i + v_i tau, tau in [-dt/2, dt/2] (the
+ *      merged drift around t, during which velocities do not change).
+ *  S2  Sect. 5.3 does not define "a collision during the time-step": two
+ *      lines collide when their smallest distance over that interval is below
+ *      R_a + R_b (closest approach tau* = -(r.u)/|u|^2, clamped).
+ *  S3  the x extent of a trajectory is [x - |v_x| dt/2 - R, x + |v_x| dt/2 + R]
+ *      (both drift ends, widened by the radius), plus 1e-9 Lx on each side so
+ *      rounding cannot drop a pair; ghost images in x are copies shifted by
+ *      +k Lx that are only tested against original particles.
+ *  S4  pairs from the sweep use the key and queue order of R8 and the same
+ *      resolution (Eq. 2); a pair that is receding at t is not resolved.
  */
 #include "rb_oracle.h"
 
@@ -717,6 +730,148 @@ int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const dou
     return pb.k;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Plane-sweep detection (Sect. 5.3; readings S1-S4)                         */
+/* ------------------------------------------------------------------------ */
+
+/* Straight-line criterion (reading S1): over the drift around the detection
+ * time t each particle moves on x + v tau, tau in [-dt/2, dt/2] (the
+ * positions before and after that drift are its ends).  Particle a and the
+ * image of b (offset o, velocity offset dvy in y) collide when the smallest
+ * distance between the two lines over that interval is below R_a + R_b. */
+static int orc_line_hit(const orc_params* p, int64_t a, int64_t b, const double* x,
+                        const double* y, const double* z, const double* vx, const double* vy,
+                        const double* vz, const double* r, const double* o, double dvy) {
+    double h = 0.5 * p->dt;
+    double rx = (x[b] + o[0]) - x[a], ry = (y[b] + o[1]) - y[a], rz = (z[b] + o[2]) - z[a];
+    double ux = vx[b] - vx[a], uy = (vy[b] + dvy) - vy[a], uz = vz[b] - vz[a];
+    double uu = (ux * ux + uy * uy) + uz * uz;
+    double ru = (rx * ux + ry * uy) + rz * uz;
+    double tau = 0.0;
+    if (uu > 0.0) {
+        tau = -ru / uu; /* time of closest approach, clamped to the interval */
+        if (tau < -h) tau = -h;
+        if (tau > h) tau = h;
+    }
+    double dx = rx + ux * tau, dy = ry + uy * tau, dz = rz + uz * tau;
+    double d2 = (dx * dx + dy * dy) + dz * dz;
+    double s = r[a] + r[b];
+    return d2 < s * s;
+}
+
+/* The straight-line criterion by brute force: every pair, every image. */
+int64_t orc_collide_line_brute(const orc_params* p, double t, int64_t n, const double* x,
+                               const double* y, const double* z, const double* vx, const double* vy,
+                               const double* vz, const double* r, const int64_t* id, int64_t cap,
+                               uint64_t* keys) {
+    double off[3 * ORC_MAXIMG], dvy[ORC_MAXIMG];
+    int code[ORC_MAXIMG];
+    int ni = orc_images(p, t, ORC_MAXIMG, off, dvy, code);
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) {
+            if (id[i] >= id[j]) continue;
+            for (int g = 0; g < ni; g++)
+                if (orc_line_hit(p, i, j, x, y, z, vx, vy, vz, r, off + 3 * g, dvy[g])) {
+                    if (k < cap) keys[k] = orc_pair_key(id[i], id[j], code[g]);
+                    k++;
+                }
+        }
+    qsort(keys, (size_t)(k < cap ? k : cap), sizeof(uint64_t), orc_cmp_u64);
+    return k;
+}
+
+/* One stop of the plane: the x extent of an item's trajectory.  An item is a
+ * particle (copy 0) or its copy shifted by +copy Lx (reading S3). */
+typedef struct {
+    double xs;
+    int64_t item;
+    int end; /* 0: the plane reaches the item (insert), 1: it leaves (remove) */
+} orc_stop;
+
+static int orc_cmp_stop(const void* a, const void* b) {
+    const orc_stop *p = (const orc_stop*)a, *q = (const orc_stop*)b;
+    if (p->xs != q->xs) return p->xs < q->xs ? -1 : 1;
+    if (p->end != q->end) return p->end - q->end; /* inserts before removals */
+    return p->item < q->item ? -1 : (p->item > q->item ? 1 : 0);
+}
+
+/* Plane sweep along x (Sect. 5.3).  Each trajectory's x extent (both ends of
+ * the drift, widened by the radius; reading S3) gives two stops; the stops are
+ * sorted; the plane visits them in order keeping the list of trajectories it
+ * cuts (SWEEPL); a trajectory entering the list is tested against every
+ * trajectory already in it with the straight-line criterion.  Ghost images
+ * in x are copies of the particles shifted by +k Lx, k = 1..nghost[0]; a copy
+ * is only tested against original particles, and every (pair, image) is
+ * written in the canonical orientation (lower id a, image of b as seen from
+ * a; reading S4).  Returns the number of pairs (first `cap` stored, sorted). */
+int64_t orc_collide_sweep(const orc_params* p, double t, int64_t n, const double* x,
+                          const double* y, const double* z, const double* vx, const double* vy,
+                          const double* vz, const double* r, const int64_t* id, int64_t cap,
+                          uint64_t* keys) {
+    int ngx = p->boundary == ORC_BC_OPEN ? 0 : p->nghost[0];
+    int ngy = p->boundary == ORC_BC_OPEN ? 0 : p->nghost[1];
+    int ngz = (p->boundary == ORC_BC_OPEN || !p->z_periodic) ? 0 : p->nghost[2];
+    double h = 0.5 * p->dt, Lx = p->L[0], s = shear_offset(p, t), vs = shear_speed(p);
+    double margin = 1e-9 * Lx;
+    int64_t nitem = n * (int64_t)(ngx + 1);
+    orc_stop* st = (orc_stop*)malloc((size_t)(2 * nitem > 0 ? 2 * nitem : 1) * sizeof(orc_stop));
+    for (int64_t q = 0; q < nitem; q++) {
+        int64_t i = q % n;
+        int copy = (int)(q / n);
+        double ext = fabs(vx[i]) * h + r[i];
+        double xc = x[i] + (double)copy * Lx;
+        st[2 * q] = (orc_stop){xc - ext - margin, q, 0};
+        st[2 * q + 1] = (orc_stop){xc + ext + margin, q, 1};
+    }
+    qsort(st, (size_t)(2 * nitem), sizeof(orc_stop), orc_cmp_stop);
+    int64_t* list = (int64_t*)malloc((size_t)(nitem > 0 ? nitem : 1) * sizeof(int64_t));
+    int64_t* where = (int64_t*)malloc((size_t)(nitem > 0 ? nitem : 1) * sizeof(int64_t));
+    int64_t nl = 0, k = 0;
+    for (int64_t e = 0; e < 2 * nitem; e++) {
+        int64_t q = st[e].item;
+        if (st[e].end) { /* remove q from the list (swap with the last) */
+            int64_t w = where[q];
+            list[w] = list[nl - 1];
+            where[list[w]] = w;
+            nl--;
+            continue;
+        }
+        for (int64_t l = 0; l < nl; l++) {
+            int64_t u = list[l];
+            int64_t i = q % n, j = u % n;
+            int ci = (int)(q / n), cj = (int)(u / n);
+            if ((ci != 0 && cj != 0) || i == j) continue;
+            /* image of j as seen from i, then the canonical orientation */
+            int gx = cj - ci;
+            int64_t a = i, b = j;
+            if (id[j] < id[i]) {
+                a = j;
+                b = i;
+                gx = -gx;
+            }
+            for (int gy = -ngy; gy <= ngy; gy++)
+                for (int gz = -ngz; gz <= ngz; gz++) {
+                    double o[3] = {(double)gx * Lx, (double)gy * p->L[1] - (double)gx * s,
+                                   (double)gz * p->L[2]};
+                    if (orc_line_hit(p, a, b, x, y, z, vx, vy, vz, r, o, -(double)gx * vs)) {
+                        int code = (gx + 7) | ((gy + 7) << 4) | ((gz + 7) << 8);
+                        if (k < cap) keys[k] = orc_pair_key(id[a], id[b], code);
+                        k++;
+                    }
+                }
+        }
+        list[nl] = q;
+        where[q] = nl;
+        nl++;
+    }
+    free(list);
+    free(where);
+    free(st);
+    qsort(keys, (size_t)(k < cap ? k : cap), sizeof(uint64_t), orc_cmp_u64);
+    return k;
+}
+
 /* Resolution of the collision queue (Sect. 5, Eq. 2; reading R8): pairs in
  * ascending key order; a pair is skipped unless the particles approach; the
  * relative normal velocity is multiplied by -eps and momentum is conserved.
@@ -807,6 +962,8 @@ int orc_step(const orc_params* p, int64_t step, int64_t* n, double* x, double* y
         uint64_t* keys = pairs && pair_cap > 0 ? pairs : (uint64_t*)malloc((size_t)cap * sizeof(uint64_t));
         if (p->collisions == ORC_COLL_BRUTE)
             np = orc_collide_brute(p, t2, N, x, y, z, r, id, cap, keys);
+        else if (p->collisions == ORC_COLL_SWEEP)
+            np = orc_collide_sweep(p, t2, N, x, y, z, vx, vy, vz, r, id, cap, keys);
         else
             np = orc_collide_tree(p, t2, N, x, y, z, r, id, cap, keys);
         if (np > cap) {

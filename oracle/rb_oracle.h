@@ -25,7 +25,7 @@
 enum { ORC_BC_OPEN = 0, ORC_BC_PERIODIC = 1, ORC_BC_SHEAR = 2 };
 enum { ORC_INT_LEAPFROG = 0, ORC_INT_SEI = 1 };
 enum { ORC_GRAV_NONE = 0, ORC_GRAV_TREE = 1, ORC_GRAV_DIRECT = 2 };
-enum { ORC_COLL_NONE = 0, ORC_COLL_TREE = 1, ORC_COLL_BRUTE = 2 };
+enum { ORC_COLL_NONE = 0, ORC_COLL_TREE = 1, ORC_COLL_BRUTE = 2, ORC_COLL_SWEEP = 3 };
 
 typedef struct {
     double G, omega, omega_z;   /* omega_z <= 0 means omega_z = omega */
@@ -68,6 +68,15 @@ int64_t orc_collide_tree(const orc_params* p, double t, int64_t n, const double*
 int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const double* x,
                              const double* y, const double* z, const double* r, const int64_t* id,
                              int64_t nt, const int64_t* tsel, int64_t cap, uint64_t* keys);
+/* plane sweep (Sect. 5.3): straight-line criterion over tau in [-dt/2, dt/2] */
+int64_t orc_collide_line_brute(const orc_params* p, double t, int64_t n, const double* x,
+                               const double* y, const double* z, const double* vx, const double* vy,
+                               const double* vz, const double* r, const int64_t* id, int64_t cap,
+                               uint64_t* keys);
+int64_t orc_collide_sweep(const orc_params* p, double t, int64_t n, const double* x,
+                          const double* y, const double* z, const double* vx, const double* vy,
+                          const double* vz, const double* r, const int64_t* id, int64_t cap,
+                          uint64_t* keys);
 void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, const double* y,
                  const double* z, double* vx, double* vy, double* vz, const double* m,
                  const int64_t* id, int64_t npairs, const uint64_t* keys);
