@@ -432,6 +432,188 @@ def run_ensemble(args):
     return line
 
 
+def _timed(sim, stream, steps, warmup):
+    """ms per step (CUDA events on the library's stream) and the gravity walk
+    stage's ms per step, after warm-up and autotuning."""
+    import torch
+
+    from paper_1110_4876_gb300 import rb
+
+    rb.rb_autotune(sim.h)
+    rb.rb_set_profiling(sim.h, True)
+    sim.step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    walk = 0.0
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(1)
+        walk += sim.stats()["ms_stage"]["gravity_walk"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, walk / steps
+
+
+def _errors(a, a_ref):
+    import oracle
+
+    es, rr, mr = oracle.force_errors(a, a_ref)
+    return {"e_sum": es, "rms_rel": rr, "max_rel": mr}
+
+
+def run_compare(args):
+    """The 1M sheet's step with each walk form (FP64 and FP32 at theta 0.5,
+    plain FP32 and learned at theta 0.8): particle-steps/s next to the force
+    error against the oracle's direct sum on 4096 seeded targets (all ghost
+    images).  One JSON line."""
+    import torch
+
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    P = I.sheet(L_SHEET, N_SHEET, SEED)
+    sel = np.random.default_rng(1).choice(P.n, 4096, replace=False)
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L_SHEET,) * 3, nghost=(1, 1, 0), boundary=2,
+                      integrator=1, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    t = time.perf_counter()
+    a_dir = oracle.direct_gravity(p, 0.0, P.x, P.y, P.z, P.m, targets=sel)
+    t_dir = time.perf_counter() - t
+    rows = {}
+    for name, walk, theta in [("fp64 theta=0.5", "fp64", 0.5), ("fp32 theta=0.5", "fp32", 0.5),
+                              ("fp32 theta=0.8", "fp32", 0.8), ("learned theta=0.8", "learned", 0.8)]:
+        cfg = sheet_config(rb, walk)
+        cfg["theta"] = theta
+        sim = make_sim(rb, cfg, stream.cuda_stream)
+        sim.set_particles(P)
+        a = sim.gravity()
+        err = _errors(a[sel], a_dir)
+        sim.set_particles(P)
+        ms, wms = _timed(sim, stream, args.steps, args.warmup)
+        rows[name] = {"particle_steps_per_s": N_SHEET / (ms / 1e3), "ms_per_step": ms,
+                      "walk_ms": wms, "force_error_vs_direct": err}
+        del sim
+    line = {"metric": "particle-steps/s and force error vs direct sum per walk form (1M sheet)",
+            "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "forms": rows,
+            "direct_sum": {"targets": 4096, "images": 9, "seconds": t_dir, "cores": oracle.nthreads()},
+            "data": "synthetic", "config": {"workload": workload_name("fp32")}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_plummer(args):
+    """Plummer sphere, N = 2^20 (G = M = a = 1, open, leap-frog, dt = 1e-3,
+    softening 1e-3): the FP32 and FP64 walks at theta 0.3 / 0.5 / 0.7,
+    particle-steps/s and force error against the oracle's direct sum on 4096
+    seeded targets.  One JSON line."""
+    import torch
+
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    n = 1 << 20
+    P = I.plummer(n, 3)
+    sel = np.random.default_rng(1).choice(P.n, 4096, replace=False)
+    p = oracle.Params(G=1.0, L=(128.0,) * 3, theta=0.5, soft=1e-3, dt=1e-3, gravity=1)
+    t = time.perf_counter()
+    a_dir = oracle.direct_gravity(p, 0.0, P.x, P.y, P.z, P.m, targets=sel)
+    t_dir = time.perf_counter() - t
+    rows = {}
+    for theta in (0.3, 0.5, 0.7):
+        for walk, mode in (("fp32", rb.RB_WALK_FP32), ("fp64", rb.RB_WALK_FP64)):
+            cfg = dict(G=1.0, box=(128.0,) * 3, boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG,
+                       theta=theta, softening=1e-3, dt=1e-3, gravity=1, collisions=0, walk=mode)
+            sim = rb.Sim(stream=stream.cuda_stream, **cfg)
+            sim.set_particles(P)
+            a = sim.gravity()
+            err = _errors(a[sel], a_dir)
+            sim.set_particles(P)
+            ms, wms = _timed(sim, stream, args.steps, args.warmup)
+            rows[f"{walk} theta={theta}"] = {"particle_steps_per_s": n / (ms / 1e3), "ms_per_step": ms,
+                                             "walk_ms": wms, "force_error_vs_direct": err}
+            del sim
+    line = {"metric": "particle-steps/s and force error vs direct sum, Plummer N=2^20", "unit": UNIT,
+            "steps": args.steps, "warmup": args.warmup, "forms": rows,
+            "direct_sum": {"targets": 4096, "seconds": t_dir, "cores": oracle.nthreads()},
+            "data": "synthetic (seeded Plummer sampler)",
+            "config": {"workload": "Plummer G=M=a=1, N=1,048,576, open box 128, leap-frog dt=1e-3, "
+                                   "softening 1e-3, quadrupole, no collisions"}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_sweep(args):
+    """Collision detectors on non-self-gravitating shearing sheets (the
+    paper's collision scaling test, Sect. 7): the plane sweep (Sect. 5.3) and
+    the tree search (Sect. 5.2) on an elongated box (azimuthal size 20 R,
+    optical depth 0.75) and on the square 1M sheet.  Whole collision-only
+    steps (drift, detection, pair sort, resolution), particle-steps/s, and the
+    detection's share.  One JSON line."""
+    import torch
+
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    rows = {}
+    n = args.particles
+    Ly = 20.0
+    Lx = I.long_sheet_size(n, Ly)
+    cases = [("elongated", Lx, Ly, lambda: I.sheet_xy(Lx, Ly, n, SEED)),
+             ("square", L_SHEET, L_SHEET, lambda: I.sheet(L_SHEET, N_SHEET, SEED))]
+    for name, lx, ly, make in cases:
+        if name not in args.cases.split(","):
+            continue
+        P = make()
+        for det, code in (("sweep", rb.RB_COLL_SWEEP), ("tree", rb.RB_COLL_TREE)):
+            cfg = dict(G=I.G_SI, omega=I.OMEGA, box=(lx, ly, lx), nghost=(1, 1, 0),
+                       boundary=rb.RB_BC_SHEAR, integrator=rb.RB_INT_SEI, eps=0.5, dt=I.DT_SHEET,
+                       gravity=0, collisions=code)
+            sim = rb.Sim(stream=stream.cuda_stream, **cfg)
+            sim.set_particles(P)
+            try:
+                rb.rb_autotune(sim.h)
+                rb.rb_set_profiling(sim.h, True)
+                sim.step(args.warmup)
+            except rb.RbError as e:
+                rows[f"{name} {det}"] = {"error": str(e)}
+                continue
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st_sum = {}
+            pairs = 0
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                sim.step(1)
+                st = sim.stats()
+                pairs += st["pairs_found"]
+                for k, v in st["ms_stage"].items():
+                    st_sum[k] = st_sum.get(k, 0.0) + v
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            det_ms = sum(st_sum.get(k, 0.0) for k in ("sort_gather_c", "tree_c", "collision_records",
+                                                      "collision_search")) / args.steps
+            rows[f"{name} {det}"] = {"particles": P.n, "box_m": [lx, ly], "particle_steps_per_s":
+                                     P.n / (ms / 1e3), "ms_per_step": ms, "detection_ms": det_ms,
+                                     "pairs_per_step": pairs / args.steps}
+            del sim
+    line = {"metric": "particle-steps/s of collision-only steps, plane sweep vs tree search",
+            "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "cases": rows,
+            "data": "synthetic (seeded shearing-sheet generator)",
+            "config": {"workload": f"no self-gravity, SEI, shear, eps=0.5; elongated box "
+                                   f"{Lx:.0f} x {Ly:g} m with N={n:,}; square box "
+                                   f"{L_SHEET:g} x {L_SHEET:g} m with N={N_SHEET:,}"}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -475,6 +657,13 @@ def main():
     ap.add_argument("--box", type=float, default=L_SHEET, help="sheet side in m (default 2050)")
     ap.add_argument("--ensemble", action="store_true",
                     help="measure the 256-box ensemble (batched vs looped) instead")
+    ap.add_argument("--compare", action="store_true",
+                    help="each walk form on the 1M sheet with its force error vs direct sum")
+    ap.add_argument("--plummer", action="store_true",
+                    help="FP32 and FP64 walks on the 2^20 Plummer sphere at theta 0.3/0.5/0.7")
+    ap.add_argument("--sweep", action="store_true",
+                    help="plane sweep vs tree search on collision-only elongated and square sheets")
+    ap.add_argument("--cases", default="elongated,square", help="--sweep cases to run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -483,6 +672,12 @@ def main():
         run_reference(args)
     elif args.ensemble:
         run_ensemble(args)
+    elif args.compare:
+        run_compare(args)
+    elif args.plummer:
+        run_plummer(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

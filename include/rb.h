@@ -5,8 +5,9 @@
  * Every step is the drift-kick-drift (DKD) scheme of Sect. 3: drift dt/2,
  * boundaries (Sect. 2.3), octree at the mid-step positions (Sect. 4.2),
  * Barnes-Hut self-gravity (Eq. 1, Sect. 4.2), kick dt, drift dt/2,
- * boundaries, then the tree collision search (Sect. 5.2, Eq. 3) and the
- * resolution of the collisions found (Sect. 5, Eq. 2).  All of it runs in the
+ * boundaries, then collision detection -- the tree search (Sect. 5.2, Eq. 3)
+ * or the plane sweep (Sect. 5.3) -- and the resolution of the collisions
+ * found (Sect. 5, Eq. 2).  All of it runs in the
  * library's CUDA kernels on one GPU; nothing falls back to the CPU.
  *
  * Conventions shared by every call:
@@ -19,7 +20,9 @@
  *    box; they are stable while particles move, and removed particles (open
  *    boundaries) leave gaps.  Per-particle outputs are in ascending id order.
  *  - Units are the caller's; G fixes them.  Positions are relative to the box
- *    centre: the root cube of a box of side L spans [-L/2, L/2) per axis.
+ *    centre: a box spans [-L_a/2, L_a/2) along axis a; its tree's root cube
+ *    has side L_x and contains it (L_y, L_z <= L_x, e.g. an elongated
+ *    shearing box of radial size L_x).
  */
 #ifndef RB_H
 #define RB_H
@@ -47,12 +50,18 @@ enum { RB_INT_LEAPFROG = 0, RB_INT_SEI = 1 };
 /* Precision of the gravity walk.  Positions, velocities, moments and the
  * kick/drift are FP64 in every mode. */
 enum { RB_WALK_FP64 = 0, RB_WALK_FP32 = 1, RB_WALK_FP32_LEARNED = 2 };
+/* Collision detectors: none; the tree search of Sect. 5.2 (particles that
+ * overlap at the end of the step, Eq. 3 pruning); the plane sweep along x of
+ * Sect. 5.3 (straight-line trajectories over the drift around the detection
+ * time, tau in [-dt/2, dt/2], that come closer than R_a + R_b). */
+enum { RB_COLL_NONE = 0, RB_COLL_TREE = 1, RB_COLL_SWEEP = 2 };
 
 typedef struct rb_config {
     double G;               /* gravitational constant of Eq. 1 */
     double omega;           /* epicyclic frequency Omega (SEI, shear offsets) */
     double omega_z;         /* vertical frequency Omega_z; <= 0 means = omega (Sect. 3.3) */
-    double box[3];          /* box side per axis; the root cube has side box[0] == box[1] == box[2] */
+    double box[3];          /* box side per axis (periodic lengths; open boxes remove particles
+                               outside them); box[1], box[2] <= box[0], the root cube's side */
     double theta;           /* critical opening angle (Sect. 4.2), > 0 */
     double eps_restitution; /* normal coefficient of restitution (Eq. 2), in [0, 1] */
     double softening;       /* gravitational softening b of Eq. 1, >= 0 */
@@ -65,7 +74,7 @@ typedef struct rb_config {
     int walk;               /* RB_WALK_* */
     int quadrupole;         /* 1: monopole + quadrupole cells (Sect. 4.2); 0: monopole */
     int gravity;            /* 1: tree self-gravity; 0: none */
-    int collisions;         /* 1: tree collision search + resolution; 0: none */
+    int collisions;         /* RB_COLL_*: detector whose pairs are resolved (Eq. 2) */
     int reserved[5];        /* must be zero */
 } rb_config;
 
@@ -99,12 +108,12 @@ typedef struct rb_sim rb_sim; /* opaque, owned by the library */
  * advanced together) that share `cfg`; box sizes default to cfg->box.
  * cuda_stream: a cudaStream_t (NULL: the library creates its own).  The
  * stream must outlive the simulation.  *out receives the handle.
- * Errors: RB_ERR_ARG (theta <= 0, dt <= 0, eps outside [0,1], a non-cubic
- * root box, nghost < 0 or > 7, SEI without omega, reserved != 0),
- * RB_ERR_CUDA. */
+ * Errors: RB_ERR_ARG (theta <= 0, dt <= 0, eps outside [0,1], a box side
+ * <= 0 or box[1] or box[2] above box[0], nghost < 0 or > 7, SEI without
+ * omega, an unknown detector, reserved != 0), RB_ERR_CUDA. */
 int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out);
 
-/* Set the side lengths of box `box` (host array of 3; cubic root box). */
+/* Set the side lengths of box `box` (host array of 3; L[1], L[2] <= L[0]). */
 int rb_set_box(rb_sim* sim, int box, const double L[3]);
 
 /* Copy n particles (host arrays: positions, velocities, masses, radii) into
@@ -157,7 +166,8 @@ int rb_get_counts(rb_sim* sim, int box, int64_t cap, int64_t* ncell, int64_t* nl
 int rb_get_tree(rb_sim* sim, int box, int64_t cap, int64_t* ncell, int32_t* depth,
                 int64_t* count, double* M, double* com, double* Q, int64_t member_cap,
                 int64_t* member_ids);
-/* Run the collision search (Sect. 5.2) on the current positions without
+/* Run the configured detector (tree search, Sect. 5.2, or plane sweep,
+ * Sect. 5.3, with the current velocities) on the current positions without
  * resolving; read the pairs with rb_get_pairs. */
 int rb_detect_collisions(rb_sim* sim);
 /* Collision pairs of the last search of box `box` in resolution order: ids

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "librb.so")
 BUILD = os.path.join(PKG, "_build")
 SOURCES = ["rb_sort.cu", "rb_tree.cu", "rb_walk.cu", "rb_step.cu", "rb_api.cu", "rb_noalloc.cu",
-           "rb_mlp.cu"]
+           "rb_mlp.cu", "rb_sweep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

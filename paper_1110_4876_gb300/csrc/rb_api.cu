@@ -67,6 +67,7 @@ struct rb_sim {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gafter[2] = {0, 0};
     std::vector<void*> allocs, pair_allocs;
+    Sweep SW{};   // plane-sweep items (collisions == RB_COLL_SWEEP)
     std::string err;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_stage[13] = {};
@@ -268,6 +269,17 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &s->d_boxes, s->nbox, L);
         rc |= dalloc(s, &s->e_part, 7 * kEnergyParts, L);
         rc |= dalloc(s, &s->e_out, 8, L);
+        s->SW = Sweep{};
+        if (s->cfg.collisions == RB_COLL_SWEEP) {
+            const int ic = cap * (1 + (s->cfg.boundary == RB_BC_OPEN ? 0 : s->cfg.nghost[0]));
+            rc |= dalloc(s, &s->SW.key, ic, L); rc |= dalloc(s, &s->SW.key_alt, ic, L);
+            rc |= dalloc(s, &s->SW.val, ic, L); rc |= dalloc(s, &s->SW.val_alt, ic, L);
+            rc |= dalloc(s, &s->SW.hist, radix_hist_words(ic), L);
+            double4_32a* recs = nullptr;   // 64-byte records: two double4 each
+            rc |= dalloc(s, &recs, 2 * (size_t)ic, L);
+            s->SW.rec = recs;
+            s->SW.cap = ic;
+        }
         if (rc) return RB_ERR_CUDA;
         s->ncap = cap;
         // a freshly drawn dense sheet overlaps about one pair per particle
@@ -324,6 +336,7 @@ int upload(rb_sim* s) {
     if (s->nbox > 1) {
         while ((1 << s->box_bits) <= s->nbox) s->box_bits++;
     }
+    s->SW.box_bits = s->box_bits;
     make_constants(s);
     if (box_params(s) != RB_OK) return RB_ERR_CUDA;
     s->dirty = false;
@@ -403,7 +416,16 @@ int record_step(rb_sim* s, int p) {
         for (int k = 1; k <= 5; k++) mark(s, k);
     }
     mark(s, 6);
-    if (s->cfg.collisions) {
+    if (s->cfg.collisions == RB_COLL_SWEEP) {
+        // plane sweep on the particles where they are: no collision tree
+        discard_live_count(s->ctl, st);
+        for (int k = 7; k <= 9; k++) mark(s, k);
+        sweep_search(s->P[c], s->ctl, s->d_boxes, s->C, s->SW, s->PR, 2, s->ncap, st);
+        mark(s, 10);
+        sort_pairs(s->PR, s->ctl, st);
+        mark(s, 11);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, st);
+    } else if (s->cfg.collisions) {
         sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, st);
         c = 1 - c;
         mark(s, 7);
@@ -417,6 +439,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 11);
         resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, st);
     } else {
+        discard_live_count(s->ctl, st);   // no sort follows the last drift
         for (int k = 7; k <= 11; k++) mark(s, k);
     }
     mark(s, 12);
@@ -471,10 +494,16 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve) {
     for (int attempt = 0; attempt < 2; attempt++) {
         RB_CUDA(s, cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream));
         if (clear_err(s)) return RB_ERR_CUDA;
-        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
-                         s->search_block);
+        if (s->cfg.collisions == RB_COLL_SWEEP)
+            sweep_search(s->P[c], s->ctl, s->d_boxes, s->C, s->SW, s->PR, hs, s->ncap, s->stream);
+        else
+            collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
+                             s->search_block);
         sort_pairs(s->PR, s->ctl, s->stream);
         if (read_ctl(s)) return RB_ERR_CUDA;
+        if (s->hctl.err & kErrSweepLong)
+            return fail(s, RB_ERR_CAPACITY, "plane sweep: a trajectory overlaps more than 65536 others in x "
+                                            "(use the tree detector)");
         if (s->hctl.pair_count <= s->PR.cap) {
             if (resolve) {
                 resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, kResolveRounds, s->stream);
@@ -565,8 +594,9 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
     if (!(c.eps_restitution >= 0.0 && c.eps_restitution <= 1.0))
         return fail(nullptr, RB_ERR_ARG, "eps_restitution must be in [0, 1]");
     if (!(c.softening >= 0.0)) return fail(nullptr, RB_ERR_ARG, "softening must be >= 0");
-    if (!(c.box[0] > 0.0) || c.box[0] != c.box[1] || c.box[0] != c.box[2])
-        return fail(nullptr, RB_ERR_ARG, "the root box must be a cube with box[0] == box[1] == box[2] > 0");
+    if (!(c.box[0] > 0.0 && c.box[1] > 0.0 && c.box[2] > 0.0) || c.box[1] > c.box[0] || c.box[2] > c.box[0])
+        return fail(nullptr, RB_ERR_ARG, "box sides must be > 0 with box[1], box[2] <= box[0] (the root cube)");
+    if (c.collisions < 0 || c.collisions > 2) return fail(nullptr, RB_ERR_ARG, "unknown collision detector");
     for (int a = 0; a < 3; a++)
         if (c.nghost[a] < 0 || c.nghost[a] > 7) return fail(nullptr, RB_ERR_ARG, "nghost must be in [0, 7]");
     if (c.boundary < 0 || c.boundary > 2) return fail(nullptr, RB_ERR_ARG, "unknown boundary");
@@ -603,7 +633,8 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
 
 int rb_set_box(rb_sim* s, int box, const double L[3]) {
     if (bad_box(s, box) || !L) return fail(s, RB_ERR_ARG, "bad box or null L");
-    if (!(L[0] > 0.0) || L[0] != L[1] || L[0] != L[2]) return fail(s, RB_ERR_ARG, "the root box must be a cube");
+    if (!(L[0] > 0.0 && L[1] > 0.0 && L[2] > 0.0) || L[1] > L[0] || L[2] > L[0])
+        return fail(s, RB_ERR_ARG, "box sides must be > 0 with L[1], L[2] <= L[0] (the root cube)");
     for (int a = 0; a < 3; a++) s->hb[box].L[a] = L[a];
     s->dirty = true;
     return RB_OK;
@@ -650,8 +681,13 @@ int rb_step(rb_sim* s, int64_t nsteps) {
             for (int q = 0; q < 12; q++)
                 cudaEventElapsedTime(&s->stage_ms[q], s->ev_stage[q], s->ev_stage[q + 1]);
         s->cur = s->gafter[p];
-        s->acc_set = s->cfg.gravity ? (s->cfg.collisions ? 1 - s->cur : s->cur) : -1;
-        if (s->hctl.err & kErrNonFinite) return fail(s, RB_ERR_NONFINITE, "a position became non-finite");
+        s->acc_set = s->cfg.gravity ? (s->cfg.collisions == RB_COLL_TREE ? 1 - s->cur : s->cur) : -1;
+        if (s->hctl.err & kErrNonFinite)
+            return fail(s, RB_ERR_NONFINITE, "a position became non-finite (or left the box by more than "
+                                             "4096 box lengths in one drift half)");
+        if (s->hctl.err & kErrSweepLong)
+            return fail(s, RB_ERR_CAPACITY, "plane sweep: a trajectory overlaps more than 65536 others in x "
+                                            "(use the tree detector)");
         if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
             // the step ended before resolution: search again with a larger buffer
             if ((rc = collide_with_retry(s, s->cur, 0, true))) return rc;
@@ -772,7 +808,8 @@ int rb_detect_collisions(rb_sim* s) {
     if (rc) return rc;
     if (s->ntot == 0) return RB_OK;
     rebuild_now(s);
-    build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+    if (s->cfg.collisions != RB_COLL_SWEEP)
+        build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
     return collide_with_retry(s, s->cur, 0, false);
 }
 
@@ -954,7 +991,7 @@ int rb_autotune(rb_sim* s, int use_cache) {
         }
         s->acc_set = -1;   // the tuning walks left no consistent acceleration record
     }
-    if (s->cfg.collisions) {
+    if (s->cfg.collisions == RB_COLL_TREE) {
         rebuild_now(s);
         build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
         float best = 1e30f;

@@ -65,11 +65,14 @@ struct Ctl {
     int resolved;              // pairs that were approaching and were resolved
     int err;                   // error bits (kErr*)
     int req_count;             // learned-correction requests recorded by the last walk
-    int pad_;
+    int sweep_items;           // plane sweep: trajectory extents of the last search
     unsigned long long n_cell, n_leaf, n_mac, n_recheck;
+    unsigned long long sweep_wbits;   // plane sweep: largest half extent (double bits)
 };
 constexpr int kErrNonFinite = 1;
 constexpr int kErrPairOverflow = 2;
+constexpr int kErrSweepLong = 4;    // a plane-sweep item met more than kMaxSweepScan extents
+constexpr int kMaxSweepScan = 1 << 16;
 
 // Tree and scratch buffers of one build (sized for capacity n).
 struct Tree {
@@ -107,6 +110,15 @@ struct Pairs {
     int32_t* slot_of_id;       // global id -> slot in the current set
     uint32_t *hist, *ehist;
     int cap;
+};
+
+// Plane-sweep items (trajectory x extents, Sect. 5.3) and their sort buffers.
+struct Sweep {
+    uint64_t *key, *key_alt;   // (box << 32) | quantised lower end
+    uint32_t *val, *val_alt;   // (particle slot << 3) | copy
+    uint32_t* hist;
+    void* rec;                 // per sorted item: the particle's state (64 B)
+    int cap, box_bits;         // cap = particles x (1 + nghost_x)
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -199,6 +211,11 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                       const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128);
 
+// rb_sweep.cu: plane-sweep search on set P at half-step offset hs; the
+// canonical pair keys are appended to PR like the tree search's.
+void sweep_search(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Sweep& S,
+                  const Pairs& PR, int half_step_offset, int ncap, cudaStream_t s);
+
 // rb_step.cu
 void drift_keys(const PSet& P, const Tree& T, Ctl* ctl, const BoxP* boxes, const SimC& C,
                 int ncap, int ndrift, int half_step_offset, const double* ax, const double* ay,
@@ -211,6 +228,9 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s);
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
                   double* partials, int nparts, double* out7, cudaStream_t s);
 void step_advance(Ctl* ctl, cudaStream_t s);
+// The live count the keys kernel accumulated, dropped when no sort follows
+// (the particles keep their slots; removed ones stay flagged).
+void discard_live_count(Ctl* ctl, cudaStream_t s);
 
 // rb_api.cu: message returned by rb_last_error(NULL) on this thread.
 void set_global_error(const std::string& msg);

@@ -58,10 +58,14 @@ __device__ __forceinline__ void drift_one(const SimC& C, double& x, double& y, d
     vz = __dadd_rn(__dmul_rn(C.awz, z0), __dmul_rn(C.aww, w0));
 }
 
+// Wraps in y (and z) repeat the oracle's one-box-length steps; a particle
+// that would need more than this many is reported as a runaway.
+constexpr int kMaxWraps = 1 << 12;
+
 // Boundaries after a drift half; returns false if the particle left an open
-// boundary.
+// boundary.  *runaway is set when the wraps did not bring it back.
 __device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, double t, double& x,
-                                         double& y, double& z, double& vy) {
+                                         double& y, double& z, double& vy, bool* runaway) {
     const double hx = 0.5 * bp.Lx, hy = 0.5 * bp.Ly, hz = 0.5 * bp.Lz;
     if (C.boundary == 0)
         return !(x < -hx || x >= hx || y < -hy || y >= hy || z < -hz || z >= hz);
@@ -76,11 +80,13 @@ __device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, double t
         y = __dsub_rn(y, s);
         vy = __dsub_rn(vy, vs);
     }
-    for (int k = 0; k < 8 && y >= hy; k++) y = __dsub_rn(y, bp.Ly);
-    for (int k = 0; k < 8 && y < -hy; k++) y = __dadd_rn(y, bp.Ly);
+    for (int k = 0; k < kMaxWraps && y >= hy; k++) y = __dsub_rn(y, bp.Ly);
+    for (int k = 0; k < kMaxWraps && y < -hy; k++) y = __dadd_rn(y, bp.Ly);
+    if (y >= hy || y < -hy) *runaway = true;
     if (C.z_periodic) {
-        for (int k = 0; k < 8 && z >= hz; k++) z = __dsub_rn(z, bp.Lz);
-        for (int k = 0; k < 8 && z < -hz; k++) z = __dadd_rn(z, bp.Lz);
+        for (int k = 0; k < kMaxWraps && z >= hz; k++) z = __dsub_rn(z, bp.Lz);
+        for (int k = 0; k < kMaxWraps && z < -hz; k++) z = __dadd_rn(z, bp.Lz);
+        if (z >= hz || z < -hz) *runaway = true;
         return true;
     }
     return !(z < -hz || z >= hz);
@@ -115,11 +121,12 @@ __global__ void __launch_bounds__(256) k_drift_keys(DriftArgs A, SimC C) {
             vy = __dadd_rn(vy, __dmul_rn(A.ay[i], C.dt));
             vz = __dadd_rn(vz, __dmul_rn(A.az[i], C.dt));
         }
+        bool runaway = false;
         for (int d = 0; d < A.ndrift && live; d++) {
             drift_one(C, x, y, z, vx, vy, vz);
-            live = wrap_one(C, bp, time_at(A.ctl, C, A.hs + d), x, y, z, vy);
+            live = wrap_one(C, bp, time_at(A.ctl, C, A.hs + d), x, y, z, vy, &runaway);
         }
-        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+        if (runaway || !(isfinite(x) && isfinite(y) && isfinite(z))) {
             atomicOr(&A.ctl->err, kErrNonFinite);
             live = false;
         }
@@ -157,6 +164,8 @@ __global__ void k_commit_live(Ctl* ctl) {
     ctl->n_live = ctl->n_live_next;
     ctl->n_live_next = 0;
 }
+
+__global__ void k_discard_live(Ctl* ctl) { ctl->n_live_next = 0; }
 
 // An overflowing search resolves nothing: the host grows the buffer and runs
 // the search again on the unchanged state.
@@ -429,6 +438,8 @@ void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl*
     k_permute<<<ceil_div(ncap, 256), 256, 0, s>>>(src, dst, T.idx, PR.slot_of_id, ctl, ncap);
     k_commit_live<<<1, 1, 0, s>>>(ctl);
 }
+
+void discard_live_count(Ctl* ctl, cudaStream_t s) { k_discard_live<<<1, 1, 0, s>>>(ctl); }
 
 void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s) {
     k_pairs_prep<<<1, 1, 0, s>>>(ctl, PR.cap);

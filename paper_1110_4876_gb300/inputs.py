@@ -11,6 +11,9 @@ the paper's scaling runs, Sect. 7):
                    over the L x L box, z ~ N(0, 1 m); velocities are the shear
                    flow (0, -1.5 Omega x, 0) plus isotropic Gaussian dispersion
                    sigma = 2 Omega * 1 m.
+  * sheet_xy(Lx, Ly, N): the same in an Lx x Ly box; long_sheet_size(N)
+                   gives the radial size of an elongated box of azimuthal size
+                   20 m at optical depth 0.75 (the plane-sweep workload).
   * plummer(N):    Plummer sphere, G = M = a = 1, positions by inversion of
                    the cumulative mass, speeds by von Neumann rejection on
                    q^2 (1 - q^2)^(7/2); centre-of-mass frame.
@@ -70,9 +73,22 @@ def _rng(seed: int) -> np.random.Generator:
 def sheet(L: float, N: int, seed: int, omega: float = OMEGA, sigma: float = SIGMA,
           radius: float = RADIUS, density: float = DENSITY) -> Particles:
     """Shearing-sheet initial state in the box [-L/2, L/2)^2 (x, y)."""
+    return sheet_xy(L, L, N, seed, omega, sigma, radius, density)
+
+
+def long_sheet_size(N: int, Ly: float = 20.0, tau: float = 0.75, radius: float = RADIUS) -> float:
+    """Radial size L_x of an elongated sheet of azimuthal size Ly holding N
+    particles at optical depth tau = N pi R^2 / (L_x L_y)."""
+    return N * math.pi * radius ** 2 / (tau * Ly)
+
+
+def sheet_xy(Lx: float, Ly: float, N: int, seed: int, omega: float = OMEGA, sigma: float = SIGMA,
+             radius: float = RADIUS, density: float = DENSITY) -> Particles:
+    """Shearing-sheet initial state in [-Lx/2, Lx/2) x [-Ly/2, Ly/2) (the
+    elongated boxes of the paper's collision scaling test use Ly = 20 R)."""
     g = _rng(seed)
-    x = g.uniform(-0.5 * L, 0.5 * L, N)
-    y = g.uniform(-0.5 * L, 0.5 * L, N)
+    x = g.uniform(-0.5 * Lx, 0.5 * Lx, N)
+    y = g.uniform(-0.5 * Ly, 0.5 * Ly, N)
     z = g.normal(0.0, 1.0, N)
     vx = g.normal(0.0, sigma, N)
     vy = -1.5 * omega * x + g.normal(0.0, sigma, N)

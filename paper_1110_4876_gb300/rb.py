@@ -19,6 +19,7 @@ RB_OK, RB_ERR_ARG, RB_ERR_CAPACITY, RB_ERR_TIMEOUT, RB_ERR_NONFINITE, RB_ERR_CUD
 RB_BC_OPEN, RB_BC_PERIODIC, RB_BC_SHEAR = 0, 1, 2
 RB_INT_LEAPFROG, RB_INT_SEI = 0, 1
 RB_WALK_FP64, RB_WALK_FP32, RB_WALK_FP32_LEARNED = 0, 1, 2
+RB_COLL_NONE, RB_COLL_TREE, RB_COLL_SWEEP = 0, 1, 2
 
 EXPORTS = [
     "rb_create", "rb_set_box", "rb_set_particles", "rb_step", "rb_get_particles", "rb_energy",
