@@ -188,12 +188,16 @@ int rb_stats(rb_sim* sim, rb_stats_t* out);
 /* on = 1: record CUDA events between the stages of every step (event nodes
  * inside the step graph) so rb_stats reports per-stage device times. */
 int rb_set_profiling(rb_sim* sim, int on);
-/* Time the gravity walk and the collision search at 64, 128 and 256 threads
- * per block on the current positions (best of 3 after a warm-up each) and
- * keep the fastest; results are cached per (particle-count bucket, theta,
+/* Time the gravity walk and the tree collision search at 64, 128 and 256
+ * threads per block on the current positions (best of 3 after a warm-up each)
+ * and keep the fastest; results are cached per (particle-count bucket, theta,
  * walk mode, batched) for the process, and use_cache = 1 takes a cached
  * choice without timing.  Positions and velocities are not changed. */
 int rb_autotune(rb_sim* sim, int use_cache);
+/* Set the launch shapes directly: walk_block and search_block 64, 128 or 256
+ * threads per block.  Results do not depend on them (each lane runs its own
+ * walk).  Errors: RB_ERR_ARG for any other value. */
+int rb_set_launch_shape(rb_sim* sim, int walk_block, int search_block);
 /* Destroy the simulation and free its device memory. */
 void rb_destroy(rb_sim* sim);
 

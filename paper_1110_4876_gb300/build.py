@@ -23,6 +23,9 @@ BUILD = os.path.join(PKG, "_build")
 SOURCES = ["rb_sort.cu", "rb_tree.cu", "rb_walk.cu", "rb_step.cu", "rb_api.cu", "rb_noalloc.cu",
            "rb_mlp.cu", "rb_sweep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The FP32 walks spell out every fused multiply-add, so that all their
+# variants (block sizes, prefetching, learned) round identically.
+PER_FILE = {"rb_walk.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -40,7 +43,8 @@ def _flags(extra=()):
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "rb_internal.cuh"), os.path.join(INCLUDE, "rb.h"), __file__]
+    deps = [src, os.path.join(INCLUDE, "rb.h"), __file__]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps)
 
 
@@ -52,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         if force or _stale(o, s):
-            extra = ["-Xptxas", "-v"] if ptxas_info else []
+            extra = (["-Xptxas", "-v"] if ptxas_info else []) + PER_FILE.get(src, [])
             jobs.append([nv, *_flags(extra), "-c", s, "-o", o])
 
     def run(cmd):

@@ -1017,6 +1017,18 @@ int rb_autotune(rb_sim* s, int use_cache) {
     return RB_OK;
 }
 
+int rb_set_launch_shape(rb_sim* s, int walk_block, int search_block) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    const bool ok = (walk_block == 64 || walk_block == 128 || walk_block == 256) &&
+                    (search_block == 64 || search_block == 128 || search_block == 256);
+    if (!ok) return fail(s, RB_ERR_ARG, "launch shapes: 64, 128 or 256 threads per block");
+    s->walk_block = walk_block;
+    s->search_block = search_block;
+    s->tuned = true;
+    drop_graphs(s);
+    return RB_OK;
+}
+
 int rb_set_profiling(rb_sim* s, int on) {
     if (!s) return fail(s, RB_ERR_ARG, "null sim");
     if ((on != 0) != s->profiling) {

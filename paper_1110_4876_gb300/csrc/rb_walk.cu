@@ -50,6 +50,7 @@ struct GravArgs {
     // learned walk: cell particle counts (an input of the network) and weights
     const int32_t* e_count;
     const mlp::Packed* wpk;
+    int ecap;   // entry capacity (every entry index below it is readable)
 };
 
 __device__ __forceinline__ double4_32a ld_d4(const double4_32a* p) { return *p; }
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool mac64(const double4_32a& a, double theta2, doubl
 // y' = y (3/2 - x y^2 / 2), which roughly halves its relative error.
 __device__ __forceinline__ float rsqrt_nr(float x) {
     const float y = rsqrtf(x);
-    return y * fmaf(-0.5f * x * y, y, 1.5f);
+    return y * fmaf((-0.5f * x) * y, y, 1.5f);
 }
 
 // Compensated (Kahan) accumulation: in a sheet the net force is often a
@@ -148,7 +149,10 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
     const int self_leaf = A.leaf_of[ii];
     // the FP64 target point of the current image: read only by the rare FP64
     // re-decisions, so it lives in shared memory rather than in registers
-    __shared__ double tgt[3][kMaxWalkBlock];
+    // (dynamic shared memory, 3 x 8 bytes per thread of the launch)
+    extern __shared__ __align__(16) unsigned char wsm[];
+    double* tgt = reinterpret_cast<double*>(wsm);   // [3][blockDim.x]
+    const int tid = threadIdx.x, nb = blockDim.x;
     double pot = 0.0;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // sums + compensation
     int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0, ncorr = 0;
@@ -164,9 +168,9 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                     image_offset(bp, s, gx, gy, gz, ox, oy, oz);
                     const double tx = __dsub_rn(A.x[ii], ox), ty = __dsub_rn(A.y[ii], oy),
                                  tz = __dsub_rn(A.z[ii], oz);
-                    tgt[0][threadIdx.x] = tx;
-                    tgt[1][threadIdx.x] = ty;
-                    tgt[2][threadIdx.x] = tz;
+                    tgt[tid] = tx;
+                    tgt[nb + tid] = ty;
+                    tgt[2 * nb + tid] = tz;
                     thx = __double2float_rn(tx); thy = __double2float_rn(ty); thz = __double2float_rn(tz);
                     tlx = __double2float_rn(tx - (double)thx);
                     tly = __double2float_rn(ty - (double)thy);
@@ -196,7 +200,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                     const float dx = (ra.x - thx) + (rb.x - tlx);
                     const float dy = (ra.y - thy) + (rb.y - tly);
                     const float dz = (ra.z - thz) + (rb.z - tlz);
-                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (__float_as_int(ra.w) < 0) {
                         // particle leaf: exact term of Eq. 1
                         if (act) {
@@ -204,22 +208,20 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                                 const float m = -ra.w;
                                 const float inv = rsqrt_nr(kSoft ? r2 + A.soft2f : r2);
                                 const float f = m * (inv * inv * inv);
-                                fx += f * dx;
-                                fy += f * dy;
-                                fz += f * dz;
-                                if (kPot) fp -= m * inv;
+                                fx = fmaf(f, dx, fx);
+                                fy = fmaf(f, dy, fy);
+                                fz = fmaf(f, dz, fz);
+                                if (kPot) fp = fmaf(-m, inv, fp);
                                 nleaf++;
                             }
                             next = e + 1;
                         }
                     } else if (act) {
-                        const float4 q0 = __ldg(&A.rq0[e]);
-                        const float4 q1 = __ldg(&A.rq1[e]);
                         nmac++;
                         bool acc = ra.w < r2;
                         if (fabsf(ra.w - r2) <= 1e-5f * r2) {
-                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, tgt[0][threadIdx.x],
-                                        tgt[1][threadIdx.x], tgt[2][threadIdx.x]);
+                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, tgt[tid], tgt[nb + tid],
+                                        tgt[2 * nb + tid]);
                             nrecheck++;
                         }
                         if (kInside && acc) {
@@ -231,31 +233,33 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                             const float w = ch.w, tol = 1e-5f * ch.w;
                             const float mx = fminf(fminf(ux, w - ux), fminf(fminf(uy, w - uy), fminf(uz, w - uz)));
                             if (fabsf(mx) <= tol) {
-                                acc = !inside64(ld_d4(&A.d_c[e]), tgt[0][threadIdx.x],
-                                                tgt[1][threadIdx.x], tgt[2][threadIdx.x]);
+                                acc = !inside64(ld_d4(&A.d_c[e]), tgt[tid], tgt[nb + tid],
+                                                tgt[2 * nb + tid]);
                                 nrecheck++;
                             } else if (mx > 0.f) {
                                 acc = false;
                             }
                         }
                         if (acc) {
+                            const float4 q0 = __ldg(&A.rq0[e]);
+                            const float4 q1 = __ldg(&A.rq1[e]);
                             const float inv = rsqrt_nr(r2);
                             const float inv2 = inv * inv;
                             const float invs = kSoft ? rsqrt_nr(r2 + A.soft2f) : inv;
                             const float f = q0.x * (invs * invs * invs);
                             float tx_ = f * dx, ty_ = f * dy, tz_ = f * dz;
-                            if (kPot) fp -= q0.x * invs;
+                            if (kPot) fp = fmaf(-q0.x, invs, fp);
                             if (kQuad) {
-                                const float qx = q0.y * dx + q1.x * dy + q1.y * dz;
-                                const float qy = q1.x * dx + q0.z * dy + q1.z * dz;
-                                const float qz = q1.y * dx + q1.z * dy + q0.w * dz;
-                                const float dqd = dx * qx + dy * qy + dz * qz;
+                                const float qx = fmaf(q1.y, dz, fmaf(q1.x, dy, q0.y * dx));
+                                const float qy = fmaf(q1.z, dz, fmaf(q0.z, dy, q1.x * dx));
+                                const float qz = fmaf(q0.w, dz, fmaf(q1.z, dy, q1.y * dx));
+                                const float dqd = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
                                 const float inv5 = inv2 * inv2 * inv;
                                 const float c = 2.5f * dqd * (inv5 * inv2);
-                                tx_ += c * dx - inv5 * qx;
-                                ty_ += c * dy - inv5 * qy;
-                                tz_ += c * dz - inv5 * qz;
-                                if (kPot) fp -= 0.5f * dqd * inv5;
+                                tx_ = fmaf(c, dx, fmaf(-inv5, qx, tx_));
+                                ty_ = fmaf(c, dy, fmaf(-inv5, qy, ty_));
+                                tz_ = fmaf(c, dz, fmaf(-inv5, qz, tz_));
+                                if (kPot) fp = fmaf(-0.5f * dqd, inv5, fp);
                             }
                             fx += tx_;
                             fy += ty_;
@@ -457,13 +461,13 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
                         if (act) {
                             if (e != self) {
                                 const double dx = a.x - tx, dy = a.y - ty, dz = a.z - tz;
-                                const double r2 = dx * dx + dy * dy + dz * dz + soft2;
+                                const double r2 = fma(dz, dz, fma(dy, dy, dx * dx)) + soft2;
                                 const double inv = rsqrt(r2);
                                 const double f = -a.w * (inv * inv * inv);
-                                ax += f * dx;
-                                ay += f * dy;
-                                az += f * dz;
-                                if (kPot) pot += a.w * inv;
+                                ax = fma(f, dx, ax);
+                                ay = fma(f, dy, ay);
+                                az = fma(f, dz, az);
+                                if (kPot) pot = fma(a.w, inv, pot);
                                 nleaf++;
                             }
                             next = e + 1;
@@ -475,27 +479,27 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
                         if (acc) {
                             const double4_32a q0 = ld_d4(&A.d_q0[e]);
                             const double dx = a.x - tx, dy = a.y - ty, dz = a.z - tz;
-                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
                             const double invs = rsqrt(r2 + soft2);
                             const double f = q0.x * (invs * invs * invs);
-                            ax += f * dx;
-                            ay += f * dy;
-                            az += f * dz;
-                            if (kPot) pot -= q0.x * invs;
+                            ax = fma(f, dx, ax);
+                            ay = fma(f, dy, ay);
+                            az = fma(f, dz, az);
+                            if (kPot) pot = fma(-q0.x, invs, pot);
                             if (kQuad) {
                                 const double4_32a q1 = ld_d4(&A.d_q1[e]);
                                 const double inv = rsqrt(r2);
                                 const double inv2 = inv * inv;
-                                const double qx = q0.y * dx + q1.x * dy + q1.y * dz;
-                                const double qy = q1.x * dx + q0.z * dy + q1.z * dz;
-                                const double qz = q1.y * dx + q1.z * dy + q0.w * dz;
-                                const double dqd = dx * qx + dy * qy + dz * qz;
+                                const double qx = fma(q1.y, dz, fma(q1.x, dy, q0.y * dx));
+                                const double qy = fma(q1.z, dz, fma(q0.z, dy, q1.x * dx));
+                                const double qz = fma(q0.w, dz, fma(q1.z, dy, q1.y * dx));
+                                const double dqd = fma(dz, qz, fma(dy, qy, dx * qx));
                                 const double inv5 = inv2 * inv2 * inv;
                                 const double c = 2.5 * dqd * (inv5 * inv2);
-                                ax += c * dx - inv5 * qx;
-                                ay += c * dy - inv5 * qy;
-                                az += c * dz - inv5 * qz;
-                                if (kPot) pot -= 0.5 * dqd * inv5;
+                                ax = fma(c, dx, fma(-inv5, qx, ax));
+                                ay = fma(c, dy, fma(-inv5, qy, ay));
+                                az = fma(c, dz, fma(-inv5, qz, az));
+                                if (kPot) pot = fma(-0.5 * dqd, inv5, pot);
                             }
                             ncell++;
                             next = A.e_skip[e];
@@ -611,7 +615,7 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
                                 const float dx = (ra.x - thx) + (rb.x - tlx);
                                 const float dy = (ra.y - thy) + (rb.y - tly);
                                 const float dz = (ra.z - thz) + (rb.z - tlz);
-                                const float d2 = dx * dx + dy * dy + dz * dz;
+                                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                                 const float sr = prf + rb.w;
                                 if (d2 < sr * sr * 1.0001f) {
                                     const int jid = A.id[j];
@@ -640,7 +644,7 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
                         const float dx = (ra.x - thx) + (rb.x - tlx);
                         const float dy = (ra.y - thy) + (rb.y - tly);
                         const float dz = (ra.z - thz) + (rb.z - tlz);
-                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                         const float lim = (prf + ra.w) * 1.00002f;
                         next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
                     }
@@ -669,6 +673,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     block = (block == 64 || block == 256) ? block : 128;
     if (T.cap_n <= 0) return;
     GravArgs A;
+    A.ecap = T.cap_e;
     A.e_count = T.e_count;
     A.wpk = learn ? learn->w : nullptr;
     A.req = nullptr; A.req_count = nullptr; A.req_cap = 0;
@@ -696,26 +701,28 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     const bool quad = C.quadrupole != 0;
     const bool soft = C.soft2 > 0.0;
     const int grid = ceil_div(T.cap_n, block);
-#define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, 0, s>>>(A)
+    // dynamic shared memory: the FP64 target point of each thread
+    const size_t sm_tgt = (size_t)block * 3 * sizeof(double);
+#define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, sm_tgt, s>>>(A)
 #define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, block, 0, s>>>(A)
     if (learn && !potential) {
         // FP32 walk with the learned correction of band cells (quadrupole on)
         A.band_scale = learn->band_scale;
         if (inside) {
-            if (soft) k_walk32_learn<true, true><<<grid, block, 0, s>>>(A);
-            else k_walk32_learn<true, false><<<grid, block, 0, s>>>(A);
+            if (soft) k_walk32_learn<true, true><<<grid, block, sm_tgt, s>>>(A);
+            else k_walk32_learn<true, false><<<grid, block, sm_tgt, s>>>(A);
         } else {
-            if (soft) k_walk32_learn<false, true><<<grid, block, 0, s>>>(A);
-            else k_walk32_learn<false, false><<<grid, block, 0, s>>>(A);
+            if (soft) k_walk32_learn<false, true><<<grid, block, sm_tgt, s>>>(A);
+            else k_walk32_learn<false, false><<<grid, block, sm_tgt, s>>>(A);
         }
     } else if (rec) {
         // FP32 walk that also records accepted band cells (quadrupole on)
         if (inside) {
-            if (soft) k_walk32<true, true, false, true, true><<<grid, block, 0, s>>>(A);
-            else k_walk32<true, true, false, false, true><<<grid, block, 0, s>>>(A);
+            if (soft) k_walk32<true, true, false, true, true><<<grid, block, sm_tgt, s>>>(A);
+            else k_walk32<true, true, false, false, true><<<grid, block, sm_tgt, s>>>(A);
         } else {
-            if (soft) k_walk32<true, false, false, true, true><<<grid, block, 0, s>>>(A);
-            else k_walk32<true, false, false, false, true><<<grid, block, 0, s>>>(A);
+            if (soft) k_walk32<true, false, false, true, true><<<grid, block, sm_tgt, s>>>(A);
+            else k_walk32<true, false, false, false, true><<<grid, block, sm_tgt, s>>>(A);
         }
     } else if (walk_mode == 0 || potential) {
         if (quad) {

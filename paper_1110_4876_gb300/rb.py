@@ -27,7 +27,7 @@ EXPORTS = [
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
     "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_autotune",
-    "rb_set_pair_capacity",
+    "rb_set_pair_capacity", "rb_set_launch_shape",
 ]
 RB_MLP_PARAMS = 9347
 
@@ -100,6 +100,7 @@ def load():
     lib.rb_stats.argtypes = [_P, C.POINTER(rb_stats_t)]
     lib.rb_set_profiling.argtypes = [_P, i32]
     lib.rb_autotune.argtypes = [_P, i32]
+    lib.rb_set_launch_shape.argtypes = [_P, i32, i32]
     lib.rb_set_pair_capacity.argtypes = [_P, i64]
     lib.rb_load_mlp.argtypes = [_P, _VP, i64, C.c_double]
     lib.rb_mlp_samples.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_uint64, i64,
@@ -294,6 +295,11 @@ def rb_autotune(sim, use_cache: bool = True):
     _check(load().rb_autotune(sim, 1 if use_cache else 0), sim)
     st = rb_stats(sim)
     return int(st["walk_block"]), int(st["search_block"])
+
+
+def rb_set_launch_shape(sim, walk_block: int, search_block: int):
+    """Threads per block of the walk and of the collision search (64, 128, 256)."""
+    _check(load().rb_set_launch_shape(sim, int(walk_block), int(search_block)), sim)
 
 
 def rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z, out,
