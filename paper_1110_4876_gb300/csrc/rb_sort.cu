@@ -13,8 +13,8 @@ namespace rb {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;   // 4096 keys per block
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;   // 2048 keys per block
 constexpr int kBins = 256;
 constexpr int kScanThreads = 1024;
 
@@ -35,13 +35,20 @@ __global__ void __launch_bounds__(kThreads) k_rs_up(const uint64_t* __restrict__
     __syncthreads();
     const int n = read_n(d_n, ncap);
     const int base = blockIdx.x * kTile;
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
 #pragma unroll 4
     for (int r = 0; r < kItems; r++) {
-        int i = base + r * kThreads + threadIdx.x;
-        if (i < n) {
-            uint32_t d = kBoxDigit ? (uint32_t)(box[val[i]] >> shift) & 255u
-                                   : (uint32_t)(key[i] >> shift) & 255u;
-            atomicAdd(&h[d], 1u);
+        const int i = base + r * kThreads + threadIdx.x;
+        const bool ok = i < n;
+        uint32_t d = 0;
+        if (ok)
+            d = kBoxDigit ? (uint32_t)(box[val[i]] >> shift) & 255u : (uint32_t)(key[i] >> shift) & 255u;
+        // one shared atomic per distinct digit of the warp (nearly sorted
+        // keys share their high digits)
+        const unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const unsigned peers = __match_any_sync(act, d);
+            if ((peers & lt) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
         }
     }
     __syncthreads();
@@ -116,6 +123,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_block(T* __restrict__ a, 
     if (sum && threadIdx.x == kScanThreads - 1) *sum = run;
 }
 
+// Stable scatter of one tile: ranks within the tile (warp match-any votes),
+// a local sort of the tile by digit in shared memory, then writes in local
+// order, so that consecutive threads store consecutive addresses of a digit.
 template <bool kBoxDigit>
 __global__ void __launch_bounds__(kThreads) k_rs_down(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
@@ -127,11 +137,15 @@ __global__ void __launch_bounds__(kThreads) k_rs_down(const uint64_t* __restrict
                                                       const uint32_t* __restrict__ dtot,
                                                       int nblocks) {
     __shared__ uint32_t wcnt[kThreads / 32][kBins];
-    __shared__ uint32_t boff[kBins];
+    __shared__ uint32_t gstart[kBins];   // where digit d of this tile starts in the output
+    __shared__ uint32_t lstart[kBins];   // where digit d starts inside the tile
     __shared__ uint32_t wsum[kThreads / 32];
+    __shared__ uint64_t sk[kTile];
+    __shared__ uint32_t sv[kTile];
     const int n = read_n(d_n, ncap);
     const int base = blockIdx.x * kTile;
     if (base >= n) return;
+    const int tn = min(kTile, n - base);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < (kThreads / 32) * kBins; d += kThreads) (&wcnt[0][0])[d] = 0;
     {
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_rs_down(const uint64_t* __restrict
         __syncthreads();
         uint32_t before = 0;
         for (int w = 0; w < warp; w++) before += wsum[w];
-        boff[threadIdx.x] = before + v - tot + hist[threadIdx.x * nblocks + blockIdx.x];
+        gstart[threadIdx.x] = before + v - tot + hist[threadIdx.x * nblocks + blockIdx.x];
     }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
@@ -180,23 +194,46 @@ __global__ void __launch_bounds__(kThreads) k_rs_down(const uint64_t* __restrict
     }
     __syncthreads();
     {
+        // digit d: offsets of each warp's keys inside the digit, the tile's
+        // count, and the digit's start in the tile (block scan of the counts)
         const int d = threadIdx.x;
-        uint32_t s = boff[d];
+        uint32_t c = 0;
 #pragma unroll
         for (int w = 0; w < kThreads / 32; w++) {
-            uint32_t c = wcnt[w][d];
-            wcnt[w][d] = s;
-            s += c;
+            const uint32_t x = wcnt[w][d];
+            wcnt[w][d] = c;
+            c += x;
         }
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        __syncthreads();   // wsum is reused
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; w++) before += wsum[w];
+        lstart[d] = before + x - c;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kItems; r++) {
         if (dig[r] >= 0) {
-            const uint32_t p = wcnt[warp][dig[r]] + pos[r];
-            kout[p] = k[r];
-            vout[p] = v[r];
+            const uint32_t lp = lstart[dig[r]] + wcnt[warp][dig[r]] + pos[r];
+            sk[lp] = k[r];
+            sv[lp] = v[r];
         }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < tn; j += kThreads) {
+        const uint64_t kk = sk[j];
+        const uint32_t vv = sv[j];
+        const int d = kBoxDigit ? (int)((box[vv] >> shift) & 255) : (int)((kk >> shift) & 255ull);
+        const uint32_t p = gstart[d] + ((uint32_t)j - lstart[d]);
+        kout[p] = kk;
+        vout[p] = vv;
     }
 }
 
