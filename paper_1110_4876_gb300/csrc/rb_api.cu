@@ -199,6 +199,9 @@ int alloc_pairs(rb_sim* s, int cap) {
     rc |= dalloc(s, &R.eval_alt, 2 * (size_t)cap, L);
     rc |= dalloc(s, &R.prev_a, cap, L);
     rc |= dalloc(s, &R.prev_b, cap, L);
+    rc |= dalloc(s, &R.next_a, cap, L);
+    rc |= dalloc(s, &R.next_b, cap, L);
+    rc |= dalloc(s, &R.wait, cap, L);
     rc |= dalloc(s, &R.rdone, cap, L);
     rc |= dalloc(s, &R.list0, cap, L);
     rc |= dalloc(s, &R.list1, cap, L);

@@ -104,9 +104,11 @@ struct Pairs {
     uint64_t *ekey, *ekey_alt; // pair ends: particle slot (sort key)
     uint32_t *eval, *eval_alt; // pair ends: 2 * pair + side
     int32_t *prev_a, *prev_b;  // previous pair (queue order) of particle a / b, or -1
+    int32_t *next_a, *next_b;  // next pair of particle a / b, or -1
+    int32_t* wait;             // unresolved predecessors of each pair
     int32_t* rdone;            // round in which a pair was resolved, -1 while pending
-    int32_t *list0, *list1;    // pending pairs entering a round (ping-pong)
-    int32_t* rcnt;             // rcnt[r]: pairs pending at the start of round r (64)
+    int32_t *list0, *list1;    // pairs ready in a round (ping-pong)
+    int32_t* rcnt;             // rcnt[r]: pairs ready in round r (64)
     int32_t* slot_of_id;       // global id -> slot in the current set
     uint32_t *hist, *ehist;
     int cap;

@@ -11,7 +11,11 @@
 #include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "rb_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rb {
 namespace {
@@ -182,7 +186,9 @@ struct ResolveArgs {
     PSet P;
     const uint64_t* key;
     const int32_t* slot_of_id;
-    const int32_t *prev_a, *prev_b;
+    const int32_t *prev_a, *prev_b;   // previous pair of particle a / b (queue order), or -1
+    const int32_t *next_a, *next_b;   // next pair of particle a / b, or -1
+    int32_t* wait;                    // predecessors of a pair not yet resolved
     int32_t* rdone;
     Ctl* ctl;
     const BoxP* boxes;
@@ -254,68 +260,83 @@ __global__ void __launch_bounds__(256) k_pair_prev(const uint64_t* __restrict__ 
                                                    const Ctl* __restrict__ ctl,
                                                    int32_t* __restrict__ prev_a,
                                                    int32_t* __restrict__ prev_b,
+                                                   int32_t* __restrict__ next_a,
+                                                   int32_t* __restrict__ next_b,
                                                    int32_t* __restrict__ rdone) {
     const int m = ctl->pair_ends;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
         const uint32_t v = eval[e];
         const int k = (int)(v >> 1);
         const int prev = (e > 0 && ekey[e - 1] == ekey[e]) ? (int)(eval[e - 1] >> 1) : -1;
-        if (v & 1u) prev_b[k] = prev; else prev_a[k] = prev;
-        if (!(v & 1u)) rdone[k] = -1;
+        const int next = (e + 1 < m && ekey[e + 1] == ekey[e]) ? (int)(eval[e + 1] >> 1) : -1;
+        if (v & 1u) {
+            prev_b[k] = prev;
+            next_b[k] = next;
+        } else {
+            prev_a[k] = prev;
+            next_a[k] = next;
+            rdone[k] = -1;
+        }
     }
 }
 
-// Round r: a pending pair is resolved when the previous pair of each of its
-// particles was resolved in an earlier round.  Pairs resolved in the same
-// round share no particle, and every pair sees the results of all earlier
-// pairs that share a particle with it, so the outcome equals resolving the
-// sorted queue one pair at a time (the longest chain of the queue sets the
-// number of rounds; the tail finishes whatever the rounds leave).  Each round
-// reads only the pairs still pending (round 0: all) and appends the ones that
-// stay pending to the next round's list.
+// Appends k to a list with one atomic per group of lanes appending together.
+__device__ __forceinline__ void list_push(int32_t* list, int32_t* count, int k) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(count, (int)g.size());
+    list[g.shfl(base, 0) + (int)g.thread_rank()] = k;
+}
+
+// Round 0's list: the pairs that are the first pair of both their particles;
+// every pair waits for as many predecessors as it has.
+__global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, int32_t* __restrict__ list,
+                                                  int32_t* __restrict__ rcnt) {
+    const int n = A.ctl->pair_n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int w = (A.prev_a[k] >= 0 ? 1 : 0) + (A.prev_b[k] >= 0 ? 1 : 0);
+        A.wait[k] = w;
+        if (w == 0) list_push(list, &rcnt[0], k);
+    }
+}
+
+// Resolves pair k in round r and releases its successors: a pair whose last
+// predecessor this was joins the next round's list.
+__device__ __forceinline__ bool resolve_release(const ResolveArgs& A, const SimC& C, int k, int r,
+                                                int32_t* list_out, int32_t* count_out) {
+    const bool done = resolve_one(A, C, A.key[k]);
+    A.rdone[k] = r;
+    const int na = A.next_a[k], nb = A.next_b[k];
+    if (na >= 0 && atomicSub(&A.wait[na], 1) == 1) list_push(list_out, count_out, na);
+    if (nb >= 0 && atomicSub(&A.wait[nb], 1) == 1) list_push(list_out, count_out, nb);
+    return done;
+}
+
+// Round r resolves the pairs whose predecessors (the previous pair of each
+// of its particles in queue order) were all resolved in earlier rounds: its
+// list holds exactly those, built by the rounds before.  Pairs of one round
+// share no particle, and every pair sees the results of all earlier pairs
+// that share a particle with it, so the outcome equals resolving the sorted
+// queue one pair at a time; each pair is visited once.  The longest chain of
+// the queue sets the number of rounds; the tail finishes what 32 rounds leave.
 __global__ void __launch_bounds__(256) k_res_round(ResolveArgs A, SimC C, int r,
                                                    const int32_t* __restrict__ list_in,
                                                    int32_t* __restrict__ list_out,
                                                    int32_t* __restrict__ rcnt) {
-    const int n = r == 0 ? A.ctl->pair_n : rcnt[r];
+    const int n = rcnt[r];
     if (n == 0) return;
-    const int lane = threadIdx.x & 31;
     int nd = 0, nr = 0;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const int t = base + threadIdx.x;
-        bool keep = false;
-        int k = 0;
-        if (t < n) {
-            k = r == 0 ? t : list_in[t];
-            const int pa = A.prev_a[k], pb = A.prev_b[k];
-            const bool ready_a = pa < 0 || (unsigned)A.rdone[pa] < (unsigned)r;
-            const bool ready_b = pb < 0 || (unsigned)A.rdone[pb] < (unsigned)r;
-            if (ready_a && ready_b) {
-                nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
-                A.rdone[k] = r;
-                nd++;
-            } else {
-                keep = true;
-            }
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            int pos = 0;
-            if (lane == leader) pos = atomicAdd(&rcnt[r + 1], __popc(m));
-            pos = __shfl_sync(0xffffffffu, pos, leader);
-            if (keep) list_out[pos + __popc(m & ((1u << lane) - 1u))] = k;
-        }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        nr += resolve_release(A, C, list_in[t], r, list_out, &rcnt[r + 1]) ? 1 : 0;
+        nd++;
     }
     if (nd) atomicSub(&A.ctl->pending, nd);
     if (nr) atomicAdd(&A.ctl->resolved, nr);
 }
 
 // What the grid-wide rounds left: one block keeps running rounds (same rule,
-// block barriers instead of launches) on the shrinking pending list.  The
-// lowest pending pair is always ready, so every round resolves at least one
-// pair; after kTailRounds rounds any remainder is resolved by one thread in
-// queue order.
+// block barriers instead of launches) on its ready lists.  After kTailRounds
+// rounds any remainder is resolved by one thread in queue order.
 constexpr int kTailRounds = 4096;
 
 __global__ void __launch_bounds__(1024) k_res_tail(ResolveArgs A, SimC C, int r0, int32_t* list_a,
@@ -330,18 +351,8 @@ __global__ void __launch_bounds__(1024) k_res_tail(ResolveArgs A, SimC C, int r0
     for (; n > 0 && r < r0 + kTailRounds; r++) {
         if (threadIdx.x == 0) cnt_next = 0;
         __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int k = in[t];
-            const int pa = A.prev_a[k], pb = A.prev_b[k];
-            const bool ready_a = pa < 0 || (unsigned)A.rdone[pa] < (unsigned)r;
-            const bool ready_b = pb < 0 || (unsigned)A.rdone[pb] < (unsigned)r;
-            if (ready_a && ready_b) {
-                if (resolve_one(A, C, A.key[k])) atomicAdd(&nres, 1);
-                A.rdone[k] = r;
-            } else {
-                out[atomicAdd(&cnt_next, 1)] = k;
-            }
-        }
+        for (int t = threadIdx.x; t < n; t += blockDim.x)
+            if (resolve_release(A, C, in[t], r, out, &cnt_next)) atomicAdd(&nres, 1);
         __syncthreads();
         n = cnt_next;
         int32_t* tmp = in;
@@ -352,6 +363,7 @@ __global__ void __launch_bounds__(1024) k_res_tail(ResolveArgs A, SimC C, int r0
     if (threadIdx.x == 0) {
         int nr = nres;
         if (n > 0 || r0 == 0) {
+            // rounds exhausted (or none ran): the rest in queue order
             const int np = A.ctl->pair_n;
             for (int k = 0; k < np; k++) {
                 if (A.rdone[k] >= 0) continue;
@@ -456,6 +468,7 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
     ResolveArgs A;
     A.P = P; A.key = PR.key; A.slot_of_id = PR.slot_of_id;
     A.prev_a = PR.prev_a; A.prev_b = PR.prev_b; A.rdone = PR.rdone;
+    A.next_a = PR.next_a; A.next_b = PR.next_b; A.wait = PR.wait;
     A.ctl = ctl; A.boxes = boxes; A.hs = half_step_offset;
     const int grid = std::min(ceil_div(PR.cap, 256), 4 * 152);
     k_pair_ends<<<grid, 256, 0, s>>>(A, PR.ekey, PR.eval);
@@ -464,17 +477,16 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
                                  &ctl->pair_ends, 24, nullptr, 0, PR.ehist, s);
     k_pair_prev<<<2 * grid, 256, 0, s>>>(which ? PR.ekey_alt : PR.ekey,
                                          which ? PR.eval_alt : PR.eval, ctl, PR.prev_a, PR.prev_b,
-                                         PR.rdone);
+                                         PR.next_a, PR.next_b, PR.rdone);
     cudaMemsetAsync(PR.rcnt, 0, sizeof(int32_t) * 64, s);
-    for (int r = 0; r < rounds && r < 63; r++)
-        k_res_round<<<grid, 256, 0, s>>>(A, C, r, (r & 1) ? PR.list0 : PR.list1,
-                                         (r & 1) ? PR.list1 : PR.list0, PR.rcnt);
+    // round r reads list0 (r even) or list1 (r odd) and fills the other
+    k_res_seed<<<grid, 256, 0, s>>>(A, PR.list0, PR.rcnt);
     const int last = std::min(rounds, 63);
-    // round r writes its survivors to list0 (r even) or list1 (r odd)
-    int32_t* left = (last & 1) ? PR.list0 : PR.list1;
-    int32_t* spare = (last & 1) ? PR.list1 : PR.list0;
-    // with no grid-wide round before it (r0 == 0) the tail resolves in order
-    k_res_tail<<<1, 1024, 0, s>>>(A, C, last, left, spare, PR.rcnt);
+    for (int r = 0; r < last; r++)
+        k_res_round<<<grid, 256, 0, s>>>(A, C, r, (r & 1) ? PR.list1 : PR.list0,
+                                         (r & 1) ? PR.list0 : PR.list1, PR.rcnt);
+    k_res_tail<<<1, 1024, 0, s>>>(A, C, last, (last & 1) ? PR.list1 : PR.list0,
+                                  (last & 1) ? PR.list0 : PR.list1, PR.rcnt);
 }
 
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
