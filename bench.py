@@ -216,24 +216,32 @@ def run_ours(args):
     value = whole_job_value(world, N_SHEET, args.steps, t_ms)
 
     # ---- end to end through the C ABI with host buffers ----
-    ke = max(1, min(args.steps, 3))
-    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in P.arrays()]
+    ke = max(3, min(args.steps, 10))
+    fields = ("x", "y", "z", "vx", "vy", "vz", "m", "r")
+
+    def pinned():
+        return {k: torch.empty(N_SHEET, dtype=torch.float64).pin_memory().numpy() for k in fields}
+
+    bufs = [pinned(), pinned()]
+    for k, a in zip(fields, P.arrays()):
+        bufs[0][k][:] = a
     sim_e = make_sim(rb, cfg, stream.cuda_stream)
-    sim_e.set_particles(tuple(host))
+    sim_e.set_particles(tuple(bufs[0][k] for k in fields))
     sim_e.step(1)  # capture the step graphs outside the timed region
-    state = tuple(host)
+    sim_e.particles(out=bufs[1])
     barrier()
     t0 = time.perf_counter()
-    for _ in range(ke):
-        sim_e.set_particles(state)
+    for k in range(ke):
+        src, dst = bufs[k & 1], bufs[(k + 1) & 1]
+        sim_e.set_particles(tuple(src[f] for f in fields))   # host -> device
         sim_e.step(1)
-        d = sim_e.particles()
-        state = (d["x"], d["y"], d["z"], d["vx"], d["vy"], d["vz"], d["m"], d["r"])
+        sim_e.particles(out=dst)                                # device -> host
     barrier()
     te = time.perf_counter() - t0
     e2e = {"value": world * N_SHEET * ke / te, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * 8 * N_SHEET, "d2h_bytes_per_step": (8 * 8 + 4 + 4) * N_SHEET,
-           "steps": ke}
+           "h2d_bytes_per_step": 8 * 8 * N_SHEET, "d2h_bytes_per_step": 8 * 8 * N_SHEET,
+           "steps": ke, "host_buffers": "pinned, reused; each step copies the previous step's "
+                                        "output back in"}
     del sim_e
 
     if rank != 0:

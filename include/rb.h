@@ -113,7 +113,10 @@ typedef struct rb_sim rb_sim; /* opaque, owned by the library */
  * omega, an unknown detector, reserved != 0), RB_ERR_CUDA. */
 int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out);
 
-/* Set the side lengths of box `box` (host array of 3; L[1], L[2] <= L[0]). */
+/* Set the side lengths of box `box` (host array of 3; L[1], L[2] <= L[0]).
+ * Meant before rb_set_particles; called later, it keeps the current
+ * particles of every box (ids renumbered over the live ones if an open
+ * boundary removed some) and restarts the step counter. */
 int rb_set_box(rb_sim* sim, int box, const double L[3]);
 
 /* Copy n particles (host arrays: positions, velocities, masses, radii) into

@@ -36,6 +36,8 @@ namespace {
 
 struct BoxHost {
     double L[3];
+    int64_t n = 0;       // particles given to rb_set_particles
+    bool stale = false;  // the arrays below are out of date: the data went straight to the device
     std::vector<double> x, y, z, vx, vy, vz, m, r;
 };
 
@@ -218,7 +220,7 @@ int upload(rb_sim* s) {
     s->base.assign(s->nbox, 0);
     for (int b = 0; b < s->nbox; b++) {
         s->base[b] = tot;
-        tot += (int64_t)s->hb[b].x.size();
+        tot += s->hb[b].n;
     }
     if (tot >= (1 << 24)) return fail(s, RB_ERR_ARG, "more than 2^24 - 1 particles");
     const int n = (int)tot;
@@ -314,7 +316,7 @@ int upload(rb_sim* s) {
     {
         int k = 0;
         for (int b = 0; b < s->nbox; b++)
-            for (size_t i = 0; i < s->hb[b].x.size(); i++) {
+            for (int64_t i = 0; i < s->hb[b].n; i++) {
                 ids[k] = k;
                 bx[k] = b;
                 k++;
@@ -583,6 +585,72 @@ int live_slots(rb_sim* s, int c, int b, std::vector<std::pair<int64_t, int>>& ou
 
 bool bad_box(rb_sim* s, int box) { return !s || box < 0 || box >= s->nbox; }
 
+// The live particles of a box in id order: the device writes them in id
+// order into the idle particle set, then each requested field is copied
+// straight into the caller's array.  Ids removed by an open boundary leave
+// gaps that are closed on the host.
+int read_box(rb_sim* s, int box, int64_t cap, int64_t* n_out, double* const dst[8], int64_t* id) {
+    const int nb = (int)s->hb[box].n;
+    const PSet& out = s->P[1 - s->cur];
+    int32_t* flags = s->T.start;   // scratch: ncap + 1 ints, free between steps
+    particles_by_id(s->P[s->cur], out, box, (int)s->base[box], s->ncap, flags, nb, &s->ctl->out_live,
+                    s->stream);
+    if (read_ctl(s)) return RB_ERR_CUDA;
+    const int live = s->hctl.out_live;
+    if (n_out) *n_out = live;
+    bool want = id != nullptr;
+    for (int f = 0; f < 8; f++) want = want || dst[f] != nullptr;
+    if (!want) return RB_OK;   // a count query
+    if (live > cap) return fail(s, RB_ERR_ARG, "capacity too small");
+    const double* src[8] = {out.x, out.y, out.z, out.vx, out.vy, out.vz, out.m, out.r};
+    if (live == nb) {
+        for (int f = 0; f < 8; f++)
+            if (dst[f])
+                RB_CUDA(s, cudaMemcpyAsync(dst[f], src[f], sizeof(double) * live, cudaMemcpyDeviceToHost,
+                                           s->stream));
+        RB_CUDA(s, cudaStreamSynchronize(s->stream));
+        if (id)
+            for (int k = 0; k < live; k++) id[k] = k;
+        return RB_OK;
+    }
+    std::vector<int32_t> fl;
+    if (d2h(s, fl, flags, nb)) return RB_ERR_CUDA;
+    std::vector<double> buf;
+    for (int f = 0; f < 8; f++) {
+        if (!dst[f]) continue;
+        if (d2h(s, buf, src[f], nb)) return RB_ERR_CUDA;
+        int64_t k = 0;
+        for (int j = 0; j < nb; j++)
+            if (fl[j]) dst[f][k++] = buf[j];
+    }
+    if (id) {
+        int64_t k = 0;
+        for (int j = 0; j < nb; j++)
+            if (fl[j]) id[k++] = j;
+    }
+    return RB_OK;
+}
+
+// The current particles of every box back into the host copies, before
+// anything re-stages all boxes from the host (live particles, in id order).
+int pull_to_host(rb_sim* s) {
+    for (int b = 0; b < s->nbox; b++) {
+        BoxHost& h = s->hb[b];
+        int64_t n = 0;
+        std::vector<double> f[8];
+        for (auto& v : f) v.resize(std::max<int64_t>(h.n, 1));
+        double* dst[8];
+        for (int k = 0; k < 8; k++) dst[k] = f[k].data();
+        int rc = read_box(s, b, h.n, &n, dst, nullptr);
+        if (rc) return rc;
+        std::vector<double>* hv[8] = {&h.x, &h.y, &h.z, &h.vx, &h.vy, &h.vz, &h.m, &h.r};
+        for (int k = 0; k < 8; k++) hv[k]->assign(f[k].begin(), f[k].begin() + n);
+        h.n = n;
+        h.stale = false;
+    }
+    return RB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -638,6 +706,10 @@ int rb_set_box(rb_sim* s, int box, const double L[3]) {
     if (bad_box(s, box) || !L) return fail(s, RB_ERR_ARG, "bad box or null L");
     if (!(L[0] > 0.0 && L[1] > 0.0 && L[2] > 0.0) || L[1] > L[0] || L[2] > L[0])
         return fail(s, RB_ERR_ARG, "box sides must be > 0 with L[1], L[2] <= L[0] (the root cube)");
+    if (!s->dirty) {
+        int rc = pull_to_host(s);
+        if (rc) return rc;
+    }
     for (int a = 0; a < 3; a++) s->hb[box].L[a] = L[a];
     s->dirty = true;
     return RB_OK;
@@ -655,14 +727,38 @@ int rb_set_particles(rb_sim* s, int box, int64_t n, const double* x, const doubl
         if (!(m[i] >= 0.0) || !(r[i] >= 0.0)) return fail(s, RB_ERR_ARG, "negative mass or radius");
     }
     BoxHost& h = s->hb[box];
+    double rm = 0.0;
+    for (int64_t i = 0; i < n; i++) rm = std::max(rm, r[i]);
+    if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN && 2.0 * rm >= std::min(h.L[0], h.L[1]))
+        return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
+    if (s->nbox == 1 && !s->dirty && n > 0 && n <= s->ncap && s->ctl) {
+        // one box already on the device: copy the arrays straight into the
+        // particle set (no host staging, no re-allocation)
+        const double* src[8] = {x, y, z, vx, vy, vz, m, r};
+        double* dst[8] = {s->P[0].x, s->P[0].y, s->P[0].z, s->P[0].vx,
+                          s->P[0].vy, s->P[0].vz, s->P[0].m, s->P[0].r};
+        for (int f = 0; f < 8; f++)
+            RB_CUDA(s, cudaMemcpyAsync(dst[f], src[f], sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+        reset_slots(s->P[0], s->PR.slot_of_id, (int)n, s->ncap, s->nbox, s->stream);
+        Ctl c{};
+        c.n_live = (int)n;
+        RB_CUDA(s, cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+        RB_CUDA(s, cudaStreamSynchronize(s->stream));
+        if (rm != s->rmax) drop_graphs(s);   // R_max is a launch argument of the graphs
+        s->rmax = rm;
+        s->cur = 0;
+        s->acc_set = -1;
+        s->ntot = (int)n;
+        s->base.assign(1, 0);
+        h.n = n;
+        h.stale = true;
+        return RB_OK;
+    }
     h.x.assign(x, x + n); h.y.assign(y, y + n); h.z.assign(z, z + n);
     h.vx.assign(vx, vx + n); h.vy.assign(vy, vy + n); h.vz.assign(vz, vz + n);
     h.m.assign(m, m + n); h.r.assign(r, r + n);
-    if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN) {
-        double rm = 0.0;
-        for (int64_t i = 0; i < n; i++) rm = std::max(rm, r[i]);
-        if (2.0 * rm >= std::min(h.L[0], h.L[1])) return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
-    }
+    h.n = n;
+    h.stale = false;
     s->dirty = true;
     return RB_OK;
 }
@@ -705,22 +801,8 @@ int rb_get_particles(rb_sim* s, int box, int64_t cap, int64_t* n_out, double* x,
     if (bad_box(s, box)) return fail(s, RB_ERR_ARG, "bad box");
     int rc = ensure_ready(s);
     if (rc) return rc;
-    std::vector<std::pair<int64_t, int>> sl;
-    if (live_slots(s, s->cur, box, sl)) return RB_ERR_CUDA;
-    if (n_out) *n_out = (int64_t)sl.size();
-    if ((int64_t)sl.size() > cap) return fail(s, RB_ERR_ARG, "capacity too small");
-    const PSet& P = s->P[s->cur];
-    const double* src[8] = {P.x, P.y, P.z, P.vx, P.vy, P.vz, P.m, P.r};
     double* dst[8] = {x, y, z, vx, vy, vz, m, r};
-    std::vector<double> buf;
-    for (int f = 0; f < 8; f++) {
-        if (!dst[f]) continue;
-        if (d2h(s, buf, src[f], s->ncap)) return RB_ERR_CUDA;
-        for (size_t k = 0; k < sl.size(); k++) dst[f][k] = buf[sl[k].second];
-    }
-    if (id)
-        for (size_t k = 0; k < sl.size(); k++) id[k] = sl[k].first;
-    return RB_OK;
+    return read_box(s, box, cap, n_out, dst, id);
 }
 
 int rb_compute_gravity(rb_sim* s) {
@@ -824,7 +906,7 @@ int rb_get_pairs(rb_sim* s, int box, int64_t cap, int64_t* n, int64_t* id_a, int
     std::vector<uint64_t> keys;
     if (d2h(s, keys, s->PR.key, np)) return RB_ERR_CUDA;
     const int64_t lo = s->base[box];
-    const int64_t hi = lo + (int64_t)s->hb[box].x.size();
+    const int64_t hi = lo + s->hb[box].n;
     int64_t k = 0;
     for (int i = 0; i < np; i++) {
         const int64_t a = (int64_t)(keys[i] >> 36);

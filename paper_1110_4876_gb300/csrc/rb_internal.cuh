@@ -66,6 +66,8 @@ struct Ctl {
     int err;                   // error bits (kErr*)
     int req_count;             // learned-correction requests recorded by the last walk
     int sweep_items;           // plane sweep: trajectory extents of the last search
+    int out_live;              // host exchange: live particles of the box read out
+    int pad_;
     unsigned long long n_cell, n_leaf, n_mac, n_recheck;
     unsigned long long sweep_wbits;   // plane sweep: largest half extent (double bits)
 };
@@ -230,6 +232,12 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s);
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
                   double* partials, int nparts, double* out7, cudaStream_t s);
 void step_advance(Ctl* ctl, cudaStream_t s);
+// Host exchange: the live particles of a box in id order (out: 8 arrays of
+// at least the box's size; flags: one int per id, set for live ids; *count:
+// the live count), and the slot layout of a freshly copied single box.
+void particles_by_id(const PSet& P, const PSet& out, int box, int base, int ncap, int32_t* flags,
+                     int nflags, int* count, cudaStream_t s);
+void reset_slots(const PSet& P, int32_t* slot_of_id, int n, int ncap, int nbox, cudaStream_t s);
 // The live count the keys kernel accumulated, dropped when no sort follows
 // (the particles keep their slots; removed ones stay flagged).
 void discard_live_count(Ctl* ctl, cudaStream_t s);

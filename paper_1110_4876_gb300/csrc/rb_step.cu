@@ -453,6 +453,45 @@ void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl*
 
 void discard_live_count(Ctl* ctl, cudaStream_t s) { k_discard_live<<<1, 1, 0, s>>>(ctl); }
 
+// Live particles of one box written in id order (id - base) to out, with a
+// flag per id and a count.
+__global__ void __launch_bounds__(256) k_by_id(PSet P, PSet out, int box, int base, int ncap,
+                                               int32_t* __restrict__ flags, int* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool mine = i < ncap && P.box[i] == box;
+    if (mine) {
+        const int k = P.id[i] - base;
+        out.x[k] = P.x[i]; out.y[k] = P.y[i]; out.z[k] = P.z[i];
+        out.vx[k] = P.vx[i]; out.vy[k] = P.vy[i]; out.vz[k] = P.vz[i];
+        out.m[k] = P.m[i]; out.r[k] = P.r[i];
+        flags[k] = 1;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, mine);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, __popc(b));
+}
+
+// Slots of a freshly copied single box: slot i holds id i; slots from n on
+// are unused (box = nbox).
+__global__ void __launch_bounds__(256) k_reset_slots(PSet P, int32_t* __restrict__ slot_of_id, int n,
+                                                     int ncap, int nbox) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncap) return;
+    P.id[i] = i;
+    P.box[i] = i < n ? 0 : nbox;
+    slot_of_id[i] = i;
+}
+
+void particles_by_id(const PSet& P, const PSet& out, int box, int base, int ncap, int32_t* flags,
+                     int nflags, int* count, cudaStream_t s) {
+    cudaMemsetAsync(flags, 0, sizeof(int32_t) * (size_t)(nflags > 0 ? nflags : 1), s);
+    cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (ncap > 0) k_by_id<<<ceil_div(ncap, 256), 256, 0, s>>>(P, out, box, base, ncap, flags, count);
+}
+
+void reset_slots(const PSet& P, int32_t* slot_of_id, int n, int ncap, int nbox, cudaStream_t s) {
+    if (ncap > 0) k_reset_slots<<<ceil_div(ncap, 256), 256, 0, s>>>(P, slot_of_id, n, ncap, nbox);
+}
+
 void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s) {
     k_pairs_prep<<<1, 1, 0, s>>>(ctl, PR.cap);
     const int which = radix_sort(PR.key, PR.val, PR.key_alt, PR.val_alt, PR.cap, &ctl->pair_n, 60,

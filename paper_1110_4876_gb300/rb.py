@@ -175,18 +175,25 @@ def rb_step(sim, nsteps: int = 1):
     _check(load().rb_step(sim, nsteps), sim)
 
 
-def rb_get_particles(sim, box: int = 0):
-    """Live particles of a box in id order: dict of arrays (x..r, id)."""
+_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m", "r")
+
+
+def rb_get_particles(sim, box: int = 0, out=None):
+    """Live particles of a box in id order: dict of arrays (x..r, id).  out:
+    optional dict of preallocated float64 arrays (e.g. pinned) for the eight
+    fields, each at least as long as the box; "id" is filled when present."""
     lib = load()
     n = C.c_int64(0)
-    lib.rb_get_particles(sim, box, 0, C.byref(n), *([None] * 9))
-    cap = n.value
-    out = {k: np.zeros(cap) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "r")}
-    out["id"] = np.zeros(cap, dtype=np.int64)
-    rc = lib.rb_get_particles(sim, box, cap, C.byref(n), *(_ptr(out[k]) for k in
-                              ("x", "y", "z", "vx", "vy", "vz", "m", "r", "id")))
+    if out is None:
+        _check(lib.rb_get_particles(sim, box, 0, C.byref(n), *([None] * 9)), sim)
+        cap = n.value
+        out = {k: np.empty(cap) for k in _FIELDS}
+        out["id"] = np.empty(cap, dtype=np.int64)
+    cap = min(len(out[k]) for k in _FIELDS)
+    rc = lib.rb_get_particles(sim, box, cap, C.byref(n), *(_ptr(out[k]) for k in _FIELDS),
+                              _ptr(out.get("id")))
     _check(rc, sim)
-    return out
+    return {k: v[:n.value] for k, v in out.items()}
 
 
 def rb_energy(sim, box: int = 0):
@@ -398,8 +405,8 @@ class Sim:
     def step(self, n: int = 1):
         rb_step(self.h, n)
 
-    def particles(self, box: int = 0):
-        return rb_get_particles(self.h, box)
+    def particles(self, box: int = 0, out=None):
+        return rb_get_particles(self.h, box, out)
 
     def gravity(self, box: int = 0, counts: bool = False):
         rb_compute_gravity(self.h)
