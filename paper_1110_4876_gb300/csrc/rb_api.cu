@@ -720,33 +720,36 @@ int rb_set_particles(rb_sim* s, int box, int64_t n, const double* x, const doubl
                      const double* m, const double* r) {
     if (bad_box(s, box) || n < 0) return fail(s, RB_ERR_ARG, "bad box or n < 0");
     if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !m || !r)) return fail(s, RB_ERR_ARG, "null array");
-    for (int64_t i = 0; i < n; i++) {
-        if (!(std::isfinite(x[i]) && std::isfinite(y[i]) && std::isfinite(z[i]) && std::isfinite(vx[i]) &&
-              std::isfinite(vy[i]) && std::isfinite(vz[i])))
-            return fail(s, RB_ERR_NONFINITE, "non-finite particle state");
-        if (!(m[i] >= 0.0) || !(r[i] >= 0.0)) return fail(s, RB_ERR_ARG, "negative mass or radius");
-    }
     BoxHost& h = s->hb[box];
-    double rm = 0.0;
-    for (int64_t i = 0; i < n; i++) rm = std::max(rm, r[i]);
-    if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN && 2.0 * rm >= std::min(h.L[0], h.L[1]))
-        return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
     if (s->nbox == 1 && !s->dirty && n > 0 && n <= s->ncap && s->ctl) {
         // one box already on the device: copy the arrays straight into the
-        // particle set (no host staging, no re-allocation)
+        // idle particle set, check them there, and switch to it (the current
+        // state stays intact if the check fails)
+        const int c = 1 - s->cur;
+        const PSet& P = s->P[c];
         const double* src[8] = {x, y, z, vx, vy, vz, m, r};
-        double* dst[8] = {s->P[0].x, s->P[0].y, s->P[0].z, s->P[0].vx,
-                          s->P[0].vy, s->P[0].vz, s->P[0].m, s->P[0].r};
+        double* dst[8] = {P.x, P.y, P.z, P.vx, P.vy, P.vz, P.m, P.r};
         for (int f = 0; f < 8; f++)
             RB_CUDA(s, cudaMemcpyAsync(dst[f], src[f], sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-        reset_slots(s->P[0], s->PR.slot_of_id, (int)n, s->ncap, s->nbox, s->stream);
-        Ctl c{};
-        c.n_live = (int)n;
-        RB_CUDA(s, cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+        unsigned long long* chk = reinterpret_cast<unsigned long long*>(s->e_out);
+        check_particles(P, (int)n, chk, s->stream);
+        unsigned long long hc[2] = {0, 0};
+        RB_CUDA(s, cudaMemcpyAsync(hc, chk, sizeof(hc), cudaMemcpyDeviceToHost, s->stream));
+        RB_CUDA(s, cudaStreamSynchronize(s->stream));
+        if (hc[0] & 1ull) return fail(s, RB_ERR_NONFINITE, "non-finite particle state");
+        if (hc[0] & 2ull) return fail(s, RB_ERR_ARG, "negative mass or radius");
+        double rm = 0.0;
+        memcpy(&rm, &hc[1], sizeof(rm));
+        if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN && 2.0 * rm >= std::min(h.L[0], h.L[1]))
+            return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
+        reset_slots(P, s->PR.slot_of_id, (int)n, s->ncap, s->nbox, s->stream);
+        Ctl cc{};
+        cc.n_live = (int)n;
+        RB_CUDA(s, cudaMemcpyAsync(s->ctl, &cc, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
         RB_CUDA(s, cudaStreamSynchronize(s->stream));
         if (rm != s->rmax) drop_graphs(s);   // R_max is a launch argument of the graphs
         s->rmax = rm;
-        s->cur = 0;
+        s->cur = c;
         s->acc_set = -1;
         s->ntot = (int)n;
         s->base.assign(1, 0);
@@ -754,6 +757,16 @@ int rb_set_particles(rb_sim* s, int box, int64_t n, const double* x, const doubl
         h.stale = true;
         return RB_OK;
     }
+    for (int64_t i = 0; i < n; i++) {
+        if (!(std::isfinite(x[i]) && std::isfinite(y[i]) && std::isfinite(z[i]) && std::isfinite(vx[i]) &&
+              std::isfinite(vy[i]) && std::isfinite(vz[i])))
+            return fail(s, RB_ERR_NONFINITE, "non-finite particle state");
+        if (!(m[i] >= 0.0) || !(r[i] >= 0.0)) return fail(s, RB_ERR_ARG, "negative mass or radius");
+    }
+    double rm = 0.0;
+    for (int64_t i = 0; i < n; i++) rm = std::max(rm, r[i]);
+    if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN && 2.0 * rm >= std::min(h.L[0], h.L[1]))
+        return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
     h.x.assign(x, x + n); h.y.assign(y, y + n); h.z.assign(z, z + n);
     h.vx.assign(vx, vx + n); h.vy.assign(vy, vy + n); h.vz.assign(vz, vz + n);
     h.m.assign(m, m + n); h.r.assign(r, r + n);

@@ -238,6 +238,9 @@ void step_advance(Ctl* ctl, cudaStream_t s);
 void particles_by_id(const PSet& P, const PSet& out, int box, int base, int ncap, int32_t* flags,
                      int nflags, int* count, cudaStream_t s);
 void reset_slots(const PSet& P, int32_t* slot_of_id, int n, int ncap, int nbox, cudaStream_t s);
+// out2[0]: bit 0 non-finite state, bit 1 negative mass or radius; out2[1]:
+// the largest radius (double bits).  Particles [0, n) of P.
+void check_particles(const PSet& P, int n, unsigned long long* out2, cudaStream_t s);
 // The live count the keys kernel accumulated, dropped when no sort follows
 // (the particles keep their slots; removed ones stay flagged).
 void discard_live_count(Ctl* ctl, cudaStream_t s);

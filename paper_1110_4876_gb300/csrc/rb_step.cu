@@ -481,6 +481,36 @@ __global__ void __launch_bounds__(256) k_reset_slots(PSet P, int32_t* __restrict
     slot_of_id[i] = i;
 }
 
+// Checks of freshly copied particles: bit 0 a non-finite position or
+// velocity, bit 1 a negative (or NaN) mass or radius; the largest radius as
+// the bits of a non-negative double.
+__global__ void __launch_bounds__(256) k_check_particles(PSet P, int n,
+                                                         unsigned long long* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long bad = 0, rb = 0;
+    if (i < n) {
+        if (!(isfinite(P.x[i]) && isfinite(P.y[i]) && isfinite(P.z[i]) && isfinite(P.vx[i]) &&
+              isfinite(P.vy[i]) && isfinite(P.vz[i])))
+            bad |= 1ull;
+        const double r = P.r[i];
+        if (!(P.m[i] >= 0.0) || !(r >= 0.0)) bad |= 2ull;
+        else if (r > 0.0) rb = (unsigned long long)__double_as_longlong(r);   // not -0.0
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        rb = max(rb, __shfl_xor_sync(0xffffffffu, rb, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&out[0], bad);
+        if (rb) atomicMax(&out[1], rb);
+    }
+}
+
+void check_particles(const PSet& P, int n, unsigned long long* out2, cudaStream_t s) {
+    cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
+    if (n > 0) k_check_particles<<<ceil_div(n, 256), 256, 0, s>>>(P, n, out2);
+}
+
 void particles_by_id(const PSet& P, const PSet& out, int box, int base, int ncap, int32_t* flags,
                      int nflags, int* count, cudaStream_t s) {
     cudaMemsetAsync(flags, 0, sizeof(int32_t) * (size_t)(nflags > 0 ? nflags : 1), s);

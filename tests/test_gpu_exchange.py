@@ -91,3 +91,24 @@ def test_set_box_keeps_the_particles(rb):
     before = sim.particles()
     sim.set_box(0, (L, L, L))
     assert _same(sim.particles(), before)
+
+
+def test_rejected_direct_copy_keeps_the_state(rb):
+    """The direct copy is checked on the device before the simulation
+    switches to it: a non-finite or negative entry is refused and the
+    previous particles stay in place."""
+    L, N = 160.0, 6000
+    sim = rb.Sim(**_cfg(rb, L))
+    sim.set_particles(I.sheet(L, N, 8))
+    sim.step(2)
+    before = sim.particles()
+    for field, value, code in ((0, np.nan, rb.RB_ERR_NONFINITE), (4, np.inf, rb.RB_ERR_NONFINITE),
+                               (6, -1.0, rb.RB_ERR_ARG), (7, -0.5, rb.RB_ERR_ARG)):
+        bad = [a.copy() for a in I.sheet(L, N, 9).arrays()]
+        bad[field][1234] = value
+        with pytest.raises(rb.RbError) as e:
+            sim.set_particles(tuple(bad))
+        assert e.value.code == code
+        assert _same(sim.particles(), before)
+    sim.step(1)
+    assert sim.stats()["steps"] == 3
