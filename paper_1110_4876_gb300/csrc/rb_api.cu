@@ -265,6 +265,8 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.box_first, s->nbox + 1, L);
         rc |= dalloc(s, &T.box_root, s->nbox, L);
         rc |= dalloc(s, &T.lvl, 96, L);
+        rc |= dalloc(s, &T.img, (size_t)s->nbox * (2 * s->cfg.nghost[0] + 1) * (2 * s->cfg.nghost[1] + 1) *
+                                    (2 * s->cfg.nghost[2] + 1), L);
         rc |= dalloc(s, &s->PR.slot_of_id, cap, L);
         rc |= dalloc(s, &s->acc_x, cap, L); rc |= dalloc(s, &s->acc_y, cap, L);
         rc |= dalloc(s, &s->acc_z, cap, L); rc |= dalloc(s, &s->phi, cap, L);

@@ -76,6 +76,13 @@ constexpr int kErrPairOverflow = 2;
 constexpr int kErrSweepLong = 4;    // a plane-sweep item met more than kMaxSweepScan extents
 constexpr int kMaxSweepScan = 1 << 16;
 
+// One ghost image of one box at the time of a walk or search (Sect. 2.3):
+// the offset in FP64 and as hi/lo floats, and the image's y velocity offset.
+struct ImgTab {
+    double ox, oy, oz, dvy;
+    float4 hi, lo;   // w unused
+};
+
 // Tree and scratch buffers of one build (sized for capacity n).
 struct Tree {
     uint64_t *key, *key_alt;    // sort keys (ping-pong)
@@ -96,6 +103,7 @@ struct Tree {
     double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
     int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
     int32_t* lvl;                   // per-depth cell counts / offsets / cursors (96)
+    ImgTab* img;                    // [box][image] offsets of the current walk or search
     int cap_n, cap_e;
 };
 

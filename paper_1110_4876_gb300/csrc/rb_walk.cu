@@ -51,6 +51,8 @@ struct GravArgs {
     const int32_t* e_count;
     const mlp::Packed* wpk;
     int ecap;   // entry capacity (every entry index below it is readable)
+    const ImgTab* img;   // [box][image] offsets at the time of this walk
+    int nimg;
 };
 
 __device__ __forceinline__ double4_32a ld_d4(const double4_32a* p) { return *p; }
@@ -92,6 +94,45 @@ __device__ __forceinline__ void kadd(float& s, float& c, float t) {
     const float u = s + y;
     c = (u - s) - y;
     s = u;
+}
+
+// Ghost-image table of the walk or search time: one thread per (box, image),
+// images in the kernels' loop order (gx outermost, gz innermost).
+__global__ void k_img_table(const BoxP* __restrict__ boxes, const Ctl* __restrict__ ctl, double t0,
+                            double half_dt, int hs, int nbox, int ngx, int ngy, int ngz,
+                            ImgTab* __restrict__ tab) {
+    const int ny = 2 * ngy + 1, nz = 2 * ngz + 1;
+    const int nimg = (2 * ngx + 1) * ny * nz;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nbox * nimg) return;
+    const int b = k / nimg, g = k % nimg;
+    const int gz = g % nz - ngz, gy = (g / nz) % ny - ngy, gx = g / (ny * nz) - ngx;
+    const BoxP bp = boxes[b];
+    const double s = shear_offset(bp, time_of(ctl, t0, half_dt, hs));
+    ImgTab T;
+    image_offset(bp, s, gx, gy, gz, T.ox, T.oy, T.oz);
+    T.dvy = __dmul_rn(-(double)gx, bp.shear_speed);
+    const float hx = __double2float_rn(T.ox), hy = __double2float_rn(T.oy), hz = __double2float_rn(T.oz);
+    T.hi = make_float4(hx, hy, hz, 0.f);
+    T.lo = make_float4(__double2float_rn(T.ox - (double)hx), __double2float_rn(T.oy - (double)hy),
+                       __double2float_rn(T.oz - (double)hz), 0.f);
+    tab[k] = T;
+}
+
+// t = p - o for hi/lo float pairs: the rounding error of ph - oh is kept
+// (Knuth's two-sum) and the low parts are subtracted, so t is good to about
+// 2^-45 of |p| without any FP64 arithmetic.
+__device__ __forceinline__ void sub_hilo(float ph, float pl, float oh, float ol, float& th, float& tl) {
+    const float s = ph - oh;
+    const float bb = s - ph;
+    const float e = (ph - (s - bb)) + (-oh - bb);
+    th = s;
+    tl = e + (pl - ol);
+}
+
+__device__ __forceinline__ void split_d(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
 }
 
 // Is the target point inside the closed cube of a cell (FP64, exact sequence)?
@@ -149,32 +190,27 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
     const int self_leaf = A.leaf_of[ii];
     // the FP64 target point of the current image: read only by the rare FP64
     // re-decisions, so it lives in shared memory rather than in registers
-    // (dynamic shared memory, 3 x 8 bytes per thread of the launch)
-    extern __shared__ __align__(16) unsigned char wsm[];
-    double* tgt = reinterpret_cast<double*>(wsm);   // [3][blockDim.x]
-    const int tid = threadIdx.x, nb = blockDim.x;
+    // the target particle as hi/lo floats; each image's offset comes from the
+    // image table, so no FP64 arithmetic is needed per image
+    float phx, plx, phy, ply, phz, plz;
+    split_d(A.x[ii], phx, plx);
+    split_d(A.y[ii], phy, ply);
+    split_d(A.z[ii], phz, plz);
+    const ImgTab* itab = A.img + (size_t)A.box[ii] * A.nimg;
+    int gi = 0;
     double pot = 0.0;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // sums + compensation
     int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0, ncorr = 0;
     int qn = 0;   // kLearn: rows waiting in this warp's queue (warp-uniform)
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
-            for (int gz = -A.ngz; gz <= A.ngz; gz++) {
+            for (int gz = -A.ngz; gz <= A.ngz; gz++, gi++) {
                 float thx, thy, thz, tlx, tly, tlz;
                 {
-                    const BoxP bp = A.boxes[A.box[ii]];
-                    const double s = shear_offset(bp, time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset));
-                    double ox, oy, oz;
-                    image_offset(bp, s, gx, gy, gz, ox, oy, oz);
-                    const double tx = __dsub_rn(A.x[ii], ox), ty = __dsub_rn(A.y[ii], oy),
-                                 tz = __dsub_rn(A.z[ii], oz);
-                    tgt[tid] = tx;
-                    tgt[nb + tid] = ty;
-                    tgt[2 * nb + tid] = tz;
-                    thx = __double2float_rn(tx); thy = __double2float_rn(ty); thz = __double2float_rn(tz);
-                    tlx = __double2float_rn(tx - (double)thx);
-                    tly = __double2float_rn(ty - (double)thy);
-                    tlz = __double2float_rn(tz - (double)thz);
+                    const float4 oh = itab[gi].hi, ol = itab[gi].lo;
+                    sub_hilo(phx, plx, oh.x, ol.x, thx, tlx);
+                    sub_hilo(phy, ply, oh.y, ol.y, thy, tly);
+                    sub_hilo(phz, plz, oh.z, ol.z, thz, tlz);
                 }
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
@@ -220,8 +256,9 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                         nmac++;
                         bool acc = ra.w < r2;
                         if (fabsf(ra.w - r2) <= 1e-5f * r2) {
-                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, tgt[tid], tgt[nb + tid],
-                                        tgt[2 * nb + tid]);
+                            // the FP64 target point x - o, as the oracle forms it
+                            acc = mac64(ld_d4(&A.d_a[e]), A.theta2, __dsub_rn(A.x[ii], itab[gi].ox),
+                                        __dsub_rn(A.y[ii], itab[gi].oy), __dsub_rn(A.z[ii], itab[gi].oz));
                             nrecheck++;
                         }
                         if (kInside && acc) {
@@ -233,8 +270,9 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                             const float w = ch.w, tol = 1e-5f * ch.w;
                             const float mx = fminf(fminf(ux, w - ux), fminf(fminf(uy, w - uy), fminf(uz, w - uz)));
                             if (fabsf(mx) <= tol) {
-                                acc = !inside64(ld_d4(&A.d_c[e]), tgt[tid], tgt[nb + tid],
-                                                tgt[2 * nb + tid]);
+                                acc = !inside64(ld_d4(&A.d_c[e]), __dsub_rn(A.x[ii], itab[gi].ox),
+                                                __dsub_rn(A.y[ii], itab[gi].oy),
+                                                __dsub_rn(A.z[ii], itab[gi].oz));
                                 nrecheck++;
                             } else if (mx > 0.f) {
                                 acc = false;
@@ -434,20 +472,18 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
     const bool valid = i < n;
     const int ii = valid ? i : n - 1;
     const double px = A.x[ii], py = A.y[ii], pz = A.z[ii];
-    const BoxP bp = A.boxes[A.box[ii]];
     const int root = A.box_root[A.box[ii]];
     const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
     const int self_leaf = A.leaf_of[ii];
-    const double t = time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset);
-    const double s = shear_offset(bp, t);
+    const ImgTab* itab = A.img + (size_t)A.box[ii] * A.nimg;
+    int gi = 0;
     const double soft2 = A.soft2;
     double ax = 0.0, ay = 0.0, az = 0.0, pot = 0.0;
     int ncell = 0, nleaf = 0, nmac = 0;
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
-            for (int gz = -A.ngz; gz <= A.ngz; gz++) {
-                double ox, oy, oz;
-                image_offset(bp, s, gx, gy, gz, ox, oy, oz);
+            for (int gz = -A.ngz; gz <= A.ngz; gz++, gi++) {
+                const double ox = itab[gi].ox, oy = itab[gi].oy, oz = itab[gi].oz;
                 const double tx = __dsub_rn(px, ox), ty = __dsub_rn(py, oy), tz = __dsub_rn(pz, oz);
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
@@ -547,6 +583,8 @@ struct CollArgs {
     int ngx, ngy, ngz;
     int half_step_offset;
     double t0, half_dt;
+    const ImgTab* img;   // [box][image] offsets at the time of this search
+    int nimg;
 };
 
 // Overlap test of Sect. 5.1 on the canonical orientation (a = lower id, b
@@ -580,24 +618,26 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
     const int ii = valid ? i : n - 1;
     const double px = A.x[ii], py = A.y[ii], pz = A.z[ii], pr = A.r[ii];
     const int pid = A.id[ii];
-    const BoxP bp = A.boxes[A.box[ii]];
     const int root = A.box_root[A.box[ii]];
     const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
-    const double t = time_of(A.ctl, A.t0, A.half_dt, A.half_step_offset);
-    const double s = shear_offset(bp, t);
     const float prf = (float)pr;
+    float phx, plx, phy, ply, phz, plz;
+    split_d(px, phx, plx);
+    split_d(py, phy, ply);
+    split_d(pz, phz, plz);
+    const ImgTab* itab = A.img + (size_t)A.box[ii] * A.nimg;
+    int gi = 0;
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
-            for (int gz = -A.ngz; gz <= A.ngz; gz++) {
-                double ox, oy, oz;
-                image_offset(bp, s, gx, gy, gz, ox, oy, oz);
+            for (int gz = -A.ngz; gz <= A.ngz; gz++, gi++) {
                 const int code = (gx + 7) | ((gy + 7) << 4) | ((gz + 7) << 8);
-                const double tx = __dsub_rn(px, ox), ty = __dsub_rn(py, oy), tz = __dsub_rn(pz, oz);
-                const float thx = __double2float_rn(tx), thy = __double2float_rn(ty),
-                            thz = __double2float_rn(tz);
-                const float tlx = __double2float_rn(tx - (double)thx);
-                const float tly = __double2float_rn(ty - (double)thy);
-                const float tlz = __double2float_rn(tz - (double)thz);
+                float thx, thy, thz, tlx, tly, tlz;
+                {
+                    const float4 oh = itab[gi].hi, ol = itab[gi].lo;
+                    sub_hilo(phx, plx, oh.x, ol.x, thx, tlx);
+                    sub_hilo(phy, ply, oh.y, ol.y, thy, tly);
+                    sub_hilo(phz, plz, oh.z, ol.z, thz, tlz);
+                }
                 int next = (valid && root >= 0) ? root : kEnd;
                 for (;;) {
                     if (next >= wend) next = kEnd;
@@ -619,17 +659,17 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
                                 const float sr = prf + rb.w;
                                 if (d2 < sr * sr * 1.0001f) {
                                     const int jid = A.id[j];
+                                    const double ox = itab[gi].ox, oy = itab[gi].oy, oz = itab[gi].oz;
                                     if (pid < jid) {
                                         hit = overlap64(px, py, pz, pr, A.x[j], A.y[j], A.z[j],
                                                         A.r[j], ox, oy, oz);
                                         key = ((uint64_t)pid << 36) | ((uint64_t)jid << 12) |
                                               (uint64_t)code;
                                     } else {
-                                        // j is the lower id: this particle is its image -g
-                                        double nx, ny, nz;
-                                        image_offset(bp, s, -gx, -gy, -gz, nx, ny, nz);
+                                        // j is the lower id: this particle is its image -g,
+                                        // whose offset is exactly -o (rounding is symmetric)
                                         hit = overlap64(A.x[j], A.y[j], A.z[j], A.r[j], px, py, pz,
-                                                        pr, nx, ny, nz);
+                                                        pr, -ox, -oy, -oz);
                                         const int ncode =
                                             (-gx + 7) | ((-gy + 7) << 4) | ((-gz + 7) << 8);
                                         key = ((uint64_t)jid << 36) | ((uint64_t)pid << 12) |
@@ -701,8 +741,14 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     const bool quad = C.quadrupole != 0;
     const bool soft = C.soft2 > 0.0;
     const int grid = ceil_div(T.cap_n, block);
-    // dynamic shared memory: the FP64 target point of each thread
-    const size_t sm_tgt = (size_t)block * 3 * sizeof(double);
+    const size_t sm_tgt = 0;   // no dynamic shared memory
+    A.img = T.img;
+    A.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
+    {
+        const int nt = C.nbox * A.nimg;
+        k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset,
+                                                       C.nbox, C.ngx, C.ngy, C.ngz, T.img);
+    }
 #define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, sm_tgt, s>>>(A)
 #define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, block, 0, s>>>(A)
     if (learn && !potential) {
@@ -756,6 +802,11 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.pair_key = PR.key; A.pair_cap = PR.cap; A.ncap = T.cap_n;
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
     A.half_step_offset = half_step_offset; A.t0 = C.t0; A.half_dt = C.half_dt;
+    A.img = T.img;
+    A.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
+    const int nt = C.nbox * A.nimg;
+    k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset, C.nbox,
+                                                   C.ngx, C.ngy, C.ngz, T.img);
     k_collide<<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
 }
 
