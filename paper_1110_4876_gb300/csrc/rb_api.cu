@@ -431,7 +431,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st);
         mark(s, 11);
-        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, st);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
     } else if (s->cfg.collisions) {
         sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, st);
         c = 1 - c;
@@ -444,7 +444,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st);
         mark(s, 11);
-        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, st);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
     } else {
         discard_live_count(s->ctl, st);   // no sort follows the last drift
         for (int k = 7; k <= 11; k++) mark(s, k);
@@ -513,7 +513,7 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve) {
                                             "(use the tree detector)");
         if (s->hctl.pair_count <= s->PR.cap) {
             if (resolve) {
-                resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, kResolveRounds, s->stream);
+                resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, kResolveRounds, s->T.img, s->stream);
                 if (read_ctl(s)) return RB_ERR_CUDA;
             }
             return RB_OK;

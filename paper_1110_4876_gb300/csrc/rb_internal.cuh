@@ -213,6 +213,10 @@ struct WalkLearn {
     const mlp::Packed* w;   // inference weights (device)
     float band_scale;       // (theta_lo / theta)^2
 };
+// Ghost-image table (tab: nbox x images) at the time 2 step + hs half steps;
+// returns the images per box.  Images in (gx, gy, gz) loop order, gz fastest.
+int build_image_table(const BoxP* boxes, const Ctl* ctl, const SimC& C, int half_step_offset, ImgTab* tab,
+                      cudaStream_t s);
 // Walk and search kernels take their block size (64, 128 or 256 threads)
 // at run time; the autotuner picks it.
 constexpr int kMaxWalkBlock = 256;
@@ -235,7 +239,7 @@ void drift_keys(const PSet& P, const Tree& T, Ctl* ctl, const BoxP* boxes, const
 void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl* ctl,
                       const SimC& C, int ncap, int box_bits, cudaStream_t s);
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
-                   int half_step_offset, int rounds, cudaStream_t s);
+                   int half_step_offset, int rounds, ImgTab* img, cudaStream_t s);
 void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s);
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
                   double* partials, int nparts, double* out7, cudaStream_t s);

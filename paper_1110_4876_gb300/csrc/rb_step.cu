@@ -193,6 +193,8 @@ struct ResolveArgs {
     Ctl* ctl;
     const BoxP* boxes;
     int hs;
+    const ImgTab* img;   // [box][image] offsets at the detection time
+    int nimg, ngx, ngy, ngz;
 };
 
 __device__ __forceinline__ void pair_slots(const ResolveArgs& A, uint64_t k, int& sa, int& sb) {
@@ -206,13 +208,10 @@ __device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C,
     pair_slots(A, k, a, b);
     const int code = (int)(k & 0xFFFull);
     const int gx = (code & 15) - 7, gy = ((code >> 4) & 15) - 7, gz = ((code >> 8) & 15) - 7;
-    const BoxP bp = A.boxes[A.P.box[a]];
-    const double t = time_at(A.ctl, C, A.hs);
-    const double s = bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
-    const double ox = __dmul_rn((double)gx, bp.Lx);
-    const double oy = __dsub_rn(__dmul_rn((double)gy, bp.Ly), __dmul_rn((double)gx, s));
-    const double oz = __dmul_rn((double)gz, bp.Lz);
-    const double dvg = __dmul_rn(-(double)gx, bp.shear_speed);
+    // the image's offsets from the table (same formulas as the search used)
+    const int g = ((gx + A.ngx) * (2 * A.ngy + 1) + (gy + A.ngy)) * (2 * A.ngz + 1) + (gz + A.ngz);
+    const ImgTab& T = A.img[(size_t)A.P.box[a] * A.nimg + g];
+    const double ox = T.ox, oy = T.oy, oz = T.oz, dvg = T.dvy;
     const double rx = __dsub_rn(__dadd_rn(A.P.x[b], ox), A.P.x[a]);
     const double ry = __dsub_rn(__dadd_rn(A.P.y[b], oy), A.P.y[a]);
     const double rz = __dsub_rn(__dadd_rn(A.P.z[b], oz), A.P.z[a]);
@@ -533,11 +532,14 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s) {
 }
 
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
-                   int half_step_offset, int rounds, cudaStream_t s) {
+                   int half_step_offset, int rounds, ImgTab* img, cudaStream_t s) {
     ResolveArgs A;
     A.P = P; A.key = PR.key; A.slot_of_id = PR.slot_of_id;
     A.prev_a = PR.prev_a; A.prev_b = PR.prev_b; A.rdone = PR.rdone;
     A.next_a = PR.next_a; A.next_b = PR.next_b; A.wait = PR.wait;
+    A.img = img;
+    A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
+    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, img, s);
     A.ctl = ctl; A.boxes = boxes; A.hs = half_step_offset;
     const int grid = std::min(ceil_div(PR.cap, 256), 4 * 152);
     k_pair_ends<<<grid, 256, 0, s>>>(A, PR.ekey, PR.eval);

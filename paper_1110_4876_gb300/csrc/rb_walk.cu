@@ -706,6 +706,15 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
 
 }  // namespace
 
+int build_image_table(const BoxP* boxes, const Ctl* ctl, const SimC& C, int half_step_offset, ImgTab* tab,
+                      cudaStream_t s) {
+    const int nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
+    const int nt = C.nbox * nimg;
+    k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset, C.nbox,
+                                                   C.ngx, C.ngy, C.ngz, tab);
+    return nimg;
+}
+
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
                   bool counts, cudaStream_t s, const WalkRecord* rec, int block,
@@ -743,12 +752,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     const int grid = ceil_div(T.cap_n, block);
     const size_t sm_tgt = 0;   // no dynamic shared memory
     A.img = T.img;
-    A.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
-    {
-        const int nt = C.nbox * A.nimg;
-        k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset,
-                                                       C.nbox, C.ngx, C.ngy, C.ngz, T.img);
-    }
+    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s);
 #define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, sm_tgt, s>>>(A)
 #define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, block, 0, s>>>(A)
     if (learn && !potential) {
@@ -803,10 +807,7 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
     A.half_step_offset = half_step_offset; A.t0 = C.t0; A.half_dt = C.half_dt;
     A.img = T.img;
-    A.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
-    const int nt = C.nbox * A.nimg;
-    k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset, C.nbox,
-                                                   C.ngx, C.ngy, C.ngz, T.img);
+    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s);
     k_collide<<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
 }
 
