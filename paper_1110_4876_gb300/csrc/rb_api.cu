@@ -177,6 +177,7 @@ int box_params(rb_sim* s) {
         memset(&p, 0, sizeof(p));
         p.L = s->hb[b].L[0];
         p.Lx = s->hb[b].L[0]; p.Ly = s->hb[b].L[1]; p.Lz = s->hb[b].L[2];
+        p.inv_L = 1.0 / p.L;
         p.shear_speed = s->cfg.boundary == RB_BC_SHEAR ? (1.5 * s->cfg.omega) * p.Lx : 0.0;
     }
     RB_CUDA(s, cudaMemcpyAsync(s->d_boxes, hb.data(), sizeof(BoxP) * s->nbox, cudaMemcpyHostToDevice,

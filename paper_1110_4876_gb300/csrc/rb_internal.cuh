@@ -30,7 +30,8 @@ struct BoxP {
     double L;            // root cube side (= Lx = Ly = Lz)
     double Lx, Ly, Lz;   // box sides (periodic lengths)
     double shear_speed;  // (1.5 * Omega) * Lx for shear-periodic boxes, else 0
-    double pad[3];
+    double inv_L;        // 1 / L (rounded), for the fast path of the integer coordinates
+    double pad[2];
 };
 
 // Constants of a simulation, passed by value to kernels.

@@ -31,9 +31,16 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 }
 
 // Integer coordinate floor(((x - lo) / L) * 2^21), clamped to [0, 2^21 - 1].
-__device__ __forceinline__ uint32_t icoord(double x, double lo, double L) {
-    const double u = __ddiv_rn(__dsub_rn(x, lo), L);
-    double k = floor(__dmul_rn(u, 2097152.0));
+// The quotient is first taken as (x - lo) * (1/L), within 2^-51 of the
+// correctly rounded quotient, i.e. within 2^-30 on the 2^21 grid; unless
+// that lands within 1e-7 of a grid line (about one coordinate in 10^7), the
+// floor is the same and the FP64 division is skipped.
+__device__ __forceinline__ uint32_t icoord(double x, double lo, double L, double inv_L) {
+    const double d = __dsub_rn(x, lo);
+    double k = __dmul_rn(__dmul_rn(d, inv_L), 2097152.0);
+    const double f = floor(k);
+    if (k - f < 1e-7 || f + 1.0 - k < 1e-7) k = __dmul_rn(__ddiv_rn(d, L), 2097152.0);
+    k = floor(k);
     if (!(k >= 0.0)) k = 0.0;
     if (k > 2097151.0) k = 2097151.0;
     return (uint32_t)k;
@@ -73,8 +80,9 @@ __device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, double t
     const double hx = 0.5 * bp.Lx, hy = 0.5 * bp.Ly, hz = 0.5 * bp.Lz;
     if (C.boundary == 0)
         return !(x < -hx || x >= hx || y < -hy || y >= hy || z < -hz || z >= hz);
-    const double s = bp.shear_speed != 0.0 ? fmod(__dmul_rn(bp.shear_speed, t), bp.Ly) : 0.0;
     const double vs = bp.shear_speed;
+    // the shear offset only for the few particles that cross in x
+    const double s = (x >= hx || x < -hx) && vs != 0.0 ? fmod(__dmul_rn(vs, t), bp.Ly) : 0.0;
     if (x >= hx) {
         x = __dsub_rn(x, bp.Lx);
         y = __dadd_rn(y, s);
@@ -138,8 +146,8 @@ __global__ void __launch_bounds__(256) k_drift_keys(DriftArgs A, SimC C) {
         A.P.vx[i] = vx; A.P.vy[i] = vy; A.P.vz[i] = vz;
         if (live) {
             const double lo = -0.5 * bp.L;
-            key = (spread3(icoord(x, lo, bp.L)) << 2) | (spread3(icoord(y, lo, bp.L)) << 1) |
-                  spread3(icoord(z, lo, bp.L));
+            key = (spread3(icoord(x, lo, bp.L, bp.inv_L)) << 2) |
+                  (spread3(icoord(y, lo, bp.L, bp.inv_L)) << 1) | spread3(icoord(z, lo, bp.L, bp.inv_L));
         }
     }
     A.key[i] = key;

@@ -222,3 +222,28 @@ def test_ensemble_equals_single_boxes(rb, orc):
         ge, go = ens.particles(b), one.particles()
         assert ge["id"].tolist() == go["id"].tolist()
         assert np.max(np.abs(_arrays(ge) - _arrays(go))) <= 1e-12 * L
+
+
+def test_tree_cells_on_grid_lines(rb, orc):
+    """Particles placed on the 2^21 grid lines of the root cube and one ulp
+    either side: the integer coordinates (and so the cells) equal the
+    oracle's, including the cases decided by the exact FP64 division."""
+    L, n = 100.0, 3000
+    g = np.random.default_rng(12)
+    k = g.integers(0, 2 ** 21, (3, n))
+    pos = -L / 2 + k * (L / 2 ** 21)
+    side = g.integers(-1, 2, (3, n))
+    pos = np.where(side < 0, np.nextafter(pos, -np.inf), np.where(side > 0, np.nextafter(pos, np.inf), pos))
+    pos = np.clip(pos, -L / 2, np.nextafter(L / 2, -np.inf))
+    x, y, z = pos
+    m = g.uniform(0.5, 1.5, n)
+    zero = np.zeros(n)
+    sim = rb.Sim(G=1.0, box=(L, L, L), boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG, theta=0.5,
+                 dt=1e-3, gravity=1, collisions=0, walk=rb.RB_WALK_FP64)
+    sim.set_particles((x, y, z, zero, zero, zero, m, np.zeros(n)))
+    sim.gravity()
+    got = rb.rb_get_tree(sim.h)
+    ref = orc.Tree(x, y, z, m, L).cells()
+    gs = {(d, frozenset(mm.tolist())) for d, mm, *_ in got}
+    rs = {(d, frozenset(mm.tolist())) for d, mm, *_ in ref}
+    assert gs == rs
