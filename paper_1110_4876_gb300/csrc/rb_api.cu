@@ -433,6 +433,19 @@ int record_step(rb_sim* s, int p) {
         sort_pairs(s->PR, s->ctl, st);
         mark(s, 11);
         resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
+    } else if (s->cfg.collisions && s->cfg.gravity) {
+        // the gravity tree still holds the same particles: boxes of their
+        // current positions replace a second sort and build
+        discard_live_count(s->ctl, st);
+        mark(s, 7);
+        mark(s, 8);
+        build_collision_aabb(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
+        mark(s, 9);
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block, true);
+        mark(s, 10);
+        sort_pairs(s->PR, s->ctl, st);
+        mark(s, 11);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
     } else if (s->cfg.collisions) {
         sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, st);
         c = 1 - c;
@@ -498,7 +511,7 @@ int clear_err(rb_sim* s) {
 
 // Collision search + pair sort on set c at half-step offset hs; grows the
 // pair buffer and searches again if it overflowed.  Resolves when asked.
-int collide_with_retry(rb_sim* s, int c, int hs, bool resolve) {
+int collide_with_retry(rb_sim* s, int c, int hs, bool resolve, bool aabb) {
     for (int attempt = 0; attempt < 2; attempt++) {
         RB_CUDA(s, cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream));
         if (clear_err(s)) return RB_ERR_CUDA;
@@ -506,7 +519,7 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve) {
             sweep_search(s->P[c], s->ctl, s->d_boxes, s->C, s->SW, s->PR, hs, s->ncap, s->stream);
         else
             collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
-                             s->search_block);
+                             s->search_block, aabb);
         sort_pairs(s->PR, s->ctl, s->stream);
         if (read_ctl(s)) return RB_ERR_CUDA;
         if (s->hctl.err & kErrSweepLong)
@@ -796,7 +809,7 @@ int rb_step(rb_sim* s, int64_t nsteps) {
             for (int q = 0; q < 12; q++)
                 cudaEventElapsedTime(&s->stage_ms[q], s->ev_stage[q], s->ev_stage[q + 1]);
         s->cur = s->gafter[p];
-        s->acc_set = s->cfg.gravity ? (s->cfg.collisions == RB_COLL_TREE ? 1 - s->cur : s->cur) : -1;
+        s->acc_set = s->cfg.gravity ? s->cur : -1;   // the walk's particle set (no second sort)
         if (s->hctl.err & kErrNonFinite)
             return fail(s, RB_ERR_NONFINITE, "a position became non-finite (or left the box by more than "
                                              "4096 box lengths in one drift half)");
@@ -805,7 +818,8 @@ int rb_step(rb_sim* s, int64_t nsteps) {
                                             "(use the tree detector)");
         if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
             // the step ended before resolution: search again with a larger buffer
-            if ((rc = collide_with_retry(s, s->cur, 0, true))) return rc;
+            const bool aabb = s->cfg.gravity && s->cfg.collisions == RB_COLL_TREE;
+            if ((rc = collide_with_retry(s, s->cur, 0, true, aabb))) return rc;
         }
     }
     return RB_OK;
@@ -911,7 +925,7 @@ int rb_detect_collisions(rb_sim* s) {
     rebuild_now(s);
     if (s->cfg.collisions != RB_COLL_SWEEP)
         build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
-    return collide_with_retry(s, s->cur, 0, false);
+    return collide_with_retry(s, s->cur, 0, false, false);
 }
 
 int rb_get_pairs(rb_sim* s, int box, int64_t cap, int64_t* n, int64_t* id_a, int64_t* id_b,
@@ -1093,13 +1107,22 @@ int rb_autotune(rb_sim* s, int use_cache) {
         s->acc_set = -1;   // the tuning walks left no consistent acceleration record
     }
     if (s->cfg.collisions == RB_COLL_TREE) {
+        // the records the step uses: boxes on the gravity tree, or Eq. 3's
+        // spheres on a collision tree when gravity is off
+        const bool aabb = s->cfg.gravity != 0;
         rebuild_now(s);
-        build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+        if (aabb) {
+            build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, false, s->stream);
+            build_collision_aabb(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+        } else {
+            build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+        }
         float best = 1e30f;
         for (int b : cand) {
             const float ms = time_best(s, [&] {
                 cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream);
-                collision_search(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->PR, 0, s->stream, b);
+                collision_search(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->PR, 0, s->stream, b,
+                                 aabb);
             });
             if (ms < best) { best = ms; sb = b; }
         }

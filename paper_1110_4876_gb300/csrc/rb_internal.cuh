@@ -188,6 +188,11 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
                     cudaStream_t s);
 void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
                            const SimC& C, bool fp64, cudaStream_t s);
+// Collision records on the tree of the last gravity build at the current
+// positions (cells as FP32 boxes of their particles); for collision_search
+// with aabb = true.
+void build_collision_aabb(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                          double rmax, cudaStream_t s);
 void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
                              const SimC& C, double rmax, cudaStream_t s);
 
@@ -226,7 +231,8 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
                   bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128,
                   const WalkLearn* learn = nullptr);
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
-                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128);
+                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128,
+                      bool aabb = false);
 
 // rb_sweep.cu: plane-sweep search on set P at half-step offset hs; the
 // canonical pair keys are appended to PR like the tree search's.

@@ -374,11 +374,11 @@ struct CollRecArgs {
     const int32_t* box;
     const uint64_t* key;
     const BoxP* boxes;
-    const int32_t *e_first, *e_skip;
+    const int32_t *e_first, *e_skip, *leaf_of;
     const int8_t* e_level;
     float4 *ra, *rb;
     const Ctl* ctl;
-    int ecap;
+    int ecap, ncap, nbox;
     double rmax;
 };
 
@@ -413,6 +413,60 @@ __global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
     const float h = __double2float_ru(0.8660254037844387 * w + A.rmax);
     A.ra[k] = make_float4(hx, hy, hz, h);
     A.rb[k] = make_float4(lx, ly, lz, __int_as_float(A.e_skip[k]));
+}
+
+// Collision records on the gravity tree, at the positions after the second
+// drift (Sect. 5.2, with a tighter pruning volume than Eq. 3's sphere): the
+// tree's cells still hold the same particles, and a cell records the
+// axis-aligned box of its particles' current positions (lower corner rounded
+// down, upper corner rounded up to FP32), so the search stays exact without a
+// second sort and build.  Leaves as in k_coll_records; a removed particle's
+// leaf sits at +infinity and is never close.
+__global__ void __launch_bounds__(256) k_aabb_leaves(CollRecArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int e = A.leaf_of[p];
+    if (A.box[p] >= A.nbox) {
+        const float inf = __int_as_float(0x7f800000);
+        A.ra[e] = make_float4(inf, inf, inf, __int_as_float(~p));
+        A.rb[e] = make_float4(0.f, 0.f, 0.f, (float)A.r[p]);
+        return;
+    }
+    float hx, lx, hy, ly, hz, lz;
+    split_hilo(A.x[p], hx, lx);
+    split_hilo(A.y[p], hy, ly);
+    split_hilo(A.z[p], hz, lz);
+    A.ra[e] = make_float4(hx, hy, hz, __int_as_float(~p));
+    A.rb[e] = make_float4(lx, ly, lz, (float)A.r[p]);
+}
+
+__global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t* __restrict__ lvl,
+                                                    const int32_t* __restrict__ list, int depth) {
+    const int cnt = lvl[depth], off = lvl[32 + depth];
+    const float rmaxf = __double2float_ru(A.rmax);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int k = list[off + t];
+        const int end = A.e_skip[k];
+        const float inf = __int_as_float(0x7f800000);
+        float lox = inf, loy = inf, loz = inf, hix = -inf, hiy = -inf, hiz = -inf;
+        for (int c = k + 1; c < end; c = A.e_skip[c]) {
+            if (A.e_level[c] == 22) {
+                const int p = A.e_first[c];
+                if (A.box[p] >= A.nbox) continue;
+                const double x = A.x[p], y = A.y[p], z = A.z[p];
+                lox = fminf(lox, __double2float_rd(x)); hix = fmaxf(hix, __double2float_ru(x));
+                loy = fminf(loy, __double2float_rd(y)); hiy = fmaxf(hiy, __double2float_ru(y));
+                loz = fminf(loz, __double2float_rd(z)); hiz = fmaxf(hiz, __double2float_ru(z));
+            } else {
+                const float4 a = A.ra[c], b = A.rb[c];
+                lox = fminf(lox, a.x); loy = fminf(loy, a.y); loz = fminf(loz, a.z);
+                hix = fmaxf(hix, b.x); hiy = fmaxf(hiy, b.y); hiz = fmaxf(hiz, b.z);
+            }
+        }
+        A.ra[k] = make_float4(lox, loy, loz, rmaxf);
+        A.rb[k] = make_float4(hix, hiy, hiz, __int_as_float(end));
+    }
 }
 
 }  // namespace
@@ -473,9 +527,24 @@ void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP*
     CollRecArgs A;
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
     A.box = P.box; A.key = T.key; A.boxes = boxes;
-    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level;
+    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level; A.leaf_of = T.leaf_of;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
+    A.ncap = T.cap_n; A.nbox = C.nbox;
     k_coll_records<<<ceil_div(T.cap_e, 256), 256, 0, s>>>(A);
+}
+
+void build_collision_aabb(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
+                          double rmax, cudaStream_t s) {
+    CollRecArgs A;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
+    A.box = P.box; A.key = T.key; A.boxes = boxes;
+    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level; A.leaf_of = T.leaf_of;
+    A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
+    A.ncap = T.cap_n; A.nbox = C.nbox;
+    k_aabb_leaves<<<ceil_div(T.cap_n, 256), 256, 0, s>>>(A);
+    // the cell lists per depth of the gravity build (same tree) are reused
+    const int grid = std::min(ceil_div(T.cap_n, 256), 4 * 152);
+    for (int d = kMaxDepth; d >= 0; d--) k_aabb_level<<<grid, 256, 0, s>>>(A, T.lvl, T.e_arrive, d);
 }
 
 }  // namespace rb

@@ -602,12 +602,16 @@ __device__ __forceinline__ bool overlap64(double xa, double ya, double za, doubl
 
 // Tree collision search (Sect. 5.2): descend while the distance from the
 // target point to a cell's centre is below R_i + R_max + (sqrt(3)/2) w (Eq. 3,
-// tested in FP32 with a 2e-5 relative margin so that no overlap is pruned).
+// tested in FP32 with a 2e-5 relative margin so that no overlap is pruned);
+// kAABB: while the distance to the box of the cell's particles is below
+// R_i + R_max (records of build_collision_aabb; a subset of Eq. 3's volume
+// that still holds every overlap).
 // Each unordered pair is examined once, from its lower slot (the other
 // particle reaches it through the opposite image).  A leaf is first screened
 // in FP32 (hi/lo positions, 1e-4 margin, so no overlap is lost); survivors get
 // the exact FP64 test in the oracle's operation order on the canonical
 // orientation (lower id a, image of b as seen from a).
+template <bool kAABB>
 __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
@@ -681,12 +685,24 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
                         }
                     } else if (act) {
                         const float4 rb = __ldg(&A.rb[e]);
-                        const float dx = (ra.x - thx) + (rb.x - tlx);
-                        const float dy = (ra.y - thy) + (rb.y - tly);
-                        const float dz = (ra.z - thz) + (rb.z - tlz);
-                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        const float lim = (prf + ra.w) * 1.00002f;
-                        next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
+                        if (kAABB) {
+                            // distance to the cell's box [ra.xyz, rb.xyz] of particle
+                            // positions; opened unless farther than R_i + R_max
+                            const float ex = fmaxf(fmaxf((ra.x - thx) - tlx, (thx - rb.x) + tlx), 0.f);
+                            const float ey = fmaxf(fmaxf((ra.y - thy) - tly, (thy - rb.y) + tly), 0.f);
+                            const float ez = fmaxf(fmaxf((ra.z - thz) - tlz, (thz - rb.z) + tlz), 0.f);
+                            const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                            const float lim = (prf + ra.w) * 1.0001f +
+                                              4e-7f * (fabsf(thx) + fabsf(thy) + fabsf(thz));
+                            next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
+                        } else {
+                            const float dx = (ra.x - thx) + (rb.x - tlx);
+                            const float dy = (ra.y - thy) + (rb.y - tly);
+                            const float dz = (ra.z - thz) + (rb.z - tlz);
+                            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            const float lim = (prf + ra.w) * 1.00002f;
+                            next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
+                        }
                     }
                     const unsigned hits = __ballot_sync(kFull, hit);
                     if (hits) {
@@ -796,7 +812,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
 }
 
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
-                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block) {
+                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block, bool aabb) {
     if (T.cap_n <= 0) return;
     block = (block == 64 || block == 256) ? block : 128;
     CollArgs A;
@@ -808,7 +824,8 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.half_step_offset = half_step_offset; A.t0 = C.t0; A.half_dt = C.half_dt;
     A.img = T.img;
     A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s);
-    k_collide<<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
+    if (aabb) k_collide<true><<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
+    else k_collide<false><<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
 }
 
 }  // namespace rb

@@ -72,11 +72,16 @@ def test_sheet_1m_pairs_after_steps(rb, orc, sheet1m):
     st = sim.stats()
     assert st["n_live"] == P.n
     got = sim.particles()
+    # the step's own search (boxes on the gravity tree) and a fresh search
+    # (collision tree, Eq. 3) both equal the oracle's on the same positions
+    # (resolution changes velocities only)
+    step_keys = rb.pair_keys(*sim.pairs(detect=False))
     a, b, c = sim.pairs()
     p = params(orc, L)
     ref = orc.collide_tree(p, orc.time_at(p, 4), got["x"], got["y"], got["z"], got["r"], got["id"])
     assert len(ref) > 100_000
     assert np.array_equal(rb.pair_keys(a, b, c), ref)
+    assert np.array_equal(step_keys, ref)
 
 
 def test_mid_sheet_steps_fp32_vs_fp64(rb, orc):

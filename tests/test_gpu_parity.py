@@ -247,3 +247,23 @@ def test_tree_cells_on_grid_lines(rb, orc):
     gs = {(d, frozenset(mm.tolist())) for d, mm, *_ in got}
     rs = {(d, frozenset(mm.tolist())) for d, mm, *_ in ref}
     assert gs == rs
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_step_pairs_on_the_gravity_tree(rb, orc, walk):
+    """With gravity on, the step searches the gravity tree with boxes of the
+    particles' end-of-step positions; after each step its pair set equals
+    the brute-force set on the GPU's positions."""
+    L, N = 100.0, 2400
+    P = I.sheet(L, N, 1)
+    sim = rb.Sim(**sheet_cfg(rb, L, walk))
+    sim.set_particles(P)
+    p = sheet_params(orc, L)
+    for k in range(3):
+        sim.step(1)
+        got = sim.particles()
+        keys = rb.pair_keys(*sim.pairs(detect=False))
+        ref = orc.collide_brute(p, orc.time_at(p, 2 * (k + 1)), got["x"], got["y"], got["z"], got["r"],
+                                got["id"])
+        assert len(ref) > 50
+        assert np.array_equal(keys, ref), k
