@@ -51,6 +51,7 @@ class _Params(C.Structure):
         ("nghost", C.c_int * 3),
         ("boundary", C.c_int), ("z_periodic", C.c_int), ("integrator", C.c_int),
         ("quadrupole", C.c_int), ("gravity", C.c_int), ("collisions", C.c_int),
+        ("n_active", C.c_int64), ("eps_law", C.c_int), ("eps_vc", C.c_double), ("eps_p", C.c_double),
     ]
 
 
@@ -73,6 +74,10 @@ class Params:
     quadrupole: int = 1
     gravity: int = GRAV_TREE
     collisions: int = COLL_NONE
+    n_active: int = -1        # ids >= n_active are test particles (-1: all active)
+    eps_law: int = 0          # 0 constant eps; 1 eps = min(1, (|v_n|/eps_vc)^(-eps_p))
+    eps_vc: float = 1.0
+    eps_p: float = 0.0
     extra: dict = field(default_factory=dict)
 
     def c(self) -> _Params:
@@ -83,6 +88,7 @@ class Params:
         p.nghost[:] = [int(v) for v in self.nghost]
         p.boundary, p.z_periodic, p.integrator = self.boundary, self.z_periodic, self.integrator
         p.quadrupole, p.gravity, p.collisions = self.quadrupole, self.gravity, self.collisions
+        p.n_active, p.eps_law, p.eps_vc, p.eps_p = self.n_active, self.eps_law, self.eps_vc, self.eps_p
         return p
 
 

@@ -42,6 +42,13 @@
  *      +k Lx that are only tested against original particles.
  *  S4  pairs from the sweep use the key and queue order of R8 and the same
  *      resolution (Eq. 2); a pair that is receding at t is not resolved.
+ *  T1  Sect. 4 counts the particles that exert gravity separately from those
+ *      that only feel it (N_active): particles with id >= n_active are test
+ *      particles, their mass counts for collisions and kinetic energy but
+ *      not as a source of Eq. 1 (the tree holds them with zero source mass).
+ *  V1  Sect. 5 allows a velocity-dependent coefficient of restitution without
+ *      fixing a law: law 1 is the power law eps = min(1, (|v_n|/v_c)^(-p))
+ *      (|v_n| the normal approach speed), law 0 the constant eps.
  */
 #include "rb_oracle.h"
 
@@ -899,7 +906,12 @@ void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, cons
         double rr = sqrt((rx * rx + ry * ry) + rz * rz);
         double nx = rx / rr, ny = ry / rr, nz = rz / rr;
         double vn = (ux * nx + uy * ny) + uz * nz;
-        double dlt = -(1.0 + p->eps) * vn;
+        double e = p->eps;
+        if (p->eps_law == 1) { /* reading V1 */
+            double q = pow(fabs(vn) / p->eps_vc, -p->eps_p);
+            e = q < 1.0 ? q : 1.0;
+        }
+        double dlt = -(1.0 + e) * vn;
         double mt = m[a] + m[b];
         double fa = (m[b] / mt) * dlt, fb = (m[a] / mt) * dlt;
         vx[a] = vx[a] - fa * nx; vy[a] = vy[a] - fa * ny; vz[a] = vz[a] - fa * nz;
@@ -912,9 +924,18 @@ void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, cons
 /* One DKD step (Sect. 3) with gravity (Sect. 4) and collisions (Sect. 5)    */
 /* ------------------------------------------------------------------------ */
 
+/* Source masses of Eq. 1 (reading T1): test particles exert no gravity. */
+static double* orc_source_mass(const orc_params* p, int64_t n, const double* m, const int64_t* id) {
+    double* ms = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t i = 0; i < n; i++)
+        ms[i] = (p->n_active >= 0 && id && id[i] >= p->n_active) ? 0.0 : m[i];
+    return ms;
+}
+
 static void orc_gravity_all(const orc_params* p, double t, int64_t n, const double* x,
-                            const double* y, const double* z, const double* m, double* ax,
-                            double* ay, double* az, double* phi) {
+                            const double* y, const double* z, const double* m0, const int64_t* id,
+                            double* ax, double* ay, double* az, double* phi) {
+    double* m = orc_source_mass(p, n, m0, id);
     if (p->gravity == ORC_GRAV_DIRECT) {
         orc_direct_gravity(p, t, n, x, y, z, m, 0, NULL, ax, ay, az, phi);
     } else if (p->gravity == ORC_GRAV_TREE) {
@@ -927,6 +948,7 @@ static void orc_gravity_all(const orc_params* p, double t, int64_t n, const doub
             if (phi) phi[i] = 0.0;
         }
     }
+    free(m);
 }
 
 /* Step number `step` (0 = first step after t0): drift dt/2, boundaries,
@@ -945,7 +967,7 @@ int orc_step(const orc_params* p, int64_t step, int64_t* n, double* x, double* y
     N = orc_boundary(p, t1, N, x, y, z, vx, vy, vz, m, r, id);
     double* bx = (double*)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(double));
     double *gx = bx, *gy = bx + (N > 0 ? N : 1), *gz = bx + 2 * (N > 0 ? N : 1);
-    orc_gravity_all(p, t1, N, x, y, z, m, gx, gy, gz, NULL);
+    orc_gravity_all(p, t1, N, x, y, z, m, id, gx, gy, gz, NULL);
     orc_kick(p, N, vx, vy, vz, gx, gy, gz);
     if (ax) {
         memcpy(ax, gx, (size_t)N * sizeof(double));
@@ -997,7 +1019,7 @@ void orc_energy(const orc_params* p, double t, int64_t n, const double* x, const
     }
     if (p->gravity != ORC_GRAV_NONE && n > 0) {
         double* buf = (double*)malloc((size_t)n * 4 * sizeof(double));
-        orc_gravity_all(p, t, n, x, y, z, m, buf, buf + n, buf + 2 * n, buf + 3 * n);
+        orc_gravity_all(p, t, n, x, y, z, m, NULL, buf, buf + n, buf + 2 * n, buf + 3 * n);
         for (int64_t i = 0; i < n; i++) W = W + 0.5 * m[i] * buf[3 * n + i];
         free(buf);
     }

@@ -33,6 +33,13 @@ typedef struct {
     double theta, eps, soft, dt, t0;
     int nghost[3];
     int boundary, z_periodic, integrator, quadrupole, gravity, collisions;
+    /* test particles (reading T1): ids >= n_active feel gravity but exert
+     * none; n_active < 0: every particle is active */
+    int64_t n_active;
+    /* coefficient of restitution (reading V1): law 0 the constant eps; law 1
+     * eps(v_n) = min(1, (|v_n| / eps_vc)^(-eps_p)) */
+    int eps_law;
+    double eps_vc, eps_p;
 } orc_params;
 
 typedef struct orc_tree orc_tree;
