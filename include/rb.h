@@ -55,6 +55,10 @@ enum { RB_WALK_FP64 = 0, RB_WALK_FP32 = 1, RB_WALK_FP32_LEARNED = 2 };
  * Sect. 5.3 (straight-line trajectories over the drift around the detection
  * time, tau in [-dt/2, dt/2], that come closer than R_a + R_b). */
 enum { RB_COLL_NONE = 0, RB_COLL_TREE = 1, RB_COLL_SWEEP = 2 };
+/* Laws of the normal coefficient of restitution (Sect. 5 allows a constant
+ * or a velocity-dependent one): cfg.eps_restitution, or the power law
+ * eps(v_n) = min(1, (|v_n| / v_c)^(-p)) of the normal approach speed. */
+enum { RB_EPS_CONSTANT = 0, RB_EPS_POWER = 1 };
 
 typedef struct rb_config {
     double G;               /* gravitational constant of Eq. 1 */
@@ -201,6 +205,14 @@ int rb_autotune(rb_sim* sim, int use_cache);
  * threads per block.  Results do not depend on them (each lane runs its own
  * walk).  Errors: RB_ERR_ARG for any other value. */
 int rb_set_launch_shape(rb_sim* sim, int walk_block, int search_block);
+/* Test particles (Sect. 4: particles that feel gravity without exerting it):
+ * in every box, particles with id >= n_active keep their mass for collisions
+ * and kinetic energy but are not sources of Eq. 1.  n_active < 0 (the
+ * default): every particle is a source.  Errors: RB_ERR_ARG (null sim). */
+int rb_set_n_active(rb_sim* sim, int64_t n_active);
+/* Restitution law of Eq. 2: RB_EPS_CONSTANT (cfg.eps_restitution) or
+ * RB_EPS_POWER with v_c > 0 and p >= 0 (RB_ERR_ARG otherwise). */
+int rb_set_restitution(rb_sim* sim, int law, double v_c, double p);
 /* Destroy the simulation and free its device memory. */
 void rb_destroy(rb_sim* sim);
 

@@ -70,6 +70,9 @@ struct rb_sim {
     int gafter[2] = {0, 0};
     std::vector<void*> allocs, pair_allocs;
     Sweep SW{};   // plane-sweep items (collisions == RB_COLL_SWEEP)
+    int64_t n_active = -1;                 // test particles: ids >= n_active per box
+    int eps_law = 0;                       // restitution law (RB_EPS_*)
+    double eps_vc = 1.0, eps_p = 0.0;
     std::string err;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_stage[13] = {};
@@ -147,6 +150,10 @@ void make_constants(rb_sim* s) {
     C.ngy = c.boundary == RB_BC_OPEN ? 0 : c.nghost[1];
     C.ngz = (c.boundary == RB_BC_OPEN || !c.z_periodic) ? 0 : c.nghost[2];
     C.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
+    C.has_test = s->n_active >= 0;
+    C.eps_law = s->eps_law;
+    C.eps_vc = s->eps_vc;
+    C.eps_p = s->eps_p;
     C.G = c.G;
     C.theta = c.theta;
     C.theta2 = c.theta * c.theta;
@@ -179,6 +186,8 @@ int box_params(rb_sim* s) {
         p.Lx = s->hb[b].L[0]; p.Ly = s->hb[b].L[1]; p.Lz = s->hb[b].L[2];
         p.inv_L = 1.0 / p.L;
         p.shear_speed = s->cfg.boundary == RB_BC_SHEAR ? (1.5 * s->cfg.omega) * p.Lx : 0.0;
+        p.base_id = b < (int)s->base.size() ? (int)s->base[b] : 0;
+        p.n_active = s->n_active < 0 ? 0x7fffffff : (int)std::min<int64_t>(s->n_active, 0x7fffffff);
     }
     RB_CUDA(s, cudaMemcpyAsync(s->d_boxes, hb.data(), sizeof(BoxP) * s->nbox, cudaMemcpyHostToDevice,
                                s->stream));
@@ -1149,6 +1158,28 @@ int rb_set_launch_shape(rb_sim* s, int walk_block, int search_block) {
     s->walk_block = walk_block;
     s->search_block = search_block;
     s->tuned = true;
+    drop_graphs(s);
+    return RB_OK;
+}
+
+int rb_set_n_active(rb_sim* s, int64_t n_active) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    s->n_active = n_active < 0 ? -1 : n_active;
+    make_constants(s);
+    drop_graphs(s);
+    if (s->d_boxes && box_params(s) != RB_OK) return RB_ERR_CUDA;
+    return RB_OK;
+}
+
+int rb_set_restitution(rb_sim* s, int law, double v_c, double p) {
+    if (!s) return fail(s, RB_ERR_ARG, "null sim");
+    if (law == RB_EPS_POWER && !(v_c > 0.0 && p >= 0.0 && std::isfinite(v_c) && std::isfinite(p)))
+        return fail(s, RB_ERR_ARG, "power law needs v_c > 0 and p >= 0");
+    if (law != RB_EPS_CONSTANT && law != RB_EPS_POWER) return fail(s, RB_ERR_ARG, "unknown restitution law");
+    s->eps_law = law;
+    s->eps_vc = law == RB_EPS_POWER ? v_c : 1.0;
+    s->eps_p = law == RB_EPS_POWER ? p : 0.0;
+    make_constants(s);
     drop_graphs(s);
     return RB_OK;
 }

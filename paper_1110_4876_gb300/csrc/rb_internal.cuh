@@ -31,7 +31,9 @@ struct BoxP {
     double Lx, Ly, Lz;   // box sides (periodic lengths)
     double shear_speed;  // (1.5 * Omega) * Lx for shear-periodic boxes, else 0
     double inv_L;        // 1 / L (rounded), for the fast path of the integer coordinates
-    double pad[2];
+    int base_id;         // global id of the box's particle 0
+    int n_active;        // particles with id - base_id >= n_active exert no gravity
+    double pad;
 };
 
 // Constants of a simulation, passed by value to kernels.
@@ -40,6 +42,9 @@ struct SimC {
     int boundary, z_periodic, integrator, quadrupole;
     double G, theta, theta2, soft2, eps, dt, half_dt, t0, omega, omega_z;
     double crit_scale;   // 1 / theta^2 (FP32 criterion (w / theta)^2)
+    int has_test;        // some particles are test particles (source mass 0)
+    int eps_law;         // 0: constant eps; 1: eps = min(1, (|v_n| / eps_vc)^(-eps_p))
+    double eps_vc, eps_p;
     // SEI drift coefficients for tau = dt / 2 (x, vx, vy) -> (x, y, vx, vy), and z
     double axx, axu, axv, ayx, ayu, ayv, aux, auu, auv, avx, avu, avv;
     double azz, azw, awz, aww;
@@ -137,6 +142,12 @@ struct Sweep {
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 #ifdef __CUDACC__
+// Source mass of Eq. 1: test particles (id past the box's n_active) exert
+// no gravity.
+__device__ __forceinline__ double source_mass(const BoxP& bp, int id, double m) {
+    return id - bp.base_id < bp.n_active ? m : 0.0;
+}
+
 // Time after 2 * step + hs drift halves: t0 + h * (dt / 2).
 __device__ __forceinline__ double time_of(const Ctl* ctl, double t0, double half_dt, int hs) {
     const double h = (double)(2 * ctl->step + hs);

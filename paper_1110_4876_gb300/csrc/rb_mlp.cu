@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) k_mlp_label(ReqArgs A, float* __restrict_
             const double dx = A.x[j] - v.px, dy = A.y[j] - v.py, dz = A.z[j] - v.pz;
             const double r2 = dx * dx + dy * dy + dz * dz;
             const double inv = 1.0 / sqrt(r2);
-            const double f = A.m[j] * inv * inv * inv;
+            const double f = source_mass(A.boxes[A.box[j]], A.id[j], A.m[j]) * inv * inv * inv;
             sx += f * dx;
             sy += f * dy;
             sz += f * dz;

@@ -233,7 +233,13 @@ __device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C,
         __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz)));
     const double nx = __ddiv_rn(rx, rr), ny = __ddiv_rn(ry, rr), nz = __ddiv_rn(rz, rr);
     const double vn = __dadd_rn(__dadd_rn(__dmul_rn(ux, nx), __dmul_rn(uy, ny)), __dmul_rn(uz, nz));
-    const double dlt = __dmul_rn(-__dadd_rn(1.0, C.eps), vn);
+    double e = C.eps;
+    if (C.eps_law == 1) {
+        // velocity-dependent restitution: min(1, (|v_n| / v_c)^(-p))
+        const double q = pow(__ddiv_rn(fabs(vn), C.eps_vc), -C.eps_p);
+        e = q < 1.0 ? q : 1.0;
+    }
+    const double dlt = __dmul_rn(-__dadd_rn(1.0, e), vn);
     const double ma = A.P.m[a], mb = A.P.m[b];
     const double mt = __dadd_rn(ma, mb);
     const double fa = __dmul_rn(__ddiv_rn(mb, mt), dlt), fb = __dmul_rn(__ddiv_rn(ma, mt), dlt);

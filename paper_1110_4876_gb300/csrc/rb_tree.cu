@@ -192,7 +192,8 @@ __device__ __forceinline__ void cell_index(uint64_t key, int v, double& ix, doub
 
 struct GravRecArgs {
     const double *x, *y, *z, *m;
-    const int32_t* box;
+    const int32_t *box, *id;
+    bool has_test;   // some particles are test particles (source mass 0)
     const uint64_t* key;
     const BoxP* boxes;
     const int32_t *e_first, *e_skip, *e_parent, *e_nchild, *leaf_of;
@@ -212,7 +213,8 @@ __device__ __forceinline__ void child_mass_pos(const GravRecArgs& A, int c, doub
                                                double& y, double& z) {
     if (A.e_level[c] == 22) {
         const int j = A.e_first[c];
-        m = A.m[j]; x = A.x[j]; y = A.y[j]; z = A.z[j];
+        m = A.has_test ? source_mass(A.boxes[A.box[j]], A.id[j], A.m[j]) : A.m[j];
+        x = A.x[j]; y = A.y[j]; z = A.z[j];
     } else {
         const double4_32a a = A.d_a[c];
         m = A.d_q0[c].x;
@@ -226,7 +228,8 @@ __global__ void __launch_bounds__(256) k_leaf_records(GravRecArgs A) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int e = A.leaf_of[p];
-    const double x = A.x[p], y = A.y[p], z = A.z[p], m = A.m[p];
+    const double x = A.x[p], y = A.y[p], z = A.z[p];
+    const double m = A.has_test ? source_mass(A.boxes[A.box[p]], A.id[p], A.m[p]) : A.m[p];
     A.d_a[e] = make_double4_32a(x, y, z, -m);
     if (A.fp32) {
         float hx, lx, hy, ly, hz, lz;
@@ -499,7 +502,8 @@ void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* b
     const int n = T.cap_n;
     if (n <= 0) return;
     GravRecArgs A;
-    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.box = P.box;
+    A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.box = P.box; A.id = P.id;
+    A.has_test = C.has_test != 0;
     A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_parent = T.e_parent;
     A.e_nchild = T.e_nchild; A.leaf_of = T.leaf_of; A.e_level = T.e_level;

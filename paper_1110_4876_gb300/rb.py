@@ -20,6 +20,7 @@ RB_BC_OPEN, RB_BC_PERIODIC, RB_BC_SHEAR = 0, 1, 2
 RB_INT_LEAPFROG, RB_INT_SEI = 0, 1
 RB_WALK_FP64, RB_WALK_FP32, RB_WALK_FP32_LEARNED = 0, 1, 2
 RB_COLL_NONE, RB_COLL_TREE, RB_COLL_SWEEP = 0, 1, 2
+RB_EPS_CONSTANT, RB_EPS_POWER = 0, 1
 
 EXPORTS = [
     "rb_create", "rb_set_box", "rb_set_particles", "rb_step", "rb_get_particles", "rb_energy",
@@ -27,7 +28,7 @@ EXPORTS = [
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
     "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_autotune",
-    "rb_set_pair_capacity", "rb_set_launch_shape",
+    "rb_set_pair_capacity", "rb_set_launch_shape", "rb_set_n_active", "rb_set_restitution",
 ]
 RB_MLP_PARAMS = 9347
 
@@ -101,6 +102,8 @@ def load():
     lib.rb_set_profiling.argtypes = [_P, i32]
     lib.rb_autotune.argtypes = [_P, i32]
     lib.rb_set_launch_shape.argtypes = [_P, i32, i32]
+    lib.rb_set_n_active.argtypes = [_P, C.c_int64]
+    lib.rb_set_restitution.argtypes = [_P, i32, C.c_double, C.c_double]
     lib.rb_set_pair_capacity.argtypes = [_P, i64]
     lib.rb_load_mlp.argtypes = [_P, _VP, i64, C.c_double]
     lib.rb_mlp_samples.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_uint64, i64,
@@ -302,6 +305,16 @@ def rb_autotune(sim, use_cache: bool = True):
     _check(load().rb_autotune(sim, 1 if use_cache else 0), sim)
     st = rb_stats(sim)
     return int(st["walk_block"]), int(st["search_block"])
+
+
+def rb_set_n_active(sim, n_active: int):
+    """Particles with id >= n_active (per box) feel gravity but exert none; -1: all active."""
+    _check(load().rb_set_n_active(sim, int(n_active)), sim)
+
+
+def rb_set_restitution(sim, law: int, v_c: float = 1.0, p: float = 0.0):
+    """RB_EPS_CONSTANT, or RB_EPS_POWER: eps = min(1, (|v_n| / v_c)^(-p))."""
+    _check(load().rb_set_restitution(sim, int(law), float(v_c), float(p)), sim)
 
 
 def rb_set_launch_shape(sim, walk_block: int, search_block: int):
