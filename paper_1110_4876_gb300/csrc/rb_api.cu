@@ -70,6 +70,7 @@ struct rb_sim {
     int gafter[2] = {0, 0};
     std::vector<void*> allocs, pair_allocs;
     Sweep SW{};   // plane-sweep items (collisions == RB_COLL_SWEEP)
+    int nsm = 0;                           // SMs of the device (tile queues of the walks)
     int64_t n_active = -1;                 // test particles: ids >= n_active per box
     int eps_law = 0;                       // restitution law (RB_EPS_*)
     double eps_vc = 1.0, eps_p = 0.0;
@@ -275,6 +276,8 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.box_first, s->nbox + 1, L);
         rc |= dalloc(s, &T.box_root, s->nbox, L);
         rc |= dalloc(s, &T.lvl, 96, L);
+        rc |= dalloc(s, &T.tq, kMaxTileQueues * kTileQStride, L);
+        T.nq = s->nsm > 0 ? min(s->nsm, kMaxTileQueues) : 1;
         rc |= dalloc(s, &T.img, (size_t)s->nbox * (2 * s->cfg.nghost[0] + 1) * (2 * s->cfg.nghost[1] + 1) *
                                     (2 * s->cfg.nghost[2] + 1), L);
         rc |= dalloc(s, &s->PR.slot_of_id, cap, L);
@@ -719,6 +722,7 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
         }
         s->own_stream = true;
     }
+    s->nsm = walk_prepare();
     cudaEventCreate(&s->ev0);
     cudaEventCreate(&s->ev1);
     for (auto& ev : s->ev_stage) cudaEventCreate(&ev);

@@ -110,6 +110,8 @@ struct Tree {
     int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
     int32_t* lvl;                   // per-depth cell counts / offsets / cursors (96)
     ImgTab* img;                    // [box][image] offsets of the current walk or search
+    int32_t* tq;                    // tile queues of the walks (kTileQStride ints each)
+    int nq;                         // number of tile queues (one per SM)
     int cap_n, cap_e;
 };
 
@@ -232,11 +234,23 @@ struct WalkLearn {
 };
 // Ghost-image table (tab: nbox x images) at the time 2 step + hs half steps;
 // returns the images per box.  Images in (gx, gy, gz) loop order, gz fastest.
+// With tq given, the same launch also empties the nq tile queues of the
+// next walk or search.
 int build_image_table(const BoxP* boxes, const Ctl* ctl, const SimC& C, int half_step_offset, ImgTab* tab,
-                      cudaStream_t s);
+                      cudaStream_t s, int32_t* tq = nullptr, int nq = 0);
 // Walk and search kernels take their block size (64, 128 or 256 threads)
-// at run time; the autotuner picks it.
+// at run time; the autotuner picks it.  They run persistent blocks (as many
+// as fit on the GPU at once) that take tiles of 32 consecutive targets from
+// per-SM queues: queue q holds the q-th contiguous part of the Morton order,
+// so the warps resident on one SM walk neighbouring targets and share the
+// tree records they read in that SM's L1.  An empty queue's warps take
+// tiles from the following queues.
 constexpr int kMaxWalkBlock = 256;
+constexpr int kTileQStride = 8;     // ints per queue counter (one 32-byte sector each)
+constexpr int kMaxTileQueues = 512;
+// Queries the residency of every walk and search kernel once (outside any
+// stream capture); returns the number of SMs.
+int walk_prepare();
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
                   bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128,

@@ -17,6 +17,8 @@
 // differ by less than 1e-5 relative is decided again in FP64 on the FP64
 // centre of mass, with the same operation sequence as the oracle.
 #include <cfloat>
+#include <mutex>
+#include <vector>
 
 #include "rb_internal.cuh"
 #include "rb_mlp.cuh"
@@ -53,6 +55,8 @@ struct GravArgs {
     int ecap;   // entry capacity (every entry index below it is readable)
     const ImgTab* img;   // [box][image] offsets at the time of this walk
     int nimg;
+    int32_t* tq;         // tile queues (emptied by the image-table launch)
+    int nq;
 };
 
 __device__ __forceinline__ double4_32a ld_d4(const double4_32a* p) { return *p; }
@@ -96,14 +100,65 @@ __device__ __forceinline__ void kadd(float& s, float& c, float t) {
     s = u;
 }
 
+// Tile scheduling of the walks: queue q owns tiles [b_q, b_{q+1}) with
+// b_q = floor(q T / nq) of the T tiles of 32 consecutive targets.
+__device__ __forceinline__ int tile_begin(int q, int ntile, int nq) {
+    return (int)(((long long)q * ntile) / nq);
+}
+
+__device__ __forceinline__ int sm_queue(int nq) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    return (int)(sm % (unsigned)nq);
+}
+
+// The warp's next tile, or -1 when every queue is empty: its own SM's queue
+// first, then the following queues (32 probed per vote).  Warp-uniform.
+__device__ __noinline__ int next_tile(int32_t* tq, int nq, int q, int ntile) {
+    const int lane = threadIdx.x & 31;
+    int t = -1;
+    if (lane == 0) {
+        const int b = tile_begin(q, ntile, nq);
+        const int k = atomicAdd(&tq[q * kTileQStride], 1);
+        if (k < tile_begin(q + 1, ntile, nq) - b) t = b + k;
+    }
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= 0) return t;
+    for (int k0 = 1; k0 < nq; k0 += 32) {
+        const int off = k0 + lane;
+        int qq = q + off;
+        if (qq >= nq) qq -= nq;
+        int b = 0, len = 0;
+        bool avail = false;
+        if (off < nq) {
+            b = tile_begin(qq, ntile, nq);
+            len = tile_begin(qq + 1, ntile, nq) - b;
+            avail = __ldcg(&tq[qq * kTileQStride]) < len;
+        }
+        for (unsigned m = __ballot_sync(kFull, avail); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            int got = -1;
+            if (lane == src) {
+                const int k = atomicAdd(&tq[qq * kTileQStride], 1);
+                if (k < len) got = b + k;
+            }
+            got = __shfl_sync(kFull, got, src);
+            if (got >= 0) return got;
+        }
+    }
+    return -1;
+}
+
 // Ghost-image table of the walk or search time: one thread per (box, image),
-// images in the kernels' loop order (gx outermost, gz innermost).
+// images in the kernels' loop order (gx outermost, gz innermost).  Threads
+// below nq * kTileQStride also empty the tile queues.
 __global__ void k_img_table(const BoxP* __restrict__ boxes, const Ctl* __restrict__ ctl, double t0,
                             double half_dt, int hs, int nbox, int ngx, int ngy, int ngz,
-                            ImgTab* __restrict__ tab) {
+                            ImgTab* __restrict__ tab, int32_t* __restrict__ tq, int nqw) {
     const int ny = 2 * ngy + 1, nz = 2 * ngz + 1;
     const int nimg = (2 * ngx + 1) * ny * nz;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nqw) tq[k] = 0;
     if (k >= nbox * nimg) return;
     const int b = k / nimg, g = k % nimg;
     const int gz = g % nz - ngz, gy = (g / nz) % ny - ngy, gx = g / (ny * nz) - ngx;
@@ -177,10 +232,8 @@ __device__ __forceinline__ void learn_flush(LearnQ& Q, const mlp::Packed& w, int
 }
 
 template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord, bool kLearn>
-__device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp::Packed* W) {
-    const int n = min(A.ctl->n_live, A.ncap);
-    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
-    if (wbase >= n) return;
+__device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp::Packed* W, int wbase,
+                                       int n) {
     const int lane = threadIdx.x & 31;
     const int i = wbase + lane;
     const bool valid = i < n;
@@ -281,11 +334,12 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                         if (acc) {
                             const float4 q0 = __ldg(&A.rq0[e]);
                             const float4 q1 = __ldg(&A.rq1[e]);
+                            // monopole and quadrupole (reading R3) with the radial
+                            // factors merged: a = (M/R^3 + 2.5 dQd/R^7) d - Q d/R^5
                             const float inv = rsqrt_nr(r2);
                             const float inv2 = inv * inv;
                             const float invs = kSoft ? rsqrt_nr(r2 + A.soft2f) : inv;
-                            const float f = q0.x * (invs * invs * invs);
-                            float tx_ = f * dx, ty_ = f * dy, tz_ = f * dz;
+                            float fc = q0.x * (kSoft ? invs * invs * invs : inv2 * inv);
                             if (kPot) fp = fmaf(-q0.x, invs, fp);
                             if (kQuad) {
                                 const float qx = fmaf(q1.y, dz, fmaf(q1.x, dy, q0.y * dx));
@@ -293,15 +347,15 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                                 const float qz = fmaf(q0.w, dz, fmaf(q1.z, dy, q1.y * dx));
                                 const float dqd = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
                                 const float inv5 = inv2 * inv2 * inv;
-                                const float c = 2.5f * dqd * (inv5 * inv2);
-                                tx_ = fmaf(c, dx, fmaf(-inv5, qx, tx_));
-                                ty_ = fmaf(c, dy, fmaf(-inv5, qy, ty_));
-                                tz_ = fmaf(c, dz, fmaf(-inv5, qz, tz_));
+                                fc = fmaf(2.5f, dqd * (inv5 * inv2), fc);
+                                fx = fmaf(-inv5, qx, fx);
+                                fy = fmaf(-inv5, qy, fy);
+                                fz = fmaf(-inv5, qz, fz);
                                 if (kPot) fp = fmaf(-0.5f * dqd, inv5, fp);
                             }
-                            fx += tx_;
-                            fy += ty_;
-                            fz += tz_;
+                            fx = fmaf(fc, dx, fx);
+                            fy = fmaf(fc, dy, fy);
+                            fz = fmaf(fc, dz, fz);
                             ncell++;
                             next = __float_as_int(rb.w);
                             if (kLearn && ra.w > A.band_scale * r2) {
@@ -442,7 +496,10 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
 
 template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false>
 __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
-    walk32<kQuad, kInside, kPot, kSoft, kRecord, false>(A, nullptr, nullptr);
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
+    for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile))
+        walk32<kQuad, kInside, kPot, kSoft, kRecord, false>(A, nullptr, nullptr, t << 5, n);
 }
 
 // Learned walk: the network's weights and one queue per warp in shared
@@ -457,16 +514,16 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 2) k_walk32_learn(GravArgs A) {
         for (int k = threadIdx.x; k < (int)(sizeof(mlp::Packed) / 16); k += blockDim.x) dst[k] = src[k];
     }
     __syncthreads();
-    walk32<true, kInside, false, kSoft, false, true>(A, &q[threadIdx.x >> 5], &w);
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int ntile = (n + 31) >> 5, sq = sm_queue(A.nq);
+    for (int t = next_tile(A.tq, A.nq, sq, ntile); t >= 0; t = next_tile(A.tq, A.nq, sq, ntile))
+        walk32<true, kInside, false, kSoft, false, true>(A, &q[threadIdx.x >> 5], &w, t << 5, n);
 }
 
 // FP64 walk: the same traversal on FP64 records, every opening test in the
 // oracle's operation sequence.
 template <bool kQuad, bool kInside, bool kPot>
-__global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
-    const int n = min(A.ctl->n_live, A.ncap);
-    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
-    if (wbase >= n) return;
+__device__ __forceinline__ void walk64(const GravArgs& A, int wbase, int n) {
     const int lane = threadIdx.x & 31;
     const int i = wbase + lane;
     const bool valid = i < n;
@@ -570,6 +627,14 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
     }
 }
 
+template <bool kQuad, bool kInside, bool kPot>
+__global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
+    for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile))
+        walk64<kQuad, kInside, kPot>(A, t << 5, n);
+}
+
 struct CollArgs {
     const double *x, *y, *z, *r;
     const int32_t *id, *box;
@@ -585,16 +650,21 @@ struct CollArgs {
     double t0, half_dt;
     const ImgTab* img;   // [box][image] offsets at the time of this search
     int nimg;
+    int32_t* tq;         // tile queues (emptied by the image-table launch)
+    int nq;
 };
 
 // Overlap test of Sect. 5.1 on the canonical orientation (a = lower id, b
 // seen through image offset o), operation for operation as the oracle.
+// kNeg: the offset is -o (b + (-o) and b - o round identically in IEEE
+// arithmetic, so no negated copy of o is formed).
+template <bool kNeg = false>
 __device__ __forceinline__ bool overlap64(double xa, double ya, double za, double ra, double xb,
                                           double yb, double zb, double rb, double ox, double oy,
                                           double oz) {
-    const double rx = __dsub_rn(__dadd_rn(xb, ox), xa);
-    const double ry = __dsub_rn(__dadd_rn(yb, oy), ya);
-    const double rz = __dsub_rn(__dadd_rn(zb, oz), za);
+    const double rx = __dsub_rn(kNeg ? __dsub_rn(xb, ox) : __dadd_rn(xb, ox), xa);
+    const double ry = __dsub_rn(kNeg ? __dsub_rn(yb, oy) : __dadd_rn(yb, oy), ya);
+    const double rz = __dsub_rn(kNeg ? __dsub_rn(zb, oz) : __dadd_rn(zb, oz), za);
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
     const double sr = __dadd_rn(ra, rb);
     return r2 < __dmul_rn(sr, sr);
@@ -607,15 +677,15 @@ __device__ __forceinline__ bool overlap64(double xa, double ya, double za, doubl
 // R_i + R_max (records of build_collision_aabb; a subset of Eq. 3's volume
 // that still holds every overlap).
 // Each unordered pair is examined once, from its lower slot (the other
-// particle reaches it through the opposite image).  A leaf is first screened
-// in FP32 (hi/lo positions, 1e-4 margin, so no overlap is lost); survivors get
-// the exact FP64 test in the oracle's operation order on the canonical
-// orientation (lower id a, image of b as seen from a).
+// particle reaches it through the opposite image).  A leaf's overlap is
+// decided in FP32 on hi/lo positions (distance good to ~1e-7 relative) unless
+// d^2 lies within 1e-4 of (R_a + R_b)^2; only those pairs get the exact FP64
+// test in the oracle's operation order on the canonical orientation (lower
+// id a, image of b as seen from a).  On GB300 an FP64 instruction occupies
+// the SM's FP64 pipe 16 cycles per warp, so the exact test on every overlap
+// kept that pipe busy for most of the search.
 template <bool kAABB>
-__global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
-    const int n = min(A.ctl->n_live, A.ncap);
-    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5;
-    if (wbase >= n) return;
+__device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
     const int lane = threadIdx.x & 31;
     const int i = wbase + lane;
     const bool valid = i < n;
@@ -661,24 +731,26 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
                                 const float dz = (ra.z - thz) + (rb.z - tlz);
                                 const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                                 const float sr = prf + rb.w;
-                                if (d2 < sr * sr * 1.0001f) {
+                                const float s2 = sr * sr;
+                                if (d2 < s2 * 1.0001f) {
                                     const int jid = A.id[j];
-                                    const double ox = itab[gi].ox, oy = itab[gi].oy, oz = itab[gi].oz;
-                                    if (pid < jid) {
-                                        hit = overlap64(px, py, pz, pr, A.x[j], A.y[j], A.z[j],
-                                                        A.r[j], ox, oy, oz);
-                                        key = ((uint64_t)pid << 36) | ((uint64_t)jid << 12) |
-                                              (uint64_t)code;
+                                    const bool low = pid < jid;
+                                    if (d2 < s2 * 0.9999f) {
+                                        // clear of the threshold (the FP32 distance is good to
+                                        // ~1e-7): an overlap without FP64 work
+                                        hit = true;
                                     } else {
-                                        // j is the lower id: this particle is its image -g,
-                                        // whose offset is exactly -o (rounding is symmetric)
-                                        hit = overlap64(A.x[j], A.y[j], A.z[j], A.r[j], px, py, pz,
-                                                        pr, -ox, -oy, -oz);
-                                        const int ncode =
-                                            (-gx + 7) | ((-gy + 7) << 4) | ((-gz + 7) << 8);
-                                        key = ((uint64_t)jid << 36) | ((uint64_t)pid << 12) |
-                                              (uint64_t)ncode;
+                                        const double ox = itab[gi].ox, oy = itab[gi].oy, oz = itab[gi].oz;
+                                        // j the lower id: this particle is its image -g, whose
+                                        // offset is exactly -o (the table is symmetric)
+                                        hit = low ? overlap64(px, py, pz, pr, A.x[j], A.y[j], A.z[j],
+                                                              A.r[j], ox, oy, oz)
+                                                  : overlap64<true>(A.x[j], A.y[j], A.z[j], A.r[j], px,
+                                                                    py, pz, pr, ox, oy, oz);
                                     }
+                                    const int ncode = (-gx + 7) | ((-gy + 7) << 4) | ((-gz + 7) << 8);
+                                    key = low ? ((uint64_t)pid << 36) | ((uint64_t)jid << 12) | (uint64_t)code
+                                              : ((uint64_t)jid << 36) | ((uint64_t)pid << 12) | (uint64_t)ncode;
                                 }
                             }
                             next = e + 1;
@@ -720,15 +792,99 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
             }
 }
 
+template <bool kAABB>
+__global__ void __launch_bounds__(kMaxWalkBlock) k_collide(CollArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
+    for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile))
+        collide<kAABB>(A, t << 5, n);
+}
+
 }  // namespace
 
 int build_image_table(const BoxP* boxes, const Ctl* ctl, const SimC& C, int half_step_offset, ImgTab* tab,
-                      cudaStream_t s) {
+                      cudaStream_t s, int32_t* tq, int nq) {
     const int nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
-    const int nt = C.nbox * nimg;
+    const int nqw = tq ? nq * kTileQStride : 0;
+    const int nt = max(C.nbox * nimg, nqw);
     k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset, C.nbox,
-                                                   C.ngx, C.ngy, C.ngz, tab);
+                                                   C.ngx, C.ngy, C.ngz, tab, tq, nqw);
     return nimg;
+}
+
+namespace {
+
+// Resident blocks per SM of each walk / search kernel at each block size,
+// queried once: a stream capture must not see the first query of a kernel.
+struct Residency {
+    const void* fn;
+    int block, per_sm;
+};
+std::mutex g_res_mu;
+std::vector<Residency> g_res;
+int g_nsm = 0;
+
+int query_residency(const void* fn, int block) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return max(per_sm, 1);
+}
+
+int residency(const void* fn, int block) {
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    for (const Residency& r : g_res)
+        if (r.fn == fn && r.block == block) return r.per_sm;
+    const int per_sm = query_residency(fn, block);
+    g_res.push_back({fn, block, per_sm});
+    return per_sm;
+}
+
+// Persistent grid of kernel fn: the blocks that fit on the GPU at once, but
+// no more than the blocks that one target per thread would need.
+template <typename F>
+int persistent_grid(F fn, int block, int cap_n) {
+    const int need = ceil_div(cap_n, block);
+    const int fit = max(g_nsm, 1) * residency(reinterpret_cast<const void*>(fn), block);
+    return max(1, min(need, fit));
+}
+
+template <typename F>
+void prepare_one(F fn) {
+    for (int b : {64, 128, 256}) residency(reinterpret_cast<const void*>(fn), b);
+}
+
+}  // namespace
+
+int walk_prepare() {
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        if (g_nsm > 0) return g_nsm;
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        g_nsm = nsm;
+    }
+    prepare_one(k_walk32<true, true, false, true>); prepare_one(k_walk32<true, true, false, false>);
+    prepare_one(k_walk32<true, false, false, true>); prepare_one(k_walk32<true, false, false, false>);
+    prepare_one(k_walk32<false, true, false, true>); prepare_one(k_walk32<false, true, false, false>);
+    prepare_one(k_walk32<false, false, false, true>); prepare_one(k_walk32<false, false, false, false>);
+    prepare_one(k_walk32<true, true, false, true, true>); prepare_one(k_walk32<true, true, false, false, true>);
+    prepare_one(k_walk32<true, false, false, true, true>); prepare_one(k_walk32<true, false, false, false, true>);
+    prepare_one(k_walk32_learn<true, true>); prepare_one(k_walk32_learn<true, false>);
+    prepare_one(k_walk32_learn<false, true>); prepare_one(k_walk32_learn<false, false>);
+    prepare_one(k_walk64<true, true, true>); prepare_one(k_walk64<true, true, false>);
+    prepare_one(k_walk64<true, false, true>); prepare_one(k_walk64<true, false, false>);
+    prepare_one(k_walk64<false, true, true>); prepare_one(k_walk64<false, true, false>);
+    prepare_one(k_walk64<false, false, true>); prepare_one(k_walk64<false, false, false>);
+    prepare_one(k_collide<true>);
+    prepare_one(k_collide<false>);
+    return g_nsm;
 }
 
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
@@ -765,30 +921,32 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     const bool inside = C.theta2 > (1.0 / 3.0);
     const bool quad = C.quadrupole != 0;
     const bool soft = C.soft2 > 0.0;
-    const int grid = ceil_div(T.cap_n, block);
-    const size_t sm_tgt = 0;   // no dynamic shared memory
     A.img = T.img;
-    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s);
-#define RB_W32(Q, I, PO, S) k_walk32<Q, I, PO, S><<<grid, block, sm_tgt, s>>>(A)
-#define RB_W64(Q, I, PO) k_walk64<Q, I, PO><<<grid, block, 0, s>>>(A)
+    A.tq = T.tq;
+    A.nq = T.nq;
+    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s, T.tq, T.nq);
+    // every kernel below runs the persistent grid that fits on the GPU
+#define RB_LAUNCH(...) __VA_ARGS__<<<persistent_grid(__VA_ARGS__, block, T.cap_n), block, 0, s>>>(A)
+#define RB_W32(Q, I, PO, S) RB_LAUNCH(k_walk32<Q, I, PO, S>)
+#define RB_W64(Q, I, PO) RB_LAUNCH(k_walk64<Q, I, PO>)
     if (learn && !potential) {
         // FP32 walk with the learned correction of band cells (quadrupole on)
         A.band_scale = learn->band_scale;
         if (inside) {
-            if (soft) k_walk32_learn<true, true><<<grid, block, sm_tgt, s>>>(A);
-            else k_walk32_learn<true, false><<<grid, block, sm_tgt, s>>>(A);
+            if (soft) RB_LAUNCH(k_walk32_learn<true, true>);
+            else RB_LAUNCH(k_walk32_learn<true, false>);
         } else {
-            if (soft) k_walk32_learn<false, true><<<grid, block, sm_tgt, s>>>(A);
-            else k_walk32_learn<false, false><<<grid, block, sm_tgt, s>>>(A);
+            if (soft) RB_LAUNCH(k_walk32_learn<false, true>);
+            else RB_LAUNCH(k_walk32_learn<false, false>);
         }
     } else if (rec) {
         // FP32 walk that also records accepted band cells (quadrupole on)
         if (inside) {
-            if (soft) k_walk32<true, true, false, true, true><<<grid, block, sm_tgt, s>>>(A);
-            else k_walk32<true, true, false, false, true><<<grid, block, sm_tgt, s>>>(A);
+            if (soft) RB_LAUNCH(k_walk32<true, true, false, true, true>);
+            else RB_LAUNCH(k_walk32<true, true, false, false, true>);
         } else {
-            if (soft) k_walk32<true, false, false, true, true><<<grid, block, sm_tgt, s>>>(A);
-            else k_walk32<true, false, false, false, true><<<grid, block, sm_tgt, s>>>(A);
+            if (soft) RB_LAUNCH(k_walk32<true, false, false, true, true>);
+            else RB_LAUNCH(k_walk32<true, false, false, false, true>);
         }
     } else if (walk_mode == 0 || potential) {
         if (quad) {
@@ -823,9 +981,12 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
     A.half_step_offset = half_step_offset; A.t0 = C.t0; A.half_dt = C.half_dt;
     A.img = T.img;
-    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s);
-    if (aabb) k_collide<true><<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
-    else k_collide<false><<<ceil_div(T.cap_n, block), block, 0, s>>>(A);
+    A.tq = T.tq;
+    A.nq = T.nq;
+    A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s, T.tq, T.nq);
+    if (aabb) RB_LAUNCH(k_collide<true>);
+    else RB_LAUNCH(k_collide<false>);
+#undef RB_LAUNCH
 }
 
 }  // namespace rb
