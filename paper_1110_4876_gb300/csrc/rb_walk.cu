@@ -231,7 +231,9 @@ __device__ __forceinline__ void learn_flush(LearnQ& Q, const mlp::Packed& w, int
     __syncwarp();
 }
 
-template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord, bool kLearn>
+// kOne: a single box, so every lane's walk ends at the same entry and no
+// lane can run into another box's tree.
+template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord, bool kLearn, bool kOne = false>
 __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp::Packed* W, int wbase,
                                        int n) {
     const int lane = threadIdx.x & 31;
@@ -274,7 +276,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                 bool want = false;    // kLearn: this lane accepted a band cell this iteration
                 float fin[12], funit = 0.f;
                 for (;;) {
-                    if (next >= wend) next = kEnd;
+                    if (!kOne && next >= wend) next = kEnd;
                     if ((++it & 15) == 0) {   // warp-uniform flush into the compensated sums
                         kadd(sx, cx, fx);
                         kadd(sy, cy, fy);
@@ -282,7 +284,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                         fx = fy = fz = 0.f;
                     }
                     const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
-                    if (e == kEnd) break;
+                    if (kOne ? e >= wend : e == kEnd) break;
                     const float4 ra = __ldg(&A.ra[e]);
                     const float4 rb = __ldg(&A.rb[e]);
                     const bool act = next == e;
@@ -494,12 +496,12 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
     }
 }
 
-template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false>
+template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord = false, bool kOne = false>
 __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
     for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile))
-        walk32<kQuad, kInside, kPot, kSoft, kRecord, false>(A, nullptr, nullptr, t << 5, n);
+        walk32<kQuad, kInside, kPot, kSoft, kRecord, false, kOne>(A, nullptr, nullptr, t << 5, n);
 }
 
 // Learned walk: the network's weights and one queue per warp in shared
@@ -874,6 +876,14 @@ int walk_prepare() {
     prepare_one(k_walk32<true, false, false, true>); prepare_one(k_walk32<true, false, false, false>);
     prepare_one(k_walk32<false, true, false, true>); prepare_one(k_walk32<false, true, false, false>);
     prepare_one(k_walk32<false, false, false, true>); prepare_one(k_walk32<false, false, false, false>);
+    prepare_one(k_walk32<true, true, false, true, false, true>);
+    prepare_one(k_walk32<true, true, false, false, false, true>);
+    prepare_one(k_walk32<true, false, false, true, false, true>);
+    prepare_one(k_walk32<true, false, false, false, false, true>);
+    prepare_one(k_walk32<false, true, false, true, false, true>);
+    prepare_one(k_walk32<false, true, false, false, false, true>);
+    prepare_one(k_walk32<false, false, false, true, false, true>);
+    prepare_one(k_walk32<false, false, false, false, false, true>);
     prepare_one(k_walk32<true, true, false, true, true>); prepare_one(k_walk32<true, true, false, false, true>);
     prepare_one(k_walk32<true, false, false, true, true>); prepare_one(k_walk32<true, false, false, false, true>);
     prepare_one(k_walk32_learn<true, true>); prepare_one(k_walk32_learn<true, false>);
@@ -927,7 +937,11 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s, T.tq, T.nq);
     // every kernel below runs the persistent grid that fits on the GPU
 #define RB_LAUNCH(...) __VA_ARGS__<<<persistent_grid(__VA_ARGS__, block, T.cap_n), block, 0, s>>>(A)
-#define RB_W32(Q, I, PO, S) RB_LAUNCH(k_walk32<Q, I, PO, S>)
+#define RB_W32(Q, I, PO, S)                                          \
+    do {                                                             \
+        if (C.nbox == 1) RB_LAUNCH(k_walk32<Q, I, PO, S, false, true>); \
+        else RB_LAUNCH(k_walk32<Q, I, PO, S>);                        \
+    } while (0)
 #define RB_W64(Q, I, PO) RB_LAUNCH(k_walk64<Q, I, PO>)
     if (learn && !potential) {
         // FP32 walk with the learned correction of band cells (quadrupole on)
