@@ -414,7 +414,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 2);
         build_topology(s->T, s->P[c], s->ctl, s->d_boxes, s->C, st);
         mark(s, 3);
-        build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st);
+        build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st, true);
         mark(s, 4);
         if (s->cfg.walk == RB_WALK_FP32_LEARNED) {
             // walk at theta; accepted cells with w/R > theta_fb get the
@@ -576,7 +576,7 @@ int gravity_now(rb_sim* s, bool potential) {
     if (learned && !s->mlp_loaded) return fail(s, RB_ERR_STATE, "the learned walk needs rb_load_mlp first");
     rebuild_now(s);
     const bool fp64 = potential || s->cfg.walk == RB_WALK_FP64;
-    build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
+    build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream, true);
     clear_walk_stats(s->ctl, s->stream);
     if (learned) {
         cudaMemsetAsync(&s->ctl->req_count, 0, sizeof(int), s->stream);
@@ -1105,7 +1105,7 @@ int rb_autotune(rb_sim* s, int use_cache) {
     if (s->cfg.gravity) {
         rebuild_now(s);
         const bool fp64 = s->cfg.walk == RB_WALK_FP64;
-        build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream);
+        build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream, true);
         const bool learned = s->cfg.walk == RB_WALK_FP32_LEARNED && s->mlp_loaded;
         const WalkLearn L = learn_args(s);
         float best = 1e30f;

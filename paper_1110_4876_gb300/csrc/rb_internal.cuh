@@ -199,8 +199,11 @@ size_t scan_part_words(int ncap);
 // rb_tree.cu
 void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                     cudaStream_t s);
+// Moments and walk records.  fp64: FP64 records only (FP64 walk, potential);
+// otherwise FP64 and FP32 records, and with f32q the quadrupole is summed in
+// FP32 (the FP64 quadrupole records then hold its FP32 values).
 void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
-                           const SimC& C, bool fp64, cudaStream_t s);
+                           const SimC& C, bool fp64, cudaStream_t s, bool f32q = false);
 // Collision records on the tree of the last gravity build at the current
 // positions (cells as FP32 boxes of their particles); for collision_search
 // with aabb = true.

@@ -290,67 +290,129 @@ __global__ void __launch_bounds__(256) k_level_fill(const int8_t* __restrict__ e
 }
 
 // The cells of one depth.  A cell's moments come from its children (deeper
-// cells, done by earlier launches, or particles): M = sum M_c, centre of
-// mass = sum M_c com_c / M, Q = sum [Q_c + M_c (3 d d^T - |d|^2 I)],
-// d = com_c - com (the traceless quadrupole about the centre of mass, by the
-// parallel-axis theorem).
+// cells, done by earlier launches, or particle leaves) in one pass: about the
+// first child's position o, M = sum M_c, S = sum M_c d_c and
+// Q_o = sum [Q_c + M_c (3 d_c d_c^T - |d_c|^2 I)], d_c = com_c - o; then the
+// centre of mass is o + S / M and the parallel-axis theorem moves Q_o to it:
+// Q = Q_o - M (3 s s^T - |s|^2 I), s = S / M (the traceless quadrupole about
+// the centre of mass, reading R3).  Every |d_c| and |s| is below the cell's
+// diagonal, so no term is much larger than the result.
+// kF32Q: the quadrupole is only needed by the FP32 walk, so it is summed in
+// FP32 on the hi/lo records (d_c good to ~1e-7 relative); mass and centre of
+// mass stay FP64.  On GB300 FP64 instructions cost 64 times FP32 ones.
+template <bool kF32Q>
 __global__ void __launch_bounds__(256) k_moments_level(GravRecArgs A, const int32_t* __restrict__ lvl,
                                                        const int32_t* __restrict__ list, int depth) {
     const int cnt = lvl[depth], off = lvl[32 + depth];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const int k = list[off + t];
         const int end = A.e_skip[k];
+        const double4_32a a0 = A.d_a[k + 1];
+        const double ox = a0.x, oy = a0.y, oz = a0.z;
+        float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), l0 = h0;
+        if (kF32Q) {
+            h0 = A.ra[k + 1];
+            l0 = A.rb[k + 1];
+        }
         double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        double q[6] = {0, 0, 0, 0, 0, 0};
+        float qf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int c = k + 1; c < end; c = A.e_skip[c]) {
-            double mc, px, py, pz;
-            child_mass_pos(A, c, mc, px, py, pz);
+            const double4_32a a = A.d_a[c];
+            const bool leaf = __double_as_longlong(a.w) < 0;   // leaf records hold -m (m >= 0)
+            const double mc = leaf ? -a.w : A.d_q0[c].x;
+            const double dx = a.x - ox, dy = a.y - oy, dz = a.z - oz;
             M += mc;
-            sx += mc * px;
-            sy += mc * py;
-            sz += mc * pz;
+            sx = fma(mc, dx, sx);
+            sy = fma(mc, dy, sy);
+            sz = fma(mc, dz, sz);
+            if (kF32Q) {
+                const float4 h = A.ra[c], l = A.rb[c];
+                const float fx = (h.x - h0.x) + (l.x - l0.x);
+                const float fy = (h.y - h0.y) + (l.y - l0.y);
+                const float fz = (h.z - h0.z) + (l.z - l0.z);
+                float fm;
+                if (leaf) {
+                    fm = -h.w;
+                } else {
+                    const float4 c0 = A.rq0[c], c1 = A.rq1[c];
+                    fm = c0.x;
+                    qf[0] += c0.y; qf[1] += c0.z; qf[2] += c0.w;
+                    qf[3] += c1.x; qf[4] += c1.y; qf[5] += c1.z;
+                }
+                const float d2 = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+                const float m3x = 3.f * fm * fx, m3y = 3.f * fm * fy;
+                qf[0] += fmaf(m3x, fx, -fm * d2);
+                qf[1] += fmaf(m3y, fy, -fm * d2);
+                qf[2] += fmaf(3.f * fm * fz, fz, -fm * d2);
+                qf[3] += m3x * fy;
+                qf[4] += m3x * fz;
+                qf[5] += m3y * fz;
+            } else {
+                if (!leaf) {
+                    const double4_32a c0 = A.d_q0[c], c1 = A.d_q1[c];
+                    q[0] += c0.y; q[1] += c0.z; q[2] += c0.w;
+                    q[3] += c1.x; q[4] += c1.y; q[5] += c1.z;
+                }
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                q[0] += mc * (3.0 * dx * dx - d2);
+                q[1] += mc * (3.0 * dy * dy - d2);
+                q[2] += mc * (3.0 * dz * dz - d2);
+                q[3] += mc * (3.0 * dx * dy);
+                q[4] += mc * (3.0 * dx * dz);
+                q[5] += mc * (3.0 * dy * dz);
+            }
         }
         const int v = depth;
         const int first = A.e_first[k];
         const BoxP bp = A.boxes[A.box[first]];
         const double w = ldexp(bp.L, -v);
-        double ix, iy, iz;
-        cell_index(A.key[first], v, ix, iy, iz);
         const double lo = -0.5 * bp.L;
-        double cx, cy, cz;
+        double ix = 0.0, iy = 0.0, iz = 0.0;
+        if (A.inside || !(M > 0.0)) cell_index(A.key[first], v, ix, iy, iz);
+        double cx, cy, cz, ux, uy, uz;   // centre of mass and its offset from o
         if (M > 0.0) {
-            cx = sx / M; cy = sy / M; cz = sz / M;
+            const double iM = 1.0 / M;
+            ux = sx * iM; uy = sy * iM; uz = sz * iM;
+            cx = ox + ux; cy = oy + uy; cz = oz + uz;
         } else {
+            // no source mass (test particles only): the geometric centre
             cx = lo + (ix + 0.5) * w; cy = lo + (iy + 0.5) * w; cz = lo + (iz + 0.5) * w;
+            ux = uy = uz = 0.0;
         }
-        double q[6] = {0, 0, 0, 0, 0, 0};
-        for (int c = k + 1; c < end; c = A.e_skip[c]) {
-            double mc;
-            double4_32a a;
-            child_mass_pos(A, c, mc, a.x, a.y, a.z);
-            if (A.e_level[c] != 22) {
-                const double4_32a q0 = A.d_q0[c];
-                const double4_32a q1 = A.d_q1[c];
-                q[0] += q0.y; q[1] += q0.z; q[2] += q0.w;
-                q[3] += q1.x; q[4] += q1.y; q[5] += q1.z;
-            }
-            const double dx = a.x - cx, dy = a.y - cy, dz = a.z - cz;
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            q[0] += mc * (3.0 * dx * dx - d2);
-            q[1] += mc * (3.0 * dy * dy - d2);
-            q[2] += mc * (3.0 * dz * dz - d2);
-            q[3] += mc * (3.0 * dx * dy);
-            q[4] += mc * (3.0 * dx * dz);
-            q[5] += mc * (3.0 * dy * dz);
+        if (kF32Q) {
+            const float fx = (float)ux, fy = (float)uy, fz = (float)uz, fm = (float)M;
+            const float d2 = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+            qf[0] -= fm * fmaf(3.f * fx, fx, -d2);
+            qf[1] -= fm * fmaf(3.f * fy, fy, -d2);
+            qf[2] -= fm * fmaf(3.f * fz, fz, -d2);
+            qf[3] -= 3.f * fm * fx * fy;
+            qf[4] -= 3.f * fm * fx * fz;
+            qf[5] -= 3.f * fm * fy * fz;
+#pragma unroll
+            for (int j = 0; j < 6; j++) q[j] = (double)qf[j];
+        } else {
+            const double d2 = ux * ux + uy * uy + uz * uz;
+            q[0] -= M * (3.0 * ux * ux - d2);
+            q[1] -= M * (3.0 * uy * uy - d2);
+            q[2] -= M * (3.0 * uz * uz - d2);
+            q[3] -= M * (3.0 * ux * uy);
+            q[4] -= M * (3.0 * ux * uz);
+            q[5] -= M * (3.0 * uy * uz);
         }
         const bool group = v == kMaxDepth;   // leaf group: never used as a multipole
         const double ww = w * w;
         A.d_a[k] = make_double4_32a(cx, cy, cz, group ? __longlong_as_double(0x7ff0000000000000ll) : ww);
         A.d_q0[k] = make_double4_32a(M, q[0], q[1], q[2]);
         A.d_q1[k] = make_double4_32a(q[3], q[4], q[5], w);
-        // cell corner lo + i w, rounded as two separate operations
-        const double c0x = __dadd_rn(lo, __dmul_rn(ix, w)), c0y = __dadd_rn(lo, __dmul_rn(iy, w));
-        const double c0z = __dadd_rn(lo, __dmul_rn(iz, w));
-        if (A.inside) A.d_c[k] = make_double4_32a(c0x, c0y, c0z, w);
+        double c0x = 0.0, c0y = 0.0, c0z = 0.0;
+        if (A.inside) {
+            // cell corner lo + i w, rounded as two separate operations
+            c0x = __dadd_rn(lo, __dmul_rn(ix, w));
+            c0y = __dadd_rn(lo, __dmul_rn(iy, w));
+            c0z = __dadd_rn(lo, __dmul_rn(iz, w));
+            A.d_c[k] = make_double4_32a(c0x, c0y, c0z, w);
+        }
         if (A.fp32) {
             float hx, lx, hy, ly, hz, lz;
             split_hilo(cx, hx, lx);
@@ -359,8 +421,13 @@ __global__ void __launch_bounds__(256) k_moments_level(GravRecArgs A, const int3
             const float crit = group ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
             A.ra[k] = make_float4(hx, hy, hz, crit);
             A.rb[k] = make_float4(lx, ly, lz, __int_as_float(end));
-            A.rq0[k] = make_float4((float)M, (float)q[0], (float)q[1], (float)q[2]);
-            A.rq1[k] = make_float4((float)q[3], (float)q[4], (float)q[5], 0.f);
+            if (kF32Q) {
+                A.rq0[k] = make_float4((float)M, qf[0], qf[1], qf[2]);
+                A.rq1[k] = make_float4(qf[3], qf[4], qf[5], 0.f);
+            } else {
+                A.rq0[k] = make_float4((float)M, (float)q[0], (float)q[1], (float)q[2]);
+                A.rq1[k] = make_float4((float)q[3], (float)q[4], (float)q[5], 0.f);
+            }
             if (A.inside) {
                 split_hilo(c0x, hx, lx);
                 split_hilo(c0y, hy, ly);
@@ -454,15 +521,19 @@ __global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t
         const float inf = __int_as_float(0x7f800000);
         float lox = inf, loy = inf, loz = inf, hix = -inf, hiy = -inf, hiz = -inf;
         for (int c = k + 1; c < end; c = A.e_skip[c]) {
-            if (A.e_level[c] == 22) {
-                const int p = A.e_first[c];
-                if (A.box[p] >= A.nbox) continue;
-                const double x = A.x[p], y = A.y[p], z = A.z[p];
-                lox = fminf(lox, __double2float_rd(x)); hix = fmaxf(hix, __double2float_ru(x));
-                loy = fminf(loy, __double2float_rd(y)); hiy = fmaxf(hiy, __double2float_ru(y));
-                loz = fminf(loz, __double2float_rd(z)); hiz = fmaxf(hiz, __double2float_ru(z));
+            const float4 a = A.ra[c], b = A.rb[c];
+            if (__float_as_int(a.w) < 0) {
+                // particle leaf: hi/lo floats of its position (hi = x rounded
+                // to nearest, lo the sign of x - hi), so x lies in
+                // [hi, next float up] or [next float down, hi]
+                if (a.x == inf) continue;   // removed particle
+                lox = fminf(lox, b.x < 0.f ? nextafterf(a.x, -inf) : a.x);
+                hix = fmaxf(hix, b.x > 0.f ? nextafterf(a.x, inf) : a.x);
+                loy = fminf(loy, b.y < 0.f ? nextafterf(a.y, -inf) : a.y);
+                hiy = fmaxf(hiy, b.y > 0.f ? nextafterf(a.y, inf) : a.y);
+                loz = fminf(loz, b.z < 0.f ? nextafterf(a.z, -inf) : a.z);
+                hiz = fmaxf(hiz, b.z > 0.f ? nextafterf(a.z, inf) : a.z);
             } else {
-                const float4 a = A.ra[c], b = A.rb[c];
                 lox = fminf(lox, a.x); loy = fminf(loy, a.y); loz = fminf(loz, a.z);
                 hix = fmaxf(hix, b.x); hiy = fmaxf(hiy, b.y); hiz = fmaxf(hiz, b.z);
             }
@@ -498,7 +569,7 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
 }
 
 void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
-                           const SimC& C, bool fp64, cudaStream_t s) {
+                           const SimC& C, bool fp64, cudaStream_t s, bool f32q) {
     const int n = T.cap_n;
     if (n <= 0) return;
     GravRecArgs A;
@@ -522,8 +593,11 @@ void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* b
     k_level_offsets<<<1, 1, 0, s>>>(T.lvl);
     k_level_fill<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_level, ctl, ne, T.lvl, T.e_arrive);
     const int grid = std::min(ceil_div(n, 256), 4 * 152);
-    for (int d = kMaxDepth; d >= 0; d--)
-        k_moments_level<<<grid, 256, 0, s>>>(A, T.lvl, T.e_arrive, d);
+    const bool q32 = f32q && !fp64;
+    for (int d = kMaxDepth; d >= 0; d--) {
+        if (q32) k_moments_level<true><<<grid, 256, 0, s>>>(A, T.lvl, T.e_arrive, d);
+        else k_moments_level<false><<<grid, 256, 0, s>>>(A, T.lvl, T.e_arrive, d);
+    }
 }
 
 void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
