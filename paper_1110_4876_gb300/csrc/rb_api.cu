@@ -268,9 +268,16 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.e_nchild, ecap, L); rc |= dalloc(s, &T.e_arrive, ecap, L);
         rc |= dalloc(s, &T.e_level, ecap, L);
         rc |= dalloc(s, &T.leaf_of, cap, L);
-        rc |= dalloc(s, &T.ra, ecap, L); rc |= dalloc(s, &T.rb, ecap, L);
-        rc |= dalloc(s, &T.rq0, ecap, L); rc |= dalloc(s, &T.rq1, ecap, L);
-        rc |= dalloc(s, &T.rc_hi, ecap, L); rc |= dalloc(s, &T.rc_lo, ecap, L);
+        {
+            // FP32 record pairs, each pair interleaved (Rec4)
+            float4 *rab = nullptr, *rq = nullptr, *rcc = nullptr;
+            rc |= dalloc(s, &rab, 2 * (size_t)ecap, L);
+            rc |= dalloc(s, &rq, 2 * (size_t)ecap, L);
+            rc |= dalloc(s, &rcc, 2 * (size_t)ecap, L);
+            T.ra.p = rab; T.rb.p = rab ? rab + 1 : nullptr;
+            T.rq0.p = rq; T.rq1.p = rq ? rq + 1 : nullptr;
+            T.rc_hi.p = rcc; T.rc_lo.p = rcc ? rcc + 1 : nullptr;
+        }
         rc |= dalloc(s, &T.d_a, ecap, L); rc |= dalloc(s, &T.d_q0, ecap, L);
         rc |= dalloc(s, &T.d_q1, ecap, L); rc |= dalloc(s, &T.d_c, ecap, L);
         rc |= dalloc(s, &T.box_first, s->nbox + 1, L);

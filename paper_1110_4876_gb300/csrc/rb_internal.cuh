@@ -90,6 +90,14 @@ struct ImgTab {
 };
 
 // Tree and scratch buffers of one build (sized for capacity n).
+// One of two float4 records that an entry keeps side by side, so that the
+// pair read together (e.g. centre of mass hi and lo) is one 32-byte sector:
+// a view with stride 2 over the interleaved array.
+struct Rec4 {
+    float4* p = nullptr;
+    __host__ __device__ float4& operator[](long long i) const { return p[2 * i]; }
+};
+
 struct Tree {
     uint64_t *key, *key_alt;    // sort keys (ping-pong)
     uint32_t *idx, *idx_alt;    // sort values: slot in the unsorted set
@@ -104,8 +112,8 @@ struct Tree {
     int8_t* e_level;            // depth of a cell; 22 marks a particle leaf
     int32_t* leaf_of;           // per particle: its leaf entry
     double *M, *cx, *cy, *cz, *Q;   // FP64 moments per entry (Q: 6 x cap, xx yy zz xy xz yz)
-    float4 *ra, *rb, *rq0, *rq1;    // FP32 walk records
-    float4 *rc_hi, *rc_lo;          // FP32 cell corner (hi/lo) + width, inside test
+    Rec4 ra, rb, rq0, rq1;          // FP32 walk records (pairs ra/rb, rq0/rq1 interleaved)
+    Rec4 rc_hi, rc_lo;              // FP32 cell corner (hi/lo) + width, inside test
     double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
     int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
     int32_t* lvl;                   // per-depth cell counts / offsets / cursors (96)

@@ -200,7 +200,7 @@ struct GravRecArgs {
     const int8_t* e_level;
     int32_t* e_arrive;
     double4_32a *d_a, *d_q0, *d_q1, *d_c;
-    float4 *ra, *rb, *rq0, *rq1, *rc_hi, *rc_lo;
+    Rec4 ra, rb, rq0, rq1, rc_hi, rc_lo;
     const Ctl* ctl;
     int ncap;
     double crit_scale;  // 1 / theta^2
@@ -446,7 +446,7 @@ struct CollRecArgs {
     const BoxP* boxes;
     const int32_t *e_first, *e_skip, *leaf_of;
     const int8_t* e_level;
-    float4 *ra, *rb;
+    Rec4 ra, rb;
     const Ctl* ctl;
     int ecap, ncap, nbox;
     double rmax;

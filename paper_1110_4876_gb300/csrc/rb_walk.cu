@@ -31,7 +31,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct GravArgs {
     const double *x, *y, *z;
     const int32_t* box;
-    const float4 *ra, *rb, *rq0, *rq1, *rc_hi, *rc_lo;
+    Rec4 ra, rb, rq0, rq1, rc_hi, rc_lo;
     const double4_32a *d_a, *d_q0, *d_q1, *d_c;
     const int32_t *e_skip, *leaf_of, *box_root;
     const BoxP* boxes;
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(kMaxWalkBlock) k_walk64(GravArgs A) {
 struct CollArgs {
     const double *x, *y, *z, *r;
     const int32_t *id, *box;
-    const float4 *ra, *rb;
+    Rec4 ra, rb;
     const int32_t *box_root, *e_skip;
     const BoxP* boxes;
     Ctl* ctl;
