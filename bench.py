@@ -192,7 +192,7 @@ def run_ours(args):
     # ---- device-resident throughput (inputs already in HBM) ----
     walk_ms, walk_flops, stage_sum = [], [], {}
     launches = 0
-    pairs, corr = [], []
+    pairs, corr, counts = [], [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -209,6 +209,8 @@ def run_ours(args):
             launches += st["kernels_per_step"]
             pairs.append(st["pairs_found"])
             corr.append(st["corrections"])
+            counts.append((st["cell_interactions"], st["leaf_interactions"], st["mac_tests"],
+                           st["warp_iterations"]))
         e1.record(stream)
         barrier()
     t_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
@@ -264,6 +266,13 @@ def run_ours(args):
                     f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
                     "(MEASURED_PEAKS.json sm_max_mhz)",
                 "flops_per_launch": statistics.mean(walk_flops), "ms_per_launch": wms}
+    ncell, nleaf, nmac, niter = (statistics.mean(c[k] for c in counts) for k in range(4))
+    roofline["per_particle"] = {"cells": ncell / N_SHEET, "leaves": nleaf / N_SHEET,
+                                "opening_tests": nmac / N_SHEET}
+    if niter > 0:
+        # entries a lane evaluates / entries the warps step through x 32 lanes
+        roofline["warp_iterations_per_launch"] = niter
+        roofline["lane_utilisation"] = (nleaf + nmac) / (32.0 * niter)
     if args.walk == "learned":
         # tensor-core work of the network: 2 (12 64 + 2 64 64 + 64 3) flops per corrected cell
         mlp = FLOP_MLP * statistics.mean(corr)

@@ -104,6 +104,8 @@ typedef struct rb_stats_t {
      * 9 collision search, 10 pair sort, 11 resolution */
     double  ms_stage[12];
     int64_t corrections;      /* learned walk: band cells corrected by the network in the last walk */
+    int64_t warp_iterations;  /* FP32 walk: entries processed by warps (32 targets each) in the
+                                 last walk; (leaf + mac) / (32 x this) is the lane utilisation */
 } rb_stats_t;
 
 typedef struct rb_sim rb_sim; /* opaque, owned by the library */

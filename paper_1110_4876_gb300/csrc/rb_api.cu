@@ -1041,6 +1041,7 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     out->search_block = s->search_block;
     for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
     out->corrections = s->cfg.walk == RB_WALK_FP32_LEARNED ? c.req_count : 0;
+    out->warp_iterations = (int64_t)c.n_iter;
     return RB_OK;
 }
 

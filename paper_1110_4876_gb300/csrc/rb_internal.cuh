@@ -75,6 +75,7 @@ struct Ctl {
     int out_live;              // host exchange: live particles of the box read out
     int pad_;
     unsigned long long n_cell, n_leaf, n_mac, n_recheck;
+    unsigned long long n_iter;        // warp iterations of the last FP32 walk (entries visited)
     unsigned long long sweep_wbits;   // plane sweep: largest half extent (double bits)
 };
 constexpr int kErrNonFinite = 1;

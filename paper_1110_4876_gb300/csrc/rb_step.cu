@@ -583,7 +583,7 @@ void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int
 void step_advance(Ctl* ctl, cudaStream_t s) { k_step_advance<<<1, 1, 0, s>>>(ctl); }
 
 void clear_walk_stats(Ctl* ctl, cudaStream_t s) {
-    cudaMemsetAsync(&ctl->n_cell, 0, 4 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(&ctl->n_cell, 0, 5 * sizeof(unsigned long long), s);
 }
 
 }  // namespace rb

@@ -256,6 +256,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
     double pot = 0.0;
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;  // sums + compensation
     int ncell = 0, nleaf = 0, nmac = 0, nrecheck = 0, ncorr = 0;
+    int iters = 0;   // entries processed by the warp (warp-uniform)
     int qn = 0;   // kLearn: rows waiting in this warp's queue (warp-uniform)
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
@@ -446,6 +447,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                 kadd(sy, cy, fy);
                 kadd(sz, cz, fz);
                 pot += (double)fp;
+                iters += it - 1;
             }
     if (kLearn && qn > 0) {
         // the last partial tile: empty rows have zero inputs and no owner
@@ -487,6 +489,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
         atomicAdd(&A.ctl->n_leaf, c1);
         atomicAdd(&A.ctl->n_mac, c2);
         atomicAdd(&A.ctl->n_recheck, c3);
+        atomicAdd(&A.ctl->n_iter, (unsigned long long)iters);
     }
     if (kLearn) {
         int c4 = ncorr;

@@ -60,7 +60,7 @@ class rb_stats_t(C.Structure):
         ("mac_tests", C.c_int64), ("fp64_rechecks", C.c_int64), ("pair_capacity", C.c_int64),
         ("kernels_per_step", C.c_int64), ("walk_block", C.c_int64), ("search_block", C.c_int64),
         ("t", C.c_double), ("ms_last_step", C.c_double), ("ms_stage", C.c_double * 12),
-        ("corrections", C.c_int64),
+        ("corrections", C.c_int64), ("warp_iterations", C.c_int64),
     ]
 
 
