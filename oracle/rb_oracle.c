@@ -882,7 +882,10 @@ int64_t orc_collide_sweep(const orc_params* p, double t, int64_t n, const double
 /* Resolution of the collision queue (Sect. 5, Eq. 2; reading R8): pairs in
  * ascending key order; a pair is skipped unless the particles approach; the
  * relative normal velocity is multiplied by -eps and momentum is conserved.
- * Later pairs see the velocities left by earlier ones. */
+ * Later pairs see the velocities left by earlier ones.  With u = v_b - v_a
+ * and r = x_b - x_a, the normal velocity changes by -(1 + eps) (u.r)/|r|, so
+ * v_a gains (1 + eps) (m_b/M) (u.r)/|r|^2 r and v_b loses the same with m_a
+ * (M = m_a + m_b): the impulse along n = r/|r| written without forming n. */
 void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, const double* y,
                  const double* z, double* vx, double* vy, double* vz, const double* m,
                  const int64_t* id, int64_t npairs, const uint64_t* keys) {
@@ -903,19 +906,18 @@ void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, cons
         double ux = vx[b] - vx[a], uy = (vy[b] + dvg) - vy[a], uz = vz[b] - vz[a];
         double rv = (rx * ux + ry * uy) + rz * uz;
         if (rv >= 0.0) continue; /* not approaching */
-        double rr = sqrt((rx * rx + ry * ry) + rz * rz);
-        double nx = rx / rr, ny = ry / rr, nz = rz / rr;
-        double vn = (ux * nx + uy * ny) + uz * nz;
+        double r2 = (rx * rx + ry * ry) + rz * rz;
         double e = p->eps;
-        if (p->eps_law == 1) { /* reading V1 */
+        if (p->eps_law == 1) { /* reading V1: |v_n| = |u.r| / |r| */
+            double vn = rv / sqrt(r2);
             double q = pow(fabs(vn) / p->eps_vc, -p->eps_p);
             e = q < 1.0 ? q : 1.0;
         }
-        double dlt = -(1.0 + e) * vn;
         double mt = m[a] + m[b];
-        double fa = (m[b] / mt) * dlt, fb = (m[a] / mt) * dlt;
-        vx[a] = vx[a] - fa * nx; vy[a] = vy[a] - fa * ny; vz[a] = vz[a] - fa * nz;
-        vx[b] = vx[b] + fb * nx; vy[b] = vy[b] + fb * ny; vz[b] = vz[b] + fb * nz;
+        double g = ((1.0 + e) * rv) / (r2 * mt);
+        double ga = g * m[b], gb = g * m[a];
+        vx[a] = vx[a] + ga * rx; vy[a] = vy[a] + ga * ry; vz[a] = vz[a] + ga * rz;
+        vx[b] = vx[b] - gb * rx; vy[b] = vy[b] - gb * ry; vz[b] = vz[b] - gb * rz;
     }
     free(slot);
 }

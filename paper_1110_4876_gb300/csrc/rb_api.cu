@@ -113,6 +113,14 @@ int fail(rb_sim* s, int code, const std::string& msg) {
             return fail(sim, RB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Bits of the largest pair key (id_a << 36 | id_b << 12 | image code): ids
+// are below the particle capacity, so the sort skips the digits above them.
+int pair_key_bits(const rb_sim* s) {
+    int b = 1;
+    while (b < 24 && (1 << b) < s->ncap) b++;
+    return std::min(60, 36 + b);
+}
+
 template <typename T>
 int dalloc(rb_sim* s, T** p, size_t count, std::vector<void*>& list) {
     void* q = nullptr;
@@ -449,7 +457,7 @@ int record_step(rb_sim* s, int p) {
         for (int k = 7; k <= 9; k++) mark(s, k);
         sweep_search(s->P[c], s->ctl, s->d_boxes, s->C, s->SW, s->PR, 2, s->ncap, st);
         mark(s, 10);
-        sort_pairs(s->PR, s->ctl, st);
+        sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
         resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
     } else if (s->cfg.collisions && s->cfg.gravity) {
@@ -462,7 +470,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 9);
         collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block, true);
         mark(s, 10);
-        sort_pairs(s->PR, s->ctl, st);
+        sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
         resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
     } else if (s->cfg.collisions) {
@@ -475,7 +483,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 9);
         collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block);
         mark(s, 10);
-        sort_pairs(s->PR, s->ctl, st);
+        sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
         resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
     } else {
@@ -539,7 +547,7 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve, bool aabb) {
         else
             collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
                              s->search_block, aabb);
-        sort_pairs(s->PR, s->ctl, s->stream);
+        sort_pairs(s->PR, s->ctl, s->stream, pair_key_bits(s));
         if (read_ctl(s)) return RB_ERR_CUDA;
         if (s->hctl.err & kErrSweepLong)
             return fail(s, RB_ERR_CAPACITY, "plane sweep: a trajectory overlaps more than 65536 others in x "
@@ -954,7 +962,7 @@ int rb_get_pairs(rb_sim* s, int box, int64_t cap, int64_t* n, int64_t* id_a, int
     if (read_ctl(s)) return RB_ERR_CUDA;
     const int np = s->hctl.pair_n;
     std::vector<uint64_t> keys;
-    if (d2h(s, keys, s->PR.key, np)) return RB_ERR_CUDA;
+    if (d2h(s, keys, s->PR.sorted(), np)) return RB_ERR_CUDA;
     const int64_t lo = s->base[box];
     const int64_t hi = lo + s->hb[box].n;
     int64_t k = 0;

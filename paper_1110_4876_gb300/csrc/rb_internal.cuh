@@ -139,6 +139,8 @@ struct Pairs {
     int32_t* slot_of_id;       // global id -> slot in the current set
     uint32_t *hist, *ehist;
     int cap;
+    bool sorted_alt = false;   // the last pair sort left the sorted keys in key_alt
+    const uint64_t* sorted() const { return sorted_alt ? key_alt : key; }
 };
 
 // Plane-sweep items (trajectory x extents, Sect. 5.3) and their sort buffers.
@@ -284,7 +286,8 @@ void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl*
                       const SimC& C, int ncap, int box_bits, cudaStream_t s);
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
                    int half_step_offset, int rounds, ImgTab* img, cudaStream_t s);
-void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s);
+// key_bits: bits of the largest pair key, 36 + the bits of the largest id
+void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s, int key_bits = 60);
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
                   double* partials, int nparts, double* out7, cudaStream_t s);
 void step_advance(Ctl* ctl, cudaStream_t s);

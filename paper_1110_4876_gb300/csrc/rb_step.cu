@@ -229,26 +229,27 @@ __device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C,
                  uz = __dsub_rn(vzb, vza);
     const double rv = __dadd_rn(__dadd_rn(__dmul_rn(rx, ux), __dmul_rn(ry, uy)), __dmul_rn(rz, uz));
     if (rv >= 0.0) return false;
-    const double rr =
-        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz)));
-    const double nx = __ddiv_rn(rx, rr), ny = __ddiv_rn(ry, rr), nz = __ddiv_rn(rz, rr);
-    const double vn = __dadd_rn(__dadd_rn(__dmul_rn(ux, nx), __dmul_rn(uy, ny)), __dmul_rn(uz, nz));
+    // the impulse along n = r/|r| without forming n: v_a gains
+    // (1 + eps) (m_b/M) (u.r)/|r|^2 r, v_b loses the same with m_a (one
+    // division, no square root: GB300's FP64 rate is 1/64 of FP32)
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
     double e = C.eps;
     if (C.eps_law == 1) {
-        // velocity-dependent restitution: min(1, (|v_n| / v_c)^(-p))
+        // velocity-dependent restitution: min(1, (|v_n| / v_c)^(-p)), |v_n| = |u.r| / |r|
+        const double vn = __ddiv_rn(rv, __dsqrt_rn(r2));
         const double q = pow(__ddiv_rn(fabs(vn), C.eps_vc), -C.eps_p);
         e = q < 1.0 ? q : 1.0;
     }
-    const double dlt = __dmul_rn(-__dadd_rn(1.0, e), vn);
     const double ma = A.P.m[a], mb = A.P.m[b];
     const double mt = __dadd_rn(ma, mb);
-    const double fa = __dmul_rn(__ddiv_rn(mb, mt), dlt), fb = __dmul_rn(__ddiv_rn(ma, mt), dlt);
-    A.P.vx[a] = __dsub_rn(vxa, __dmul_rn(fa, nx));
-    A.P.vy[a] = __dsub_rn(vya, __dmul_rn(fa, ny));
-    A.P.vz[a] = __dsub_rn(vza, __dmul_rn(fa, nz));
-    A.P.vx[b] = __dadd_rn(vxb, __dmul_rn(fb, nx));
-    A.P.vy[b] = __dadd_rn(vyb, __dmul_rn(fb, ny));
-    A.P.vz[b] = __dadd_rn(vzb, __dmul_rn(fb, nz));
+    const double gi = __ddiv_rn(__dmul_rn(__dadd_rn(1.0, e), rv), __dmul_rn(r2, mt));
+    const double ga = __dmul_rn(gi, mb), gb = __dmul_rn(gi, ma);
+    A.P.vx[a] = __dadd_rn(vxa, __dmul_rn(ga, rx));
+    A.P.vy[a] = __dadd_rn(vya, __dmul_rn(ga, ry));
+    A.P.vz[a] = __dadd_rn(vza, __dmul_rn(ga, rz));
+    A.P.vx[b] = __dsub_rn(vxb, __dmul_rn(gb, rx));
+    A.P.vy[b] = __dsub_rn(vyb, __dmul_rn(gb, ry));
+    A.P.vz[b] = __dsub_rn(vzb, __dmul_rn(gb, rz));
     return true;
 }
 
@@ -535,20 +536,18 @@ void reset_slots(const PSet& P, int32_t* slot_of_id, int n, int ncap, int nbox, 
     if (ncap > 0) k_reset_slots<<<ceil_div(ncap, 256), 256, 0, s>>>(P, slot_of_id, n, ncap, nbox);
 }
 
-void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s) {
+void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s, int key_bits) {
     k_pairs_prep<<<1, 1, 0, s>>>(ctl, PR.cap);
-    const int which = radix_sort(PR.key, PR.val, PR.key_alt, PR.val_alt, PR.cap, &ctl->pair_n, 60,
-                                 nullptr, 0, PR.hist, s);
-    if (which == 1) {
-        uint64_t* k = PR.key; PR.key = PR.key_alt; PR.key_alt = k;
-        uint32_t* v = PR.val; PR.val = PR.val_alt; PR.val_alt = v;
-    }
+    // an odd number of passes leaves the keys in key_alt; the buffers are
+    // not swapped, so every captured graph finds them in the same place
+    PR.sorted_alt = radix_sort(PR.key, PR.val, PR.key_alt, PR.val_alt, PR.cap, &ctl->pair_n,
+                               key_bits, nullptr, 0, PR.hist, s) == 1;
 }
 
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
                    int half_step_offset, int rounds, ImgTab* img, cudaStream_t s) {
     ResolveArgs A;
-    A.P = P; A.key = PR.key; A.slot_of_id = PR.slot_of_id;
+    A.P = P; A.key = PR.sorted(); A.slot_of_id = PR.slot_of_id;
     A.prev_a = PR.prev_a; A.prev_b = PR.prev_b; A.rdone = PR.rdone;
     A.next_a = PR.next_a; A.next_b = PR.next_b; A.wait = PR.wait;
     A.img = img;
