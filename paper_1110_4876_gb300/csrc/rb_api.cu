@@ -468,7 +468,8 @@ int record_step(rb_sim* s, int p) {
         mark(s, 8);
         build_collision_aabb(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
         mark(s, 9);
-        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block, true);
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block, true,
+                         s->rmax);
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
@@ -546,7 +547,7 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve, bool aabb) {
             sweep_search(s->P[c], s->ctl, s->d_boxes, s->C, s->SW, s->PR, hs, s->ncap, s->stream);
         else
             collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
-                             s->search_block, aabb);
+                             s->search_block, aabb, s->rmax);
         sort_pairs(s->PR, s->ctl, s->stream, pair_key_bits(s));
         if (read_ctl(s)) return RB_ERR_CUDA;
         if (s->hctl.err & kErrSweepLong)
@@ -1151,7 +1152,7 @@ int rb_autotune(rb_sim* s, int use_cache) {
             const float ms = time_best(s, [&] {
                 cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream);
                 collision_search(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->PR, 0, s->stream, b,
-                                 aabb);
+                                 aabb, s->rmax);
             });
             if (ms < best) { best = ms; sb = b; }
         }

@@ -269,9 +269,10 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
                   bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128,
                   const WalkLearn* learn = nullptr);
+// aabb: the records of build_collision_aabb, with rmax the largest radius.
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                       const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128,
-                      bool aabb = false);
+                      bool aabb = false, double rmax = 0.0);
 
 // rb_sweep.cu: plane-sweep search on set P at half-step offset hs; the
 // canonical pair keys are appended to PR like the tree search's.

@@ -207,21 +207,6 @@ struct GravRecArgs {
     bool fp32, inside;
 };
 
-// Mass and position of a child entry: a particle leaf is read from the
-// particle arrays, a cell from the records an earlier (deeper) level wrote.
-__device__ __forceinline__ void child_mass_pos(const GravRecArgs& A, int c, double& m, double& x,
-                                               double& y, double& z) {
-    if (A.e_level[c] == 22) {
-        const int j = A.e_first[c];
-        m = A.has_test ? source_mass(A.boxes[A.box[j]], A.id[j], A.m[j]) : A.m[j];
-        x = A.x[j]; y = A.y[j]; z = A.z[j];
-    } else {
-        const double4_32a a = A.d_a[c];
-        m = A.d_q0[c].x;
-        x = a.x; y = a.y; z = a.z;
-    }
-}
-
 // Leaf records (FP64 and FP32) of every particle.
 __global__ void __launch_bounds__(256) k_leaf_records(GravRecArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
@@ -490,8 +475,11 @@ __global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
 // tree's cells still hold the same particles, and a cell records the
 // axis-aligned box of its particles' current positions (lower corner rounded
 // down, upper corner rounded up to FP32), so the search stays exact without a
-// second sort and build.  Leaves as in k_coll_records; a removed particle's
-// leaf sits at +infinity and is never close.
+// second sort and build.  A cell's record also holds the largest particle
+// slot below it (ra.w), so a search from slot i skips subtrees whose pairs
+// with i are examined from the other particle.  Leaves as in
+// k_coll_records; a removed particle's leaf sits at +infinity and is never
+// close.
 __global__ void __launch_bounds__(256) k_aabb_leaves(CollRecArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -514,12 +502,12 @@ __global__ void __launch_bounds__(256) k_aabb_leaves(CollRecArgs A) {
 __global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t* __restrict__ lvl,
                                                     const int32_t* __restrict__ list, int depth) {
     const int cnt = lvl[depth], off = lvl[32 + depth];
-    const float rmaxf = __double2float_ru(A.rmax);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const int k = list[off + t];
         const int end = A.e_skip[k];
         const float inf = __int_as_float(0x7f800000);
         float lox = inf, loy = inf, loz = inf, hix = -inf, hiy = -inf, hiz = -inf;
+        int top = -1;   // largest particle slot below the cell
         for (int c = k + 1; c < end; c = A.e_skip[c]) {
             const float4 a = A.ra[c], b = A.rb[c];
             if (__float_as_int(a.w) < 0) {
@@ -527,6 +515,7 @@ __global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t
                 // to nearest, lo the sign of x - hi), so x lies in
                 // [hi, next float up] or [next float down, hi]
                 if (a.x == inf) continue;   // removed particle
+                top = max(top, ~__float_as_int(a.w));
                 lox = fminf(lox, b.x < 0.f ? nextafterf(a.x, -inf) : a.x);
                 hix = fmaxf(hix, b.x > 0.f ? nextafterf(a.x, inf) : a.x);
                 loy = fminf(loy, b.y < 0.f ? nextafterf(a.y, -inf) : a.y);
@@ -536,9 +525,10 @@ __global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t
             } else {
                 lox = fminf(lox, a.x); loy = fminf(loy, a.y); loz = fminf(loz, a.z);
                 hix = fmaxf(hix, b.x); hiy = fmaxf(hiy, b.y); hiz = fmaxf(hiz, b.z);
+                top = max(top, __float_as_int(a.w));
             }
         }
-        A.ra[k] = make_float4(lox, loy, loz, rmaxf);
+        A.ra[k] = make_float4(lox, loy, loz, __int_as_float(top));
         A.rb[k] = make_float4(hix, hiy, hiz, __int_as_float(end));
     }
 }

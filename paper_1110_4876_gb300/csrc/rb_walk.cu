@@ -657,6 +657,7 @@ struct CollArgs {
     int nimg;
     int32_t* tq;         // tile queues (emptied by the image-table launch)
     int nq;
+    float rmaxf;         // largest radius, rounded up (box records)
 };
 
 // Overlap test of Sect. 5.1 on the canonical orientation (a = lower id, b
@@ -764,14 +765,17 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                         const float4 rb = __ldg(&A.rb[e]);
                         if (kAABB) {
                             // distance to the cell's box [ra.xyz, rb.xyz] of particle
-                            // positions; opened unless farther than R_i + R_max
+                            // positions; opened unless farther than R_i + R_max, or
+                            // unless every particle below sits at a slot <= i (those
+                            // pairs are examined from the other particle)
                             const float ex = fmaxf(fmaxf((ra.x - thx) - tlx, (thx - rb.x) + tlx), 0.f);
                             const float ey = fmaxf(fmaxf((ra.y - thy) - tly, (thy - rb.y) + tly), 0.f);
                             const float ez = fmaxf(fmaxf((ra.z - thz) - tlz, (thz - rb.z) + tlz), 0.f);
                             const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                            const float lim = (prf + ra.w) * 1.0001f +
+                            const float lim = (prf + A.rmaxf) * 1.0001f +
                                               4e-7f * (fabsf(thx) + fabsf(thy) + fabsf(thz));
-                            next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
+                            next = (__float_as_int(ra.w) > i && d2 < lim * lim) ? e + 1
+                                                                                : __float_as_int(rb.w);
                         } else {
                             const float dx = (ra.x - thx) + (rb.x - tlx);
                             const float dy = (ra.y - thy) + (rb.y - tly);
@@ -987,10 +991,13 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
 }
 
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
-                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block, bool aabb) {
+                      const Pairs& PR, int half_step_offset, cudaStream_t s, int block, bool aabb,
+                      double rmax) {
     if (T.cap_n <= 0) return;
     block = (block == 64 || block == 256) ? block : 128;
     CollArgs A;
+    A.rmaxf = (float)rmax;
+    if ((double)A.rmaxf < rmax) A.rmaxf = nextafterf(A.rmaxf, FLT_MAX);
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r; A.id = P.id; A.box = P.box;
     A.ra = T.ra; A.rb = T.rb; A.box_root = T.box_root; A.e_skip = T.e_skip; A.boxes = boxes;
     A.ctl = ctl;
