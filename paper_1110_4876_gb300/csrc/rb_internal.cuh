@@ -110,6 +110,7 @@ struct Tree {
     int32_t *node_a, *node_b;   // per split: particle range of the cell (reps only)
     int8_t* node_v;             // per split: cell depth if representative, else -1
     int32_t *e_first, *e_count, *e_skip, *e_parent, *e_nchild, *e_arrive;
+    int32_t* e_top;             // collision records on spheres: largest particle slot below
     int8_t* e_level;            // depth of a cell; 22 marks a particle leaf
     int32_t* leaf_of;           // per particle: its leaf entry
     double *M, *cx, *cy, *cz, *Q;   // FP64 moments per entry (Q: 6 x cap, xx yy zz xy xz yz)

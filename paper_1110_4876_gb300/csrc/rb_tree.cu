@@ -429,7 +429,8 @@ struct CollRecArgs {
     const int32_t* box;
     const uint64_t* key;
     const BoxP* boxes;
-    const int32_t *e_first, *e_skip, *leaf_of;
+    const int32_t *e_first, *e_skip, *leaf_of, *e_count;
+    int32_t* e_top;
     const int8_t* e_level;
     Rec4 ra, rb;
     const Ctl* ctl;
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
     const float h = __double2float_ru(0.8660254037844387 * w + A.rmax);
     A.ra[k] = make_float4(hx, hy, hz, h);
     A.rb[k] = make_float4(lx, ly, lz, __int_as_float(A.e_skip[k]));
+    A.e_top[k] = first + A.e_count[k] - 1;   // particles below sit at slots first ..
 }
 
 // Collision records on the gravity tree, at the positions after the second
@@ -596,6 +598,7 @@ void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP*
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
     A.box = P.box; A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level; A.leaf_of = T.leaf_of;
+    A.e_count = T.e_count; A.e_top = T.e_top;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
     A.ncap = T.cap_n; A.nbox = C.nbox;
     k_coll_records<<<ceil_div(T.cap_e, 256), 256, 0, s>>>(A);
@@ -607,6 +610,7 @@ void build_collision_aabb(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* bo
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
     A.box = P.box; A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level; A.leaf_of = T.leaf_of;
+    A.e_count = T.e_count; A.e_top = T.e_top;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
     A.ncap = T.cap_n; A.nbox = C.nbox;
     k_aabb_leaves<<<ceil_div(T.cap_n, 256), 256, 0, s>>>(A);

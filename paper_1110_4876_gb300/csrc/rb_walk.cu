@@ -658,6 +658,7 @@ struct CollArgs {
     int32_t* tq;         // tile queues (emptied by the image-table launch)
     int nq;
     float rmaxf;         // largest radius, rounded up (box records)
+    const int32_t* e_top;   // sphere records: largest particle slot below each cell
 };
 
 // Overlap test of Sect. 5.1 on the canonical orientation (a = lower id, b
@@ -683,7 +684,8 @@ __device__ __forceinline__ bool overlap64(double xa, double ya, double za, doubl
 // R_i + R_max (records of build_collision_aabb; a subset of Eq. 3's volume
 // that still holds every overlap).
 // Each unordered pair is examined once, from its lower slot (the other
-// particle reaches it through the opposite image).  A leaf's overlap is
+// particle reaches it through the opposite image), so a subtree whose
+// particles all sit at slots <= i is skipped as well.  A leaf's overlap is
 // decided in FP32 on hi/lo positions (distance good to ~1e-7 relative) unless
 // d^2 lies within 1e-4 of (R_a + R_b)^2; only those pairs get the exact FP64
 // test in the oracle's operation order on the canonical orientation (lower
@@ -782,7 +784,8 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                             const float dz = (ra.z - thz) + (rb.z - tlz);
                             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                             const float lim = (prf + ra.w) * 1.00002f;
-                            next = d2 < lim * lim ? e + 1 : __float_as_int(rb.w);
+                            next = (__ldg(&A.e_top[e]) > i && d2 < lim * lim) ? e + 1
+                                                                              : __float_as_int(rb.w);
                         }
                     }
                     const unsigned hits = __ballot_sync(kFull, hit);
@@ -1000,6 +1003,7 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     if ((double)A.rmaxf < rmax) A.rmaxf = nextafterf(A.rmaxf, FLT_MAX);
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r; A.id = P.id; A.box = P.box;
     A.ra = T.ra; A.rb = T.rb; A.box_root = T.box_root; A.e_skip = T.e_skip; A.boxes = boxes;
+    A.e_top = T.e_top;
     A.ctl = ctl;
     A.pair_key = PR.key; A.pair_cap = PR.cap; A.ncap = T.cap_n;
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
