@@ -271,21 +271,16 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
                 float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // sums of the last <= 16 iterations
-                int it = 0;
+                int it = 0;           // entries processed (warp-uniform)
                 bool rec = false;     // kRecord: this lane accepted a band cell this iteration
                 uint64_t rkey = 0;
                 bool want = false;    // kLearn: this lane accepted a band cell this iteration
                 float fin[12], funit = 0.f;
-                for (;;) {
+                // one entry of the union walk; false when every lane is done
+                auto step = [&]() -> bool {
                     if (!kOne && next >= wend) next = kEnd;
-                    if ((++it & 15) == 0) {   // warp-uniform flush into the compensated sums
-                        kadd(sx, cx, fx);
-                        kadd(sy, cy, fy);
-                        kadd(sz, cz, fz);
-                        fx = fy = fz = 0.f;
-                    }
                     const int e = (int)__reduce_min_sync(kFull, (unsigned)next);
-                    if (kOne ? e >= wend : e == kEnd) break;
+                    if (kOne ? e >= wend : e == kEnd) return false;
                     const float4 ra = __ldg(&A.ra[e]);
                     const float4 rb = __ldg(&A.rb[e]);
                     const bool act = next == e;
@@ -442,12 +437,29 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                         }
                         want = false;
                     }
+                    return true;
+                };
+                // two entries per pass; the warp-uniform flush into the
+                // compensated sums every 16 entries
+                for (;;) {
+                    if (it != 0 && (it & 15) == 0) {
+                        kadd(sx, cx, fx);
+                        kadd(sy, cy, fy);
+                        kadd(sz, cz, fz);
+                        fx = fy = fz = 0.f;
+                    }
+                    if (!step()) break;
+                    if (!step()) {
+                        it += 1;
+                        break;
+                    }
+                    it += 2;
                 }
                 kadd(sx, cx, fx);
                 kadd(sy, cy, fy);
                 kadd(sz, cz, fz);
                 pot += (double)fp;
-                iters += it - 1;
+                iters += it;
             }
     if (kLearn && qn > 0) {
         // the last partial tile: empty rows have zero inputs and no owner
