@@ -272,8 +272,8 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.node_a, cap, L); rc |= dalloc(s, &T.node_b, cap, L);
         rc |= dalloc(s, &T.node_v, cap, L);
         rc |= dalloc(s, &T.e_first, ecap, L); rc |= dalloc(s, &T.e_count, ecap, L);
-        rc |= dalloc(s, &T.e_skip, ecap, L); rc |= dalloc(s, &T.e_parent, ecap, L);
-        rc |= dalloc(s, &T.e_nchild, ecap, L); rc |= dalloc(s, &T.e_arrive, ecap, L);
+        rc |= dalloc(s, &T.e_skip, ecap, L); rc |= dalloc(s, &T.e_child, 8 * (size_t)ecap, L);
+        rc |= dalloc(s, &T.e_cmask, ecap, L); rc |= dalloc(s, &T.e_arrive, ecap, L);
         rc |= dalloc(s, &T.e_top, ecap, L);
         rc |= dalloc(s, &T.e_level, ecap, L);
         rc |= dalloc(s, &T.leaf_of, cap, L);

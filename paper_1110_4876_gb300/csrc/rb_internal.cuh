@@ -107,9 +107,11 @@ struct Tree {
     int32_t* scan_part;         // block partials of the entry scan
     uint32_t* mask;             // per particle: levels of cells starting there
     int32_t* start;             // per particle: first entry starting there (n + 1)
-    int32_t *node_a, *node_b;   // per split: particle range of the cell (reps only)
-    int8_t* node_v;             // per split: cell depth if representative, else -1
-    int32_t *e_first, *e_count, *e_skip, *e_parent, *e_nchild, *e_arrive;
+    int32_t *node_a, *node_b;   // per split: first particle of its cell (last: reps only)
+    int8_t* node_v;             // per split: cell depth (+32 unless representative), -1 none
+    int32_t *e_first, *e_count, *e_skip, *e_arrive;
+    int32_t* e_child;           // per cell entry: the child entry of each octant (8 slots)
+    uint32_t* e_cmask;          // per cell entry: octants that hold a child
     int32_t* e_top;             // collision records on spheres: largest particle slot below
     int8_t* e_level;            // depth of a cell; 22 marks a particle leaf
     int32_t* leaf_of;           // per particle: its leaf entry

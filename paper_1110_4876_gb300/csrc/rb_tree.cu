@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(256) k_nodes(const uint64_t* __restrict__ key,
         }
         const int a = good;
         const bool rep = (a == i) || (lcp_level<kMultiBox>(key, box, a, i) > v);
+        node_a[i] = a;
+        outv = (int8_t)(v + 32);   // the split's cell; its representative is another split
         if (rep) {
             // rightmost particle b with min(delta_i .. delta_{b-1}) >= v
             int g2 = i + 1, st = 1, b2 = n;
@@ -80,7 +82,6 @@ __global__ void __launch_bounds__(256) k_nodes(const uint64_t* __restrict__ key,
                 const int mid = (g2 + b2) >> 1;
                 if (lcp_level<kMultiBox>(key, box, i, mid) >= v) g2 = mid; else b2 = mid;
             }
-            node_a[i] = a;
             node_b[i] = g2;
             outv = (int8_t)v;
             atomicOr(&mask[a], 1u << v);
@@ -108,7 +109,10 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ mask,
                                               int32_t* __restrict__ e_count,
                                               int32_t* __restrict__ e_skip,
                                               int8_t* __restrict__ e_level,
-                                              int32_t* __restrict__ leaf_of) {
+                                              int32_t* __restrict__ leaf_of,
+                                              const uint64_t* __restrict__ key,
+                                              int32_t* __restrict__ e_child,
+                                              uint32_t* __restrict__ e_cmask) {
     const int n = min(ctl->n_live, ncap);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -120,14 +124,33 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ mask,
     e_level[li] = 22;
     leaf_of[i] = li;
     if (i < n - 1) {
-        const int v = node_v[i];
-        if (v >= 0) {
-            const int a = node_a[i], b = node_b[i];
-            const int idx = start[a] + __popc(mask[a] & ((1u << v) - 1u));
-            e_first[idx] = a;
-            e_count[idx] = b - a + 1;
-            e_skip[idx] = start[b + 1];
-            e_level[idx] = (int8_t)v;
+        const int vv = node_v[i];
+        if (vv >= 0) {
+            const int v = vv & 31;
+            const int a = node_a[i];
+            const int idx = start[a] + __popc(mask[a] & ((1u << v) - 1u));   // the split's cell
+            if (vv < 32) {
+                const int b = node_b[i];
+                e_first[idx] = a;
+                e_count[idx] = b - a + 1;
+                e_skip[idx] = start[b + 1];
+                e_level[idx] = (int8_t)v;
+            }
+            // child table (not for depth-21 groups, whose members share one key):
+            // particles i and i + 1 part at depth v + 1, so the child of cell idx
+            // that starts at particle i + 1 is its shallowest entry there; the
+            // representative also enters the first child, entry idx + 1
+            if (v < kMaxDepth) {
+                const int sh = 3 * (kMaxDepth - 1 - v);
+                const int o = (int)((key[i + 1] >> sh) & 7ull);
+                e_child[8 * (size_t)idx + o] = start[i + 1];
+                atomicOr(&e_cmask[idx], 1u << o);
+                if (vv < 32) {
+                    const int o0 = (int)((key[a] >> sh) & 7ull);
+                    e_child[8 * (size_t)idx + o0] = idx + 1;
+                    atomicOr(&e_cmask[idx], 1u << o0);
+                }
+            }
         }
     }
 }
@@ -196,7 +219,8 @@ struct GravRecArgs {
     bool has_test;   // some particles are test particles (source mass 0)
     const uint64_t* key;
     const BoxP* boxes;
-    const int32_t *e_first, *e_skip, *e_parent, *e_nchild, *leaf_of;
+    const int32_t *e_first, *e_skip, *e_child, *leaf_of;
+    const uint32_t* e_cmask;
     const int8_t* e_level;
     int32_t* e_arrive;
     double4_32a *d_a, *d_q0, *d_q1, *d_c;
@@ -285,10 +309,210 @@ __global__ void __launch_bounds__(256) k_level_fill(const int8_t* __restrict__ e
 // kF32Q: the quadrupole is only needed by the FP32 walk, so it is summed in
 // FP32 on the hi/lo records (d_c good to ~1e-7 relative); mass and centre of
 // mass stay FP64.  On GB300 FP64 instructions cost 64 times FP32 ones.
+// Running sums of one cell's moments about its first child's position o.
+struct MomSums {
+    double M, sx, sy, sz;   // mass and sum of M_c d_c (FP64)
+    double q[6];            // quadrupole about o (FP64 form)
+    float qf[6];            // quadrupole about o (FP32 form)
+};
+
+__device__ __forceinline__ void mom_zero(MomSums& S) {
+    S.M = S.sx = S.sy = S.sz = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        S.q[j] = 0.0;
+        S.qf[j] = 0.f;
+    }
+}
+
+// Adds child entry c (a particle leaf or a finished deeper cell).
+template <bool kF32Q>
+__device__ __forceinline__ void mom_add(const GravRecArgs& A, int c, double ox, double oy, double oz,
+                                        float4 h0, float4 l0, MomSums& S) {
+    const double4_32a a = A.d_a[c];
+    const bool leaf = __double_as_longlong(a.w) < 0;   // leaf records hold -m (m >= 0)
+    const double mc = leaf ? -a.w : A.d_q0[c].x;
+    const double dx = a.x - ox, dy = a.y - oy, dz = a.z - oz;
+    S.M += mc;
+    S.sx = fma(mc, dx, S.sx);
+    S.sy = fma(mc, dy, S.sy);
+    S.sz = fma(mc, dz, S.sz);
+    if (kF32Q) {
+        const float4 h = A.ra[c], l = A.rb[c];
+        const float fx = (h.x - h0.x) + (l.x - l0.x);
+        const float fy = (h.y - h0.y) + (l.y - l0.y);
+        const float fz = (h.z - h0.z) + (l.z - l0.z);
+        float fm;
+        if (leaf) {
+            fm = -h.w;
+        } else {
+            const float4 c0 = A.rq0[c], c1 = A.rq1[c];
+            fm = c0.x;
+            S.qf[0] += c0.y; S.qf[1] += c0.z; S.qf[2] += c0.w;
+            S.qf[3] += c1.x; S.qf[4] += c1.y; S.qf[5] += c1.z;
+        }
+        const float d2 = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+        const float m3x = 3.f * fm * fx, m3y = 3.f * fm * fy;
+        S.qf[0] += fmaf(m3x, fx, -fm * d2);
+        S.qf[1] += fmaf(m3y, fy, -fm * d2);
+        S.qf[2] += fmaf(3.f * fm * fz, fz, -fm * d2);
+        S.qf[3] += m3x * fy;
+        S.qf[4] += m3x * fz;
+        S.qf[5] += m3y * fz;
+    } else {
+        if (!leaf) {
+            const double4_32a c0 = A.d_q0[c], c1 = A.d_q1[c];
+            S.q[0] += c0.y; S.q[1] += c0.z; S.q[2] += c0.w;
+            S.q[3] += c1.x; S.q[4] += c1.y; S.q[5] += c1.z;
+        }
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        S.q[0] += mc * (3.0 * dx * dx - d2);
+        S.q[1] += mc * (3.0 * dy * dy - d2);
+        S.q[2] += mc * (3.0 * dz * dz - d2);
+        S.q[3] += mc * (3.0 * dx * dy);
+        S.q[4] += mc * (3.0 * dx * dz);
+        S.q[5] += mc * (3.0 * dy * dz);
+    }
+}
+
+// The cell's centre of mass, its quadrupole moved there, and its records.
+template <bool kF32Q>
+__device__ __forceinline__ void mom_finish(const GravRecArgs& A, int k, int depth, int end, double ox,
+                                           double oy, double oz, MomSums& S) {
+    const int v = depth;
+    const int first = A.e_first[k];
+    const BoxP bp = A.boxes[A.box[first]];
+    const double w = ldexp(bp.L, -v);
+    const double lo = -0.5 * bp.L;
+    double ix = 0.0, iy = 0.0, iz = 0.0;
+    if (A.inside || !(S.M > 0.0)) cell_index(A.key[first], v, ix, iy, iz);
+    double cx, cy, cz, ux, uy, uz;   // centre of mass and its offset from o
+    if (S.M > 0.0) {
+        const double iM = 1.0 / S.M;
+        ux = S.sx * iM; uy = S.sy * iM; uz = S.sz * iM;
+        cx = ox + ux; cy = oy + uy; cz = oz + uz;
+    } else {
+        // no source mass (test particles only): the geometric centre
+        cx = lo + (ix + 0.5) * w; cy = lo + (iy + 0.5) * w; cz = lo + (iz + 0.5) * w;
+        ux = uy = uz = 0.0;
+    }
+    if (kF32Q) {
+        const float fx = (float)ux, fy = (float)uy, fz = (float)uz, fm = (float)S.M;
+        const float d2 = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+        S.qf[0] -= fm * fmaf(3.f * fx, fx, -d2);
+        S.qf[1] -= fm * fmaf(3.f * fy, fy, -d2);
+        S.qf[2] -= fm * fmaf(3.f * fz, fz, -d2);
+        S.qf[3] -= 3.f * fm * fx * fy;
+        S.qf[4] -= 3.f * fm * fx * fz;
+        S.qf[5] -= 3.f * fm * fy * fz;
+#pragma unroll
+        for (int j = 0; j < 6; j++) S.q[j] = (double)S.qf[j];
+    } else {
+        const double d2 = ux * ux + uy * uy + uz * uz;
+        S.q[0] -= S.M * (3.0 * ux * ux - d2);
+        S.q[1] -= S.M * (3.0 * uy * uy - d2);
+        S.q[2] -= S.M * (3.0 * uz * uz - d2);
+        S.q[3] -= S.M * (3.0 * ux * uy);
+        S.q[4] -= S.M * (3.0 * ux * uz);
+        S.q[5] -= S.M * (3.0 * uy * uz);
+    }
+    const bool group = v == kMaxDepth;   // leaf group: never used as a multipole
+    const double ww = w * w;
+    A.d_a[k] = make_double4_32a(cx, cy, cz, group ? __longlong_as_double(0x7ff0000000000000ll) : ww);
+    A.d_q0[k] = make_double4_32a(S.M, S.q[0], S.q[1], S.q[2]);
+    A.d_q1[k] = make_double4_32a(S.q[3], S.q[4], S.q[5], w);
+    double c0x = 0.0, c0y = 0.0, c0z = 0.0;
+    if (A.inside) {
+        // cell corner lo + i w, rounded as two separate operations
+        c0x = __dadd_rn(lo, __dmul_rn(ix, w));
+        c0y = __dadd_rn(lo, __dmul_rn(iy, w));
+        c0z = __dadd_rn(lo, __dmul_rn(iz, w));
+        A.d_c[k] = make_double4_32a(c0x, c0y, c0z, w);
+    }
+    if (A.fp32) {
+        float hx, lx, hy, ly, hz, lz;
+        split_hilo(cx, hx, lx);
+        split_hilo(cy, hy, ly);
+        split_hilo(cz, hz, lz);
+        const float crit = group ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
+        A.ra[k] = make_float4(hx, hy, hz, crit);
+        A.rb[k] = make_float4(lx, ly, lz, __int_as_float(end));
+        if (kF32Q) {
+            A.rq0[k] = make_float4((float)S.M, S.qf[0], S.qf[1], S.qf[2]);
+            A.rq1[k] = make_float4(S.qf[3], S.qf[4], S.qf[5], 0.f);
+        } else {
+            A.rq0[k] = make_float4((float)S.M, (float)S.q[0], (float)S.q[1], (float)S.q[2]);
+            A.rq1[k] = make_float4((float)S.q[3], (float)S.q[4], (float)S.q[5], 0.f);
+        }
+        if (A.inside) {
+            split_hilo(c0x, hx, lx);
+            split_hilo(c0y, hy, ly);
+            split_hilo(c0z, hz, lz);
+            A.rc_hi[k] = make_float4(hx, hy, hz, (float)w);
+            A.rc_lo[k] = make_float4(lx, ly, lz, 0.f);
+        }
+    }
+}
+
+// The cells of one depth.  A cell's moments come from its children (deeper
+// cells, done by earlier launches, or particle leaves) in one pass: about the
+// first child's position o, M = sum M_c, S = sum M_c d_c and
+// Q_o = sum [Q_c + M_c (3 d_c d_c^T - |d_c|^2 I)], d_c = com_c - o; then the
+// centre of mass is o + S / M and the parallel-axis theorem moves Q_o to it:
+// Q = Q_o - M (3 s s^T - |s|^2 I), s = S / M (the traceless quadrupole about
+// the centre of mass, reading R3).  Every |d_c| and |s| is below the cell's
+// diagonal, so no term is much larger than the result.
+// kF32Q: the quadrupole is only needed by the FP32 walk, so it is summed in
+// FP32 on the hi/lo records (d_c good to ~1e-7 relative); mass and centre of
+// mass stay FP64.  On GB300 FP64 instructions cost 64 times FP32 ones.
+// A depth with few cells (the top of the tree, the deep close pairs) is
+// latency-bound: there eight lanes take one cell, one child each from the
+// octant table, and add their sums in a fixed butterfly order; a depth with
+// many cells gives each thread one cell, which follows its children in
+// pre-order.
+constexpr int kWarpCells = 19456;   // up to 4 cells per warp of the launch grid
+
 template <bool kF32Q>
 __global__ void __launch_bounds__(256) k_moments_level(GravRecArgs A, const int32_t* __restrict__ lvl,
                                                        const int32_t* __restrict__ list, int depth) {
     const int cnt = lvl[depth], off = lvl[32 + depth];
+    if (cnt <= kWarpCells && depth < kMaxDepth) {
+        const int lane = threadIdx.x & 31, o = lane & 7;   // o: octant of this lane's child
+        const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwg = (gridDim.x * blockDim.x) >> 5;
+        for (int base = 4 * wg; base < cnt; base += 4 * nwg) {
+            // a warp takes 4 cells; a group past the end still joins the shuffles
+            const int g = base + (lane >> 3);
+            const bool live = g < cnt;
+            const int k = live ? list[off + g] : 0;
+            MomSums S;
+            mom_zero(S);
+            double ox = 0.0, oy = 0.0, oz = 0.0;
+            float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), l0 = h0;
+            if (live) {
+                const double4_32a a0 = A.d_a[k + 1];   // the first child is entry k + 1
+                ox = a0.x; oy = a0.y; oz = a0.z;
+                if (kF32Q) {
+                    h0 = A.ra[k + 1];
+                    l0 = A.rb[k + 1];
+                }
+                if ((A.e_cmask[k] >> o) & 1u) mom_add<kF32Q>(A, A.e_child[8 * (size_t)k + o], ox, oy, oz, h0, l0, S);
+            }
+#pragma unroll
+            for (int x = 1; x < 8; x <<= 1) {
+                S.M += __shfl_xor_sync(0xffffffffu, S.M, x);
+                S.sx += __shfl_xor_sync(0xffffffffu, S.sx, x);
+                S.sy += __shfl_xor_sync(0xffffffffu, S.sy, x);
+                S.sz += __shfl_xor_sync(0xffffffffu, S.sz, x);
+#pragma unroll
+                for (int j = 0; j < 6; j++) {
+                    if (kF32Q) S.qf[j] += __shfl_xor_sync(0xffffffffu, S.qf[j], x);
+                    else S.q[j] += __shfl_xor_sync(0xffffffffu, S.q[j], x);
+                }
+            }
+            if (live && o == 0) mom_finish<kF32Q>(A, k, depth, A.e_skip[k], ox, oy, oz, S);
+        }
+        return;
+    }
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const int k = list[off + t];
         const int end = A.e_skip[k];
@@ -299,128 +523,10 @@ __global__ void __launch_bounds__(256) k_moments_level(GravRecArgs A, const int3
             h0 = A.ra[k + 1];
             l0 = A.rb[k + 1];
         }
-        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        double q[6] = {0, 0, 0, 0, 0, 0};
-        float qf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int c = k + 1; c < end; c = A.e_skip[c]) {
-            const double4_32a a = A.d_a[c];
-            const bool leaf = __double_as_longlong(a.w) < 0;   // leaf records hold -m (m >= 0)
-            const double mc = leaf ? -a.w : A.d_q0[c].x;
-            const double dx = a.x - ox, dy = a.y - oy, dz = a.z - oz;
-            M += mc;
-            sx = fma(mc, dx, sx);
-            sy = fma(mc, dy, sy);
-            sz = fma(mc, dz, sz);
-            if (kF32Q) {
-                const float4 h = A.ra[c], l = A.rb[c];
-                const float fx = (h.x - h0.x) + (l.x - l0.x);
-                const float fy = (h.y - h0.y) + (l.y - l0.y);
-                const float fz = (h.z - h0.z) + (l.z - l0.z);
-                float fm;
-                if (leaf) {
-                    fm = -h.w;
-                } else {
-                    const float4 c0 = A.rq0[c], c1 = A.rq1[c];
-                    fm = c0.x;
-                    qf[0] += c0.y; qf[1] += c0.z; qf[2] += c0.w;
-                    qf[3] += c1.x; qf[4] += c1.y; qf[5] += c1.z;
-                }
-                const float d2 = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
-                const float m3x = 3.f * fm * fx, m3y = 3.f * fm * fy;
-                qf[0] += fmaf(m3x, fx, -fm * d2);
-                qf[1] += fmaf(m3y, fy, -fm * d2);
-                qf[2] += fmaf(3.f * fm * fz, fz, -fm * d2);
-                qf[3] += m3x * fy;
-                qf[4] += m3x * fz;
-                qf[5] += m3y * fz;
-            } else {
-                if (!leaf) {
-                    const double4_32a c0 = A.d_q0[c], c1 = A.d_q1[c];
-                    q[0] += c0.y; q[1] += c0.z; q[2] += c0.w;
-                    q[3] += c1.x; q[4] += c1.y; q[5] += c1.z;
-                }
-                const double d2 = dx * dx + dy * dy + dz * dz;
-                q[0] += mc * (3.0 * dx * dx - d2);
-                q[1] += mc * (3.0 * dy * dy - d2);
-                q[2] += mc * (3.0 * dz * dz - d2);
-                q[3] += mc * (3.0 * dx * dy);
-                q[4] += mc * (3.0 * dx * dz);
-                q[5] += mc * (3.0 * dy * dz);
-            }
-        }
-        const int v = depth;
-        const int first = A.e_first[k];
-        const BoxP bp = A.boxes[A.box[first]];
-        const double w = ldexp(bp.L, -v);
-        const double lo = -0.5 * bp.L;
-        double ix = 0.0, iy = 0.0, iz = 0.0;
-        if (A.inside || !(M > 0.0)) cell_index(A.key[first], v, ix, iy, iz);
-        double cx, cy, cz, ux, uy, uz;   // centre of mass and its offset from o
-        if (M > 0.0) {
-            const double iM = 1.0 / M;
-            ux = sx * iM; uy = sy * iM; uz = sz * iM;
-            cx = ox + ux; cy = oy + uy; cz = oz + uz;
-        } else {
-            // no source mass (test particles only): the geometric centre
-            cx = lo + (ix + 0.5) * w; cy = lo + (iy + 0.5) * w; cz = lo + (iz + 0.5) * w;
-            ux = uy = uz = 0.0;
-        }
-        if (kF32Q) {
-            const float fx = (float)ux, fy = (float)uy, fz = (float)uz, fm = (float)M;
-            const float d2 = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
-            qf[0] -= fm * fmaf(3.f * fx, fx, -d2);
-            qf[1] -= fm * fmaf(3.f * fy, fy, -d2);
-            qf[2] -= fm * fmaf(3.f * fz, fz, -d2);
-            qf[3] -= 3.f * fm * fx * fy;
-            qf[4] -= 3.f * fm * fx * fz;
-            qf[5] -= 3.f * fm * fy * fz;
-#pragma unroll
-            for (int j = 0; j < 6; j++) q[j] = (double)qf[j];
-        } else {
-            const double d2 = ux * ux + uy * uy + uz * uz;
-            q[0] -= M * (3.0 * ux * ux - d2);
-            q[1] -= M * (3.0 * uy * uy - d2);
-            q[2] -= M * (3.0 * uz * uz - d2);
-            q[3] -= M * (3.0 * ux * uy);
-            q[4] -= M * (3.0 * ux * uz);
-            q[5] -= M * (3.0 * uy * uz);
-        }
-        const bool group = v == kMaxDepth;   // leaf group: never used as a multipole
-        const double ww = w * w;
-        A.d_a[k] = make_double4_32a(cx, cy, cz, group ? __longlong_as_double(0x7ff0000000000000ll) : ww);
-        A.d_q0[k] = make_double4_32a(M, q[0], q[1], q[2]);
-        A.d_q1[k] = make_double4_32a(q[3], q[4], q[5], w);
-        double c0x = 0.0, c0y = 0.0, c0z = 0.0;
-        if (A.inside) {
-            // cell corner lo + i w, rounded as two separate operations
-            c0x = __dadd_rn(lo, __dmul_rn(ix, w));
-            c0y = __dadd_rn(lo, __dmul_rn(iy, w));
-            c0z = __dadd_rn(lo, __dmul_rn(iz, w));
-            A.d_c[k] = make_double4_32a(c0x, c0y, c0z, w);
-        }
-        if (A.fp32) {
-            float hx, lx, hy, ly, hz, lz;
-            split_hilo(cx, hx, lx);
-            split_hilo(cy, hy, ly);
-            split_hilo(cz, hz, lz);
-            const float crit = group ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
-            A.ra[k] = make_float4(hx, hy, hz, crit);
-            A.rb[k] = make_float4(lx, ly, lz, __int_as_float(end));
-            if (kF32Q) {
-                A.rq0[k] = make_float4((float)M, qf[0], qf[1], qf[2]);
-                A.rq1[k] = make_float4(qf[3], qf[4], qf[5], 0.f);
-            } else {
-                A.rq0[k] = make_float4((float)M, (float)q[0], (float)q[1], (float)q[2]);
-                A.rq1[k] = make_float4((float)q[3], (float)q[4], (float)q[5], 0.f);
-            }
-            if (A.inside) {
-                split_hilo(c0x, hx, lx);
-                split_hilo(c0y, hy, ly);
-                split_hilo(c0z, hz, lz);
-                A.rc_hi[k] = make_float4(hx, hy, hz, (float)w);
-                A.rc_lo[k] = make_float4(lx, ly, lz, 0.f);
-            }
-        }
+        MomSums S;
+        mom_zero(S);
+        for (int c = k + 1; c < end; c = A.e_skip[c]) mom_add<kF32Q>(A, c, ox, oy, oz, h0, l0, S);
+        mom_finish<kF32Q>(A, k, depth, end, ox, oy, oz, S);
     }
 }
 
@@ -429,7 +535,8 @@ struct CollRecArgs {
     const int32_t* box;
     const uint64_t* key;
     const BoxP* boxes;
-    const int32_t *e_first, *e_skip, *leaf_of, *e_count;
+    const int32_t *e_first, *e_skip, *leaf_of, *e_count, *e_child;
+    const uint32_t* e_cmask;
     int32_t* e_top;
     const int8_t* e_level;
     Rec4 ra, rb;
@@ -501,37 +608,73 @@ __global__ void __launch_bounds__(256) k_aabb_leaves(CollRecArgs A) {
     A.rb[e] = make_float4(lx, ly, lz, (float)A.r[p]);
 }
 
+// One child's contribution to a cell's box and largest slot.
+struct BoxAcc {
+    float lox, loy, loz, hix, hiy, hiz;
+    int top;
+};
+
+__device__ __forceinline__ void box_add(const CollRecArgs& A, int c, BoxAcc& B) {
+    const float inf = __int_as_float(0x7f800000);
+    const float4 a = A.ra[c], b = A.rb[c];
+    if (__float_as_int(a.w) < 0) {
+        // particle leaf: hi/lo floats of its position (hi = x rounded to
+        // nearest, lo the sign of x - hi), so x lies in [hi, next float up]
+        // or [next float down, hi]
+        if (a.x == inf) return;   // removed particle
+        B.top = max(B.top, ~__float_as_int(a.w));
+        B.lox = fminf(B.lox, b.x < 0.f ? nextafterf(a.x, -inf) : a.x);
+        B.hix = fmaxf(B.hix, b.x > 0.f ? nextafterf(a.x, inf) : a.x);
+        B.loy = fminf(B.loy, b.y < 0.f ? nextafterf(a.y, -inf) : a.y);
+        B.hiy = fmaxf(B.hiy, b.y > 0.f ? nextafterf(a.y, inf) : a.y);
+        B.loz = fminf(B.loz, b.z < 0.f ? nextafterf(a.z, -inf) : a.z);
+        B.hiz = fmaxf(B.hiz, b.z > 0.f ? nextafterf(a.z, inf) : a.z);
+    } else {
+        B.lox = fminf(B.lox, a.x); B.loy = fminf(B.loy, a.y); B.loz = fminf(B.loz, a.z);
+        B.hix = fmaxf(B.hix, b.x); B.hiy = fmaxf(B.hiy, b.y); B.hiz = fmaxf(B.hiz, b.z);
+        B.top = max(B.top, __float_as_int(a.w));
+    }
+}
+
+// The cells of one depth (same split between eight lanes per cell and one
+// thread per cell as the moments; minima and maxima do not depend on order).
 __global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t* __restrict__ lvl,
                                                     const int32_t* __restrict__ list, int depth) {
     const int cnt = lvl[depth], off = lvl[32 + depth];
+    const float inf = __int_as_float(0x7f800000);
+    if (cnt <= kWarpCells && depth < kMaxDepth) {
+        const int lane = threadIdx.x & 31, o = lane & 7;
+        const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwg = (gridDim.x * blockDim.x) >> 5;
+        for (int base = 4 * wg; base < cnt; base += 4 * nwg) {
+            const int g = base + (lane >> 3);
+            const bool live = g < cnt;
+            const int k = live ? list[off + g] : 0;
+            BoxAcc B{inf, inf, inf, -inf, -inf, -inf, -1};
+            if (live && ((A.e_cmask[k] >> o) & 1u)) box_add(A, A.e_child[8 * (size_t)k + o], B);
+#pragma unroll
+            for (int x = 1; x < 8; x <<= 1) {
+                B.lox = fminf(B.lox, __shfl_xor_sync(0xffffffffu, B.lox, x));
+                B.loy = fminf(B.loy, __shfl_xor_sync(0xffffffffu, B.loy, x));
+                B.loz = fminf(B.loz, __shfl_xor_sync(0xffffffffu, B.loz, x));
+                B.hix = fmaxf(B.hix, __shfl_xor_sync(0xffffffffu, B.hix, x));
+                B.hiy = fmaxf(B.hiy, __shfl_xor_sync(0xffffffffu, B.hiy, x));
+                B.hiz = fmaxf(B.hiz, __shfl_xor_sync(0xffffffffu, B.hiz, x));
+                B.top = max(B.top, __shfl_xor_sync(0xffffffffu, B.top, x));
+            }
+            if (live && o == 0) {
+                A.ra[k] = make_float4(B.lox, B.loy, B.loz, __int_as_float(B.top));
+                A.rb[k] = make_float4(B.hix, B.hiy, B.hiz, __int_as_float(A.e_skip[k]));
+            }
+        }
+        return;
+    }
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const int k = list[off + t];
         const int end = A.e_skip[k];
-        const float inf = __int_as_float(0x7f800000);
-        float lox = inf, loy = inf, loz = inf, hix = -inf, hiy = -inf, hiz = -inf;
-        int top = -1;   // largest particle slot below the cell
-        for (int c = k + 1; c < end; c = A.e_skip[c]) {
-            const float4 a = A.ra[c], b = A.rb[c];
-            if (__float_as_int(a.w) < 0) {
-                // particle leaf: hi/lo floats of its position (hi = x rounded
-                // to nearest, lo the sign of x - hi), so x lies in
-                // [hi, next float up] or [next float down, hi]
-                if (a.x == inf) continue;   // removed particle
-                top = max(top, ~__float_as_int(a.w));
-                lox = fminf(lox, b.x < 0.f ? nextafterf(a.x, -inf) : a.x);
-                hix = fmaxf(hix, b.x > 0.f ? nextafterf(a.x, inf) : a.x);
-                loy = fminf(loy, b.y < 0.f ? nextafterf(a.y, -inf) : a.y);
-                hiy = fmaxf(hiy, b.y > 0.f ? nextafterf(a.y, inf) : a.y);
-                loz = fminf(loz, b.z < 0.f ? nextafterf(a.z, -inf) : a.z);
-                hiz = fmaxf(hiz, b.z > 0.f ? nextafterf(a.z, inf) : a.z);
-            } else {
-                lox = fminf(lox, a.x); loy = fminf(loy, a.y); loz = fminf(loz, a.z);
-                hix = fmaxf(hix, b.x); hiy = fmaxf(hiy, b.y); hiz = fmaxf(hiz, b.z);
-                top = max(top, __float_as_int(a.w));
-            }
-        }
-        A.ra[k] = make_float4(lox, loy, loz, __int_as_float(top));
-        A.rb[k] = make_float4(hix, hiy, hiz, __int_as_float(end));
+        BoxAcc B{inf, inf, inf, -inf, -inf, -inf, -1};
+        for (int c = k + 1; c < end; c = A.e_skip[c]) box_add(A, c, B);
+        A.ra[k] = make_float4(B.lox, B.loy, B.loz, __int_as_float(B.top));
+        A.rb[k] = make_float4(B.hix, B.hiy, B.hiz, __int_as_float(end));
     }
 }
 
@@ -550,8 +693,9 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
                                           T.mask);
     k_entry_counts<<<nb, 256, 0, s>>>(T.mask, ctl, n, T.start);
     exclusive_scan_i32(T.start, n, &ctl->n_live, T.scan_part, &ctl->n_entries, s);
+    cudaMemsetAsync(T.e_cmask, 0, sizeof(uint32_t) * T.cap_e, s);
     k_emit<<<nb, 256, 0, s>>>(T.mask, T.start, T.node_a, T.node_b, T.node_v, ctl, n, T.e_first,
-                              T.e_count, T.e_skip, T.e_level, T.leaf_of);
+                              T.e_count, T.e_skip, T.e_level, T.leaf_of, T.key, T.e_child, T.e_cmask);
     k_box_ranges<<<ceil_div(n > C.nbox + 1 ? n : C.nbox + 1, 256), 256, 0, s>>>(
         P.box, ctl, n, C.nbox, T.box_first);
     k_box_roots<<<ceil_div(C.nbox, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
@@ -568,8 +712,8 @@ void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* b
     A.x = P.x; A.y = P.y; A.z = P.z; A.m = P.m; A.box = P.box; A.id = P.id;
     A.has_test = C.has_test != 0;
     A.key = T.key; A.boxes = boxes;
-    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_parent = T.e_parent;
-    A.e_nchild = T.e_nchild; A.leaf_of = T.leaf_of; A.e_level = T.e_level;
+    A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_child = T.e_child;
+    A.e_cmask = T.e_cmask; A.leaf_of = T.leaf_of; A.e_level = T.e_level;
     A.e_arrive = T.e_arrive;
     A.d_a = T.d_a; A.d_q0 = T.d_q0; A.d_q1 = T.d_q1; A.d_c = T.d_c;
     A.ra = T.ra; A.rb = T.rb; A.rq0 = T.rq0; A.rq1 = T.rq1; A.rc_hi = T.rc_hi; A.rc_lo = T.rc_lo;
@@ -598,7 +742,7 @@ void build_collision_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP*
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
     A.box = P.box; A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level; A.leaf_of = T.leaf_of;
-    A.e_count = T.e_count; A.e_top = T.e_top;
+    A.e_count = T.e_count; A.e_top = T.e_top; A.e_child = T.e_child; A.e_cmask = T.e_cmask;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
     A.ncap = T.cap_n; A.nbox = C.nbox;
     k_coll_records<<<ceil_div(T.cap_e, 256), 256, 0, s>>>(A);
@@ -610,7 +754,7 @@ void build_collision_aabb(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* bo
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r;
     A.box = P.box; A.key = T.key; A.boxes = boxes;
     A.e_first = T.e_first; A.e_skip = T.e_skip; A.e_level = T.e_level; A.leaf_of = T.leaf_of;
-    A.e_count = T.e_count; A.e_top = T.e_top;
+    A.e_count = T.e_count; A.e_top = T.e_top; A.e_child = T.e_child; A.e_cmask = T.e_cmask;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
     A.ncap = T.cap_n; A.nbox = C.nbox;
     k_aabb_leaves<<<ceil_div(T.cap_n, 256), 256, 0, s>>>(A);
