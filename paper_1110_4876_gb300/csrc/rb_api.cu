@@ -193,7 +193,7 @@ int box_params(rb_sim* s) {
         memset(&p, 0, sizeof(p));
         p.L = s->hb[b].L[0];
         p.Lx = s->hb[b].L[0]; p.Ly = s->hb[b].L[1]; p.Lz = s->hb[b].L[2];
-        p.inv_L = 1.0 / p.L;
+        p.key_scale = (1.0 / p.L) * 2097152.0;   // exact scaling of the rounded reciprocal
         p.shear_speed = s->cfg.boundary == RB_BC_SHEAR ? (1.5 * s->cfg.omega) * p.Lx : 0.0;
         p.base_id = b < (int)s->base.size() ? (int)s->base[b] : 0;
         p.n_active = s->n_active < 0 ? 0x7fffffff : (int)std::min<int64_t>(s->n_active, 0x7fffffff);

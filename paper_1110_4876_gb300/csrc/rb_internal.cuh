@@ -30,7 +30,7 @@ struct BoxP {
     double L;            // root cube side (= Lx = Ly = Lz)
     double Lx, Ly, Lz;   // box sides (periodic lengths)
     double shear_speed;  // (1.5 * Omega) * Lx for shear-periodic boxes, else 0
-    double inv_L;        // 1 / L (rounded), for the fast path of the integer coordinates
+    double key_scale;    // (1 / L, rounded) x 2^21, for the fast path of the integer coordinates
     int base_id;         // global id of the box's particle 0
     int n_active;        // particles with id - base_id >= n_active exert no gravity
     double pad;

@@ -34,10 +34,11 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 // The quotient is first taken as (x - lo) * (1/L), within 2^-51 of the
 // correctly rounded quotient, i.e. within 2^-30 on the 2^21 grid; unless
 // that lands within 1e-7 of a grid line (about one coordinate in 10^7), the
-// floor is the same and the FP64 division is skipped.
-__device__ __forceinline__ uint32_t icoord(double x, double lo, double L, double inv_L) {
+// floor is the same and the FP64 division is skipped.  scale = (1/L) 2^21:
+// scaling by a power of two commutes with rounding, so one multiply does.
+__device__ __forceinline__ uint32_t icoord(double x, double lo, double L, double scale) {
     const double d = __dsub_rn(x, lo);
-    double k = __dmul_rn(__dmul_rn(d, inv_L), 2097152.0);
+    double k = __dmul_rn(d, scale);
     const double f = floor(k);
     if (k - f < 1e-7 || f + 1.0 - k < 1e-7) k = __dmul_rn(__ddiv_rn(d, L), 2097152.0);
     k = floor(k);
@@ -75,14 +76,15 @@ constexpr int kMaxWraps = 1 << 12;
 
 // Boundaries after a drift half; returns false if the particle left an open
 // boundary.  *runaway is set when the wraps did not bring it back.
-__device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, double t, double& x,
+__device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, const Ctl* ctl, int hs, double& x,
                                          double& y, double& z, double& vy, bool* runaway) {
     const double hx = 0.5 * bp.Lx, hy = 0.5 * bp.Ly, hz = 0.5 * bp.Lz;
     if (C.boundary == 0)
         return !(x < -hx || x >= hx || y < -hy || y >= hy || z < -hz || z >= hz);
     const double vs = bp.shear_speed;
     // the shear offset only for the few particles that cross in x
-    const double s = (x >= hx || x < -hx) && vs != 0.0 ? fmod(__dmul_rn(vs, t), bp.Ly) : 0.0;
+    const double s =
+        (x >= hx || x < -hx) && vs != 0.0 ? fmod(__dmul_rn(vs, time_at(ctl, C, hs)), bp.Ly) : 0.0;
     if (x >= hx) {
         x = __dsub_rn(x, bp.Lx);
         y = __dadd_rn(y, s);
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(256) k_drift_keys(DriftArgs A, SimC C) {
         bool runaway = false;
         for (int d = 0; d < A.ndrift && live; d++) {
             drift_one(C, x, y, z, vx, vy, vz);
-            live = wrap_one(C, bp, time_at(A.ctl, C, A.hs + d), x, y, z, vy, &runaway);
+            live = wrap_one(C, bp, A.ctl, A.hs + d, x, y, z, vy, &runaway);
         }
         if (runaway || !(isfinite(x) && isfinite(y) && isfinite(z))) {
             atomicOr(&A.ctl->err, kErrNonFinite);
@@ -146,8 +148,9 @@ __global__ void __launch_bounds__(256) k_drift_keys(DriftArgs A, SimC C) {
         A.P.vx[i] = vx; A.P.vy[i] = vy; A.P.vz[i] = vz;
         if (live) {
             const double lo = -0.5 * bp.L;
-            key = (spread3(icoord(x, lo, bp.L, bp.inv_L)) << 2) |
-                  (spread3(icoord(y, lo, bp.L, bp.inv_L)) << 1) | spread3(icoord(z, lo, bp.L, bp.inv_L));
+            key = (spread3(icoord(x, lo, bp.L, bp.key_scale)) << 2) |
+                  (spread3(icoord(y, lo, bp.L, bp.key_scale)) << 1) |
+                  spread3(icoord(z, lo, bp.L, bp.key_scale));
         }
     }
     A.key[i] = key;
