@@ -97,9 +97,6 @@ struct rb_sim {
 namespace {
 
 constexpr int kEnergyParts = 304;
-// The sorted queue of a freshly drawn 1M-particle sheet (~940k pairs) has
-// chains of at most ~24 pairs; what 32 rounds leave is finished in order.
-constexpr int kResolveRounds = 32;
 
 int fail(rb_sim* s, int code, const std::string& msg) {
     if (s) s->err = msg; else g_create_error = msg;
@@ -223,9 +220,7 @@ int alloc_pairs(rb_sim* s, int cap) {
     rc |= dalloc(s, &R.next_a, cap, L);
     rc |= dalloc(s, &R.next_b, cap, L);
     rc |= dalloc(s, &R.wait, cap, L);
-    rc |= dalloc(s, &R.rdone, cap, L);
-    rc |= dalloc(s, &R.list0, cap, L);
-    rc |= dalloc(s, &R.list1, cap, L);
+    rc |= dalloc(s, &R.queue, cap, L);
     rc |= dalloc(s, &R.rcnt, 64, L);
     rc |= dalloc(s, &R.hist, radix_hist_words(cap), L);
     rc |= dalloc(s, &R.ehist, radix_hist_words(2 * cap), L);
@@ -460,7 +455,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
-        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, s->T.img, st);
     } else if (s->cfg.collisions && s->cfg.gravity) {
         // the gravity tree still holds the same particles: boxes of their
         // current positions replace a second sort and build
@@ -474,7 +469,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
-        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, s->T.img, st);
     } else if (s->cfg.collisions) {
         sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, st);
         c = 1 - c;
@@ -487,7 +482,7 @@ int record_step(rb_sim* s, int p) {
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
-        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, kResolveRounds, s->T.img, st);
+        resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, s->T.img, st);
     } else {
         discard_live_count(s->ctl, st);   // no sort follows the last drift
         for (int k = 7; k <= 11; k++) mark(s, k);
@@ -556,8 +551,11 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve, bool aabb) {
                                             "(use the tree detector)");
         if (s->hctl.pair_count <= s->PR.cap) {
             if (resolve) {
-                resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, kResolveRounds, s->T.img, s->stream);
+                resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->T.img, s->stream);
                 if (read_ctl(s)) return RB_ERR_CUDA;
+                if (s->hctl.err & kErrResolveStall)
+                    return fail(s, RB_ERR_TIMEOUT,
+                                "collision resolution: a bounded wait for the ready queue gave up");
             }
             return RB_OK;
         }
@@ -740,6 +738,7 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
         s->own_stream = true;
     }
     s->nsm = walk_prepare();
+    resolve_prepare(s->nsm);
     cudaEventCreate(&s->ev0);
     cudaEventCreate(&s->ev1);
     for (auto& ev : s->ev_stage) cudaEventCreate(&ev);
@@ -846,6 +845,8 @@ int rb_step(rb_sim* s, int64_t nsteps) {
         if (s->hctl.err & kErrSweepLong)
             return fail(s, RB_ERR_CAPACITY, "plane sweep: a trajectory overlaps more than 65536 others in x "
                                             "(use the tree detector)");
+        if (s->hctl.err & kErrResolveStall)
+            return fail(s, RB_ERR_TIMEOUT, "collision resolution: a bounded wait for the ready queue gave up");
         if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
             // the step ended before resolution: search again with a larger buffer
             const bool aabb = s->cfg.gravity && s->cfg.collisions == RB_COLL_TREE;

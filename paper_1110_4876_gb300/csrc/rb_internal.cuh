@@ -81,6 +81,7 @@ struct Ctl {
 constexpr int kErrNonFinite = 1;
 constexpr int kErrPairOverflow = 2;
 constexpr int kErrSweepLong = 4;    // a plane-sweep item met more than kMaxSweepScan extents
+constexpr int kErrResolveStall = 8; // the resolution queue stopped filling (bounded wait gave up)
 constexpr int kMaxSweepScan = 1 << 16;
 
 // One ghost image of one box at the time of a walk or search (Sect. 2.3):
@@ -136,9 +137,8 @@ struct Pairs {
     int32_t *prev_a, *prev_b;  // previous pair (queue order) of particle a / b, or -1
     int32_t *next_a, *next_b;  // next pair of particle a / b, or -1
     int32_t* wait;             // unresolved predecessors of each pair
-    int32_t* rdone;            // round in which a pair was resolved, -1 while pending
-    int32_t *list0, *list1;    // pairs ready in a round (ping-pong)
-    int32_t* rcnt;             // rcnt[r]: pairs ready in round r (64)
+    int32_t* queue;            // pairs in the order they became ready (resolution)
+    int32_t* rcnt;             // queue counters: [0] slots written, [1] slots claimed
     int32_t* slot_of_id;       // global id -> slot in the current set
     uint32_t *hist, *ehist;
     int cap;
@@ -289,7 +289,10 @@ void drift_keys(const PSet& P, const Tree& T, Ctl* ctl, const BoxP* boxes, const
 void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl* ctl,
                       const SimC& C, int ncap, int box_bits, cudaStream_t s);
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
-                   int half_step_offset, int rounds, ImgTab* img, cudaStream_t s);
+                   int half_step_offset, ImgTab* img, cudaStream_t s);
+// Queries the resident blocks of the resolution queue once (outside any
+// stream capture).
+void resolve_prepare(int nsm);
 // key_bits: bits of the largest pair key, 36 + the bits of the largest id
 void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s, int key_bits = 60);
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,

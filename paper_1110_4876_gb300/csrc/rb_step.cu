@@ -200,7 +200,6 @@ struct ResolveArgs {
     const int32_t *prev_a, *prev_b;   // previous pair of particle a / b (queue order), or -1
     const int32_t *next_a, *next_b;   // next pair of particle a / b, or -1
     int32_t* wait;                    // predecessors of a pair not yet resolved
-    int32_t* rdone;
     Ctl* ctl;
     const BoxP* boxes;
     int hs;
@@ -213,7 +212,9 @@ __device__ __forceinline__ void pair_slots(const ResolveArgs& A, uint64_t k, int
     sb = A.slot_of_id[(int)((k >> 12) & 0xFFFFFFull)];
 }
 
-// Eq. 2 for one pair, in the oracle's operation order.
+// Eq. 2 for one pair, in the oracle's operation order.  kCG: velocities are
+// read from L2 (other SMs update them while the queue runs).
+template <bool kCG = false>
 __device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C, uint64_t k) {
     int a, b;
     pair_slots(A, k, a, b);
@@ -226,8 +227,14 @@ __device__ __forceinline__ bool resolve_one(const ResolveArgs& A, const SimC& C,
     const double rx = __dsub_rn(__dadd_rn(A.P.x[b], ox), A.P.x[a]);
     const double ry = __dsub_rn(__dadd_rn(A.P.y[b], oy), A.P.y[a]);
     const double rz = __dsub_rn(__dadd_rn(A.P.z[b], oz), A.P.z[a]);
-    double vxa = A.P.vx[a], vya = A.P.vy[a], vza = A.P.vz[a];
-    double vxb = A.P.vx[b], vyb = A.P.vy[b], vzb = A.P.vz[b];
+    double vxa, vya, vza, vxb, vyb, vzb;
+    if (kCG) {
+        vxa = __ldcg(&A.P.vx[a]); vya = __ldcg(&A.P.vy[a]); vza = __ldcg(&A.P.vz[a]);
+        vxb = __ldcg(&A.P.vx[b]); vyb = __ldcg(&A.P.vy[b]); vzb = __ldcg(&A.P.vz[b]);
+    } else {
+        vxa = A.P.vx[a]; vya = A.P.vy[a]; vza = A.P.vz[a];
+        vxb = A.P.vx[b]; vyb = A.P.vy[b]; vzb = A.P.vz[b];
+    }
     const double ux = __dsub_rn(vxb, vxa), uy = __dsub_rn(__dadd_rn(vyb, dvg), vya),
                  uz = __dsub_rn(vzb, vza);
     const double rv = __dadd_rn(__dadd_rn(__dmul_rn(rx, ux), __dmul_rn(ry, uy)), __dmul_rn(rz, uz));
@@ -278,8 +285,7 @@ __global__ void __launch_bounds__(256) k_pair_prev(const uint64_t* __restrict__ 
                                                    int32_t* __restrict__ prev_a,
                                                    int32_t* __restrict__ prev_b,
                                                    int32_t* __restrict__ next_a,
-                                                   int32_t* __restrict__ next_b,
-                                                   int32_t* __restrict__ rdone) {
+                                                   int32_t* __restrict__ next_b) {
     const int m = ctl->pair_ends;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
         const uint32_t v = eval[e];
@@ -292,7 +298,6 @@ __global__ void __launch_bounds__(256) k_pair_prev(const uint64_t* __restrict__ 
         } else {
             prev_a[k] = prev;
             next_a[k] = next;
-            rdone[k] = -1;
         }
     }
 }
@@ -305,8 +310,8 @@ __device__ __forceinline__ void list_push(int32_t* list, int32_t* count, int k) 
     list[g.shfl(base, 0) + (int)g.thread_rank()] = k;
 }
 
-// Round 0's list: the pairs that are the first pair of both their particles;
-// every pair waits for as many predecessors as it has.
+// The queue's first slots: the pairs that are the first pair of both their
+// particles; every pair waits for as many predecessors as it has.
 __global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, int32_t* __restrict__ list,
                                                   int32_t* __restrict__ rcnt) {
     const int n = A.ctl->pair_n;
@@ -317,81 +322,82 @@ __global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, int32_t* __rest
     }
 }
 
-// Resolves pair k in round r and releases its successors: a pair whose last
-// predecessor this was joins the next round's list.
-__device__ __forceinline__ bool resolve_release(const ResolveArgs& A, const SimC& C, int k, int r,
-                                                int32_t* list_out, int32_t* count_out) {
-    const bool done = resolve_one(A, C, A.key[k]);
-    A.rdone[k] = r;
-    const int na = A.next_a[k], nb = A.next_b[k];
-    if (na >= 0 && atomicSub(&A.wait[na], 1) == 1) list_push(list_out, count_out, na);
-    if (nb >= 0 && atomicSub(&A.wait[nb], 1) == 1) list_push(list_out, count_out, nb);
-    return done;
+// The queue of ready pairs, worked by every resident thread in one launch.
+// A pair enters the queue (after the seed's pairs, in the order they become
+// ready) once every earlier pair of the sorted queue that shares a particle
+// with it is resolved; its wait count of unresolved predecessors reaches zero
+// at the release of the last one.  Threads claim queue slots in order (32
+// per warp vote) and wait for their slot to be written; a slot is written by
+// the thread that released its pair, after the velocities it wrote are made
+// visible (fence), and the velocities are read from L2.  Every pair sees all
+// earlier pairs that share a particle with it, so the outcome equals
+// resolving the sorted queue one pair at a time.  The claims are in queue
+// order and a thread resolves its pair as soon as the slot is written, so
+// the wait always ends while the launch's threads are all resident; it is
+// bounded all the same, and reports kErrResolveStall if it ever gives up.
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ void queue_push(int32_t* list, int32_t* tail, int k) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(tail, (int)g.size());
+    *(volatile int32_t*)&list[g.shfl(base, 0) + (int)g.thread_rank()] = k;
 }
 
-// Round r resolves the pairs whose predecessors (the previous pair of each
-// of its particles in queue order) were all resolved in earlier rounds: its
-// list holds exactly those, built by the rounds before.  Pairs of one round
-// share no particle, and every pair sees the results of all earlier pairs
-// that share a particle with it, so the outcome equals resolving the sorted
-// queue one pair at a time; each pair is visited once.  The longest chain of
-// the queue sets the number of rounds; the tail finishes what 32 rounds leave.
-__global__ void __launch_bounds__(256) k_res_round(ResolveArgs A, SimC C, int r,
-                                                   const int32_t* __restrict__ list_in,
-                                                   int32_t* __restrict__ list_out,
-                                                   int32_t* __restrict__ rcnt) {
-    const int n = rcnt[r];
-    if (n == 0) return;
-    int nd = 0, nr = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        nr += resolve_release(A, C, list_in[t], r, list_out, &rcnt[r + 1]) ? 1 : 0;
-        nd++;
-    }
-    if (nd) atomicSub(&A.ctl->pending, nd);
-    if (nr) atomicAdd(&A.ctl->resolved, nr);
-}
-
-// What the grid-wide rounds left: one block keeps running rounds (same rule,
-// block barriers instead of launches) on its ready lists.  After kTailRounds
-// rounds any remainder is resolved by one thread in queue order.
-constexpr int kTailRounds = 4096;
-
-__global__ void __launch_bounds__(1024) k_res_tail(ResolveArgs A, SimC C, int r0, int32_t* list_a,
-                                                   int32_t* list_b, const int32_t* __restrict__ rcnt) {
-    __shared__ int cnt_next, nres;
-    if (A.ctl->pending == 0) return;
-    int n = rcnt[r0];
-    int32_t* in = list_a;
-    int32_t* out = list_b;
-    if (threadIdx.x == 0) nres = 0;
-    int r = r0;
-    for (; n > 0 && r < r0 + kTailRounds; r++) {
-        if (threadIdx.x == 0) cnt_next = 0;
-        __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x)
-            if (resolve_release(A, C, in[t], r, out, &cnt_next)) atomicAdd(&nres, 1);
-        __syncthreads();
-        n = cnt_next;
-        int32_t* tmp = in;
-        in = out;
-        out = tmp;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        int nr = nres;
-        if (n > 0 || r0 == 0) {
-            // rounds exhausted (or none ran): the rest in queue order
-            const int np = A.ctl->pair_n;
-            for (int k = 0; k < np; k++) {
-                if (A.rdone[k] >= 0) continue;
-                nr += resolve_one(A, C, A.key[k]) ? 1 : 0;
-                A.rdone[k] = r;
+__global__ void __launch_bounds__(256) k_res_queue(ResolveArgs A, SimC C, int32_t* __restrict__ list,
+                                                   int32_t* __restrict__ q) {
+    // q[0]: slots written (the seed's pairs first), q[1]: slots claimed
+    const int np = A.ctl->pair_n;
+    const int lane = threadIdx.x & 31;
+    int nres = 0, ndone = 0;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&q[1], 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= np) break;
+        const int idx = base + lane;
+        bool stalled = false;
+        if (idx < np) {
+            int k = *(volatile int32_t*)&list[idx];
+            for (int spin = 0; k < 0; spin++) {
+                if (spin >= kSpinLimit || (spin % 1024 == 1023 && (*(volatile int*)&A.ctl->err & kErrResolveStall))) {
+                    atomicOr(&A.ctl->err, kErrResolveStall);
+                    stalled = true;
+                    break;
+                }
+                __nanosleep(100);
+                k = *(volatile int32_t*)&list[idx];
+            }
+            if (!stalled) {
+                __threadfence();   // the releasing thread's velocities before ours
+                nres += resolve_one<true>(A, C, A.key[k]) ? 1 : 0;
+                ndone++;
+                __threadfence();   // our velocities before the successors are released
+                const int na = A.next_a[k], nb = A.next_b[k];
+                if (na >= 0 && atomicSub(&A.wait[na], 1) == 1) queue_push(list, &q[0], na);
+                if (nb >= 0 && atomicSub(&A.wait[nb], 1) == 1) queue_push(list, &q[0], nb);
             }
         }
-        A.ctl->resolved += nr;
-        A.ctl->pending = 0;
+        if (__any_sync(0xffffffffu, stalled)) break;
     }
+    if (ndone) atomicSub(&A.ctl->pending, ndone);
+    if (nres) atomicAdd(&A.ctl->resolved, nres);
 }
+
+int g_queue_blocks = 0;   // resident blocks of k_res_queue on the whole GPU
+
+}  // namespace
+
+void resolve_prepare(int nsm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_res_queue, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    g_queue_blocks = std::max(nsm, 1) * std::max(per_sm, 1);
+}
+
+namespace {
 
 __global__ void k_step_advance(Ctl* ctl) { ctl->step += 1; }
 
@@ -548,10 +554,10 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s, int key_bits) {
 }
 
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
-                   int half_step_offset, int rounds, ImgTab* img, cudaStream_t s) {
+                   int half_step_offset, ImgTab* img, cudaStream_t s) {
     ResolveArgs A;
     A.P = P; A.key = PR.sorted(); A.slot_of_id = PR.slot_of_id;
-    A.prev_a = PR.prev_a; A.prev_b = PR.prev_b; A.rdone = PR.rdone;
+    A.prev_a = PR.prev_a; A.prev_b = PR.prev_b;
     A.next_a = PR.next_a; A.next_b = PR.next_b; A.wait = PR.wait;
     A.img = img;
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;
@@ -564,16 +570,13 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
                                  &ctl->pair_ends, 24, nullptr, 0, PR.ehist, s);
     k_pair_prev<<<2 * grid, 256, 0, s>>>(which ? PR.ekey_alt : PR.ekey,
                                          which ? PR.eval_alt : PR.eval, ctl, PR.prev_a, PR.prev_b,
-                                         PR.next_a, PR.next_b, PR.rdone);
+                                         PR.next_a, PR.next_b);
     cudaMemsetAsync(PR.rcnt, 0, sizeof(int32_t) * 64, s);
-    // round r reads list0 (r even) or list1 (r odd) and fills the other
-    k_res_seed<<<grid, 256, 0, s>>>(A, PR.list0, PR.rcnt);
-    const int last = std::min(rounds, 63);
-    for (int r = 0; r < last; r++)
-        k_res_round<<<grid, 256, 0, s>>>(A, C, r, (r & 1) ? PR.list1 : PR.list0,
-                                         (r & 1) ? PR.list0 : PR.list1, PR.rcnt);
-    k_res_tail<<<1, 1024, 0, s>>>(A, C, last, (last & 1) ? PR.list1 : PR.list0,
-                                  (last & 1) ? PR.list0 : PR.list1, PR.rcnt);
+    cudaMemsetAsync(PR.queue, 0xff, sizeof(int32_t) * (size_t)PR.cap, s);   // every slot unwritten
+    k_res_seed<<<grid, 256, 0, s>>>(A, PR.queue, PR.rcnt);
+    // resident blocks only: a thread may wait for a slot that another writes
+    const int qgrid = std::max(1, std::min(ceil_div(PR.cap, 256), g_queue_blocks));
+    k_res_queue<<<qgrid, 256, 0, s>>>(A, C, PR.queue, PR.rcnt);
 }
 
 void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int box,
