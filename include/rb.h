@@ -189,6 +189,12 @@ int rb_get_pairs(rb_sim* sim, int box, int64_t cap, int64_t* n, int64_t* id_a, i
  * buffer and searches again before any velocity changes, so results do not
  * depend on cap. */
 int rb_set_pair_capacity(rb_sim* sim, int64_t cap);
+/* Test hook: with `on` nonzero the first pair of every sorted collision queue
+ * waits for one predecessor too many, so it never becomes ready; the
+ * resolution's threads wait for its queue slot at most half a second and the
+ * step returns RB_ERR_TIMEOUT with the device context intact (velocities then
+ * hold a partial resolution).  0 restores normal resolution. */
+int rb_debug_hold_pair(rb_sim* sim, int on);
 /* Set / read the simulation time (restarts the step counter at t). */
 int rb_set_time(rb_sim* sim, double t);
 int rb_get_time(rb_sim* sim, double* t);

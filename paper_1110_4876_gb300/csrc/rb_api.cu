@@ -73,6 +73,7 @@ struct rb_sim {
     int nsm = 0;                           // SMs of the device (tile queues of the walks)
     int64_t n_active = -1;                 // test particles: ids >= n_active per box
     int eps_law = 0;                       // restitution law (RB_EPS_*)
+    int hold_pair = 0;                     // test hook (rb_debug_hold_pair)
     double eps_vc = 1.0, eps_p = 0.0;
     std::string err;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -158,6 +159,7 @@ void make_constants(rb_sim* s) {
     C.nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
     C.has_test = s->n_active >= 0;
     C.eps_law = s->eps_law;
+    C.hold_pair = s->hold_pair;
     C.eps_vc = s->eps_vc;
     C.eps_p = s->eps_p;
     C.G = c.G;
@@ -1007,6 +1009,14 @@ int rb_set_pair_capacity(rb_sim* s, int64_t cap) {
     if (rc) return rc;
     drop_graphs(s);
     return alloc_pairs(s, (int)cap);
+}
+
+int rb_debug_hold_pair(rb_sim* s, int on) {
+    if (!s) return fail(s, RB_ERR_ARG, "null simulation");
+    s->hold_pair = on ? 1 : 0;
+    make_constants(s);
+    drop_graphs(s);
+    return RB_OK;
 }
 
 int rb_set_time(rb_sim* s, double t) {

@@ -44,6 +44,7 @@ struct SimC {
     double crit_scale;   // 1 / theta^2 (FP32 criterion (w / theta)^2)
     int has_test;        // some particles are test particles (source mass 0)
     int eps_law;         // 0: constant eps; 1: eps = min(1, (|v_n| / eps_vc)^(-eps_p))
+    int hold_pair;       // test hook: the queue's first pair never becomes ready
     double eps_vc, eps_p;
     // SEI drift coefficients for tau = dt / 2 (x, vx, vy) -> (x, y, vx, vy), and z
     double axx, axu, axv, ayx, ayu, ayv, aux, auu, auv, avx, avu, avv;

@@ -312,11 +312,11 @@ __device__ __forceinline__ void list_push(int32_t* list, int32_t* count, int k) 
 
 // The queue's first slots: the pairs that are the first pair of both their
 // particles; every pair waits for as many predecessors as it has.
-__global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, SimC C, int32_t* __restrict__ list,
                                                   int32_t* __restrict__ rcnt) {
     const int n = A.ctl->pair_n;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int w = (A.prev_a[k] >= 0 ? 1 : 0) + (A.prev_b[k] >= 0 ? 1 : 0);
+        const int w = (A.prev_a[k] >= 0 ? 1 : 0) + (A.prev_b[k] >= 0 ? 1 : 0) + (C.hold_pair && k == 0 ? 1 : 0);
         A.wait[k] = w;
         if (w == 0) list_push(list, &rcnt[0], k);
     }
@@ -333,9 +333,16 @@ __global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, int32_t* __rest
 // earlier pairs that share a particle with it, so the outcome equals
 // resolving the sorted queue one pair at a time.  The claims are in queue
 // order and a thread resolves its pair as soon as the slot is written, so
-// the wait always ends while the launch's threads are all resident; it is
-// bounded all the same, and reports kErrResolveStall if it ever gives up.
-constexpr int kSpinLimit = 1 << 22;
+// the wait ends however many of the launch's blocks are resident (slots are
+// claimed only by running threads); it is bounded all the same (half a
+// second), and reports kErrResolveStall if it ever gives up.
+constexpr unsigned long long kWaitLimitNs = 500000000ull;   // half a second
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ void queue_push(int32_t* list, int32_t* tail, int k) {
     cg::coalesced_group g = cg::coalesced_threads();
@@ -359,13 +366,15 @@ __global__ void __launch_bounds__(256) k_res_queue(ResolveArgs A, SimC C, int32_
         bool stalled = false;
         if (idx < np) {
             int k = *(volatile int32_t*)&list[idx];
-            for (int spin = 0; k < 0; spin++) {
-                if (spin >= kSpinLimit || (spin % 1024 == 1023 && (*(volatile int*)&A.ctl->err & kErrResolveStall))) {
+            const unsigned long long t0 = k < 0 ? global_ns() : 0ull;
+            while (k < 0) {
+                // bounded: half a second, or at once when another thread gave up
+                if ((*(volatile int*)&A.ctl->err & kErrResolveStall) || global_ns() - t0 > kWaitLimitNs) {
                     atomicOr(&A.ctl->err, kErrResolveStall);
                     stalled = true;
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(200);
                 k = *(volatile int32_t*)&list[idx];
             }
             if (!stalled) {
@@ -573,7 +582,7 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
                                          PR.next_a, PR.next_b);
     cudaMemsetAsync(PR.rcnt, 0, sizeof(int32_t) * 64, s);
     cudaMemsetAsync(PR.queue, 0xff, sizeof(int32_t) * (size_t)PR.cap, s);   // every slot unwritten
-    k_res_seed<<<grid, 256, 0, s>>>(A, PR.queue, PR.rcnt);
+    k_res_seed<<<grid, 256, 0, s>>>(A, C, PR.queue, PR.rcnt);
     // resident blocks only: a thread may wait for a slot that another writes
     const int qgrid = std::max(1, std::min(ceil_div(PR.cap, 256), g_queue_blocks));
     k_res_queue<<<qgrid, 256, 0, s>>>(A, C, PR.queue, PR.rcnt);

@@ -28,7 +28,7 @@ EXPORTS = [
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
     "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_autotune",
-    "rb_set_pair_capacity", "rb_set_launch_shape", "rb_set_n_active", "rb_set_restitution",
+    "rb_set_pair_capacity", "rb_debug_hold_pair", "rb_set_launch_shape", "rb_set_n_active", "rb_set_restitution",
 ]
 RB_MLP_PARAMS = 9347
 
@@ -105,6 +105,7 @@ def load():
     lib.rb_set_n_active.argtypes = [_P, C.c_int64]
     lib.rb_set_restitution.argtypes = [_P, i32, C.c_double, C.c_double]
     lib.rb_set_pair_capacity.argtypes = [_P, i64]
+    lib.rb_debug_hold_pair.argtypes = [_P, C.c_int]
     lib.rb_load_mlp.argtypes = [_P, _VP, i64, C.c_double]
     lib.rb_mlp_samples.argtypes = [_P, C.c_double, C.c_double, C.c_double, C.c_uint64, i64,
                                    C.POINTER(i64), _VP, _VP, _VP]
@@ -276,6 +277,10 @@ def rb_get_pairs(sim, box: int = 0):
 
 def rb_set_pair_capacity(sim, cap: int):
     _check(load().rb_set_pair_capacity(sim, cap), sim)
+
+
+def rb_debug_hold_pair(sim, on: bool):
+    _check(load().rb_debug_hold_pair(sim, 1 if on else 0), sim)
 
 
 def rb_set_time(sim, t: float):

@@ -1,6 +1,7 @@
 """Error handling through the C ABI without any GPU fault: the pair buffer
 overflow is repaired inside the step, bad inputs and states return their
-codes, and a position that overflows to infinity is reported."""
+codes, a position that overflows to infinity is reported, and the bounded
+wait of the resolution queue gives up with RB_ERR_TIMEOUT."""
 import numpy as np
 import pytest
 
@@ -76,3 +77,31 @@ def test_overflowing_position_is_reported(rb):
     with pytest.raises(rb.RbError) as e:
         s.step(1)
     assert e.value.code == rb.RB_ERR_NONFINITE
+
+
+def test_resolution_wait_is_bounded(rb):
+    """A pair held back from the resolution's ready queue (test hook) makes
+    the threads' bounded wait for its slot run out: the step reports
+    RB_ERR_TIMEOUT after about half a second, and the context stays usable
+    (a fresh upload steps normally, equal to an untouched simulation)."""
+    import time
+
+    L, N = 100.0, 2400
+    P = I.sheet(L, N, 1)
+    s = rb.Sim(**sheet(rb, L))
+    s.set_particles(P)
+    rb.rb_debug_hold_pair(s.h, True)
+    t0 = time.perf_counter()
+    with pytest.raises(rb.RbError) as e:
+        s.step(1)
+    assert e.value.code == rb.RB_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 20.0
+    rb.rb_debug_hold_pair(s.h, False)
+    s.set_particles(P)
+    s.step(2)
+    ref = rb.Sim(**sheet(rb, L))
+    ref.set_particles(P)
+    ref.step(2)
+    a, b = s.particles(), ref.particles()
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(a[k], b[k]), k
