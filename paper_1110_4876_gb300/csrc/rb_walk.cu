@@ -439,8 +439,9 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                     }
                     return true;
                 };
-                // two entries per pass; the warp-uniform flush into the
-                // compensated sums every 16 entries
+                // two entries per pass (one with the network or the band
+                // record inside, whose code is large); the warp-uniform flush
+                // into the compensated sums every 16 entries
                 for (;;) {
                     if (it != 0 && (it & 15) == 0) {
                         kadd(sx, cx, fx);
@@ -449,6 +450,10 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                         fx = fy = fz = 0.f;
                     }
                     if (!step()) break;
+                    if (kLearn || kRecord) {
+                        it += 1;
+                        continue;
+                    }
                     if (!step()) {
                         it += 1;
                         break;
