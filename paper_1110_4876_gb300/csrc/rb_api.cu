@@ -1047,7 +1047,7 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     const Ctl& c = s->hctl;
     out->steps = c.step;
     out->n_live = c.n_live;
-    out->cells = c.n_cells;
+    out->cells = c.n_entries > c.n_live ? c.n_entries - c.n_live : 0;   // one leaf per live particle
     out->pairs_found = c.pair_n;
     out->pairs_resolved = c.resolved;
     out->cell_interactions = (int64_t)c.n_cell;

@@ -64,7 +64,6 @@ struct Ctl {
     int n_live;                // live particles after the last sort
     int n_live_next;           // live particles counted by the keys kernel
     int n_entries;             // tree entries (cells + leaves) of the last build
-    int n_cells;
     int pair_count;            // pairs found by the last search (may exceed capacity)
     int pair_n;                // pairs to resolve (0 when the search overflowed)
     int pair_ends;             // 2 * pair_n

@@ -302,23 +302,39 @@ __global__ void __launch_bounds__(256) k_pair_prev(const uint64_t* __restrict__ 
     }
 }
 
-// Appends k to a list with one atomic per group of lanes appending together.
-__device__ __forceinline__ void list_push(int32_t* list, int32_t* count, int k) {
-    cg::coalesced_group g = cg::coalesced_threads();
-    int base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(count, (int)g.size());
-    list[g.shfl(base, 0) + (int)g.thread_rank()] = k;
-}
-
 // The queue's first slots: the pairs that are the first pair of both their
 // particles; every pair waits for as many predecessors as it has.
+// One atomic per block and pass: the block's ready pairs are ranked with a
+// block scan of warp ballots (their order in the queue does not matter).
 __global__ void __launch_bounds__(256) k_res_seed(ResolveArgs A, SimC C, int32_t* __restrict__ list,
                                                   int32_t* __restrict__ rcnt) {
+    __shared__ int wcount[8], base;
     const int n = A.ctl->pair_n;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int w = (A.prev_a[k] >= 0 ? 1 : 0) + (A.prev_b[k] >= 0 ? 1 : 0) + (C.hold_pair && k == 0 ? 1 : 0);
-        A.wait[k] = w;
-        if (w == 0) list_push(list, &rcnt[0], k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k0 = blockIdx.x * blockDim.x; k0 < n; k0 += gridDim.x * blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        bool ready = false;
+        if (k < n) {
+            const int w = (A.prev_a[k] >= 0 ? 1 : 0) + (A.prev_b[k] >= 0 ? 1 : 0) +
+                          (C.hold_pair && k == 0 ? 1 : 0);
+            A.wait[k] = w;
+            ready = w == 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ready);
+        if (lane == 0) wcount[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += wcount[q];
+            base = t ? atomicAdd(&rcnt[0], t) : 0;
+        }
+        __syncthreads();
+        if (ready) {
+            int pos = base + __popc(m & ((1u << lane) - 1u));
+            for (int q = 0; q < warp; q++) pos += wcount[q];
+            list[pos] = k;
+        }
+        __syncthreads();   // wcount and base are reused
     }
 }
 

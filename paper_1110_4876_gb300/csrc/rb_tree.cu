@@ -181,14 +181,6 @@ __global__ void k_box_roots(const int32_t* __restrict__ box_first,
     box_root[b] = box_first[b] < box_first[b + 1] ? start[box_first[b]] : -1;
 }
 
-__global__ void __launch_bounds__(256) k_count_cells(const int8_t* __restrict__ e_level,
-                                                     Ctl* __restrict__ ctl, int ecap) {
-    const int E = min(ctl->n_entries, ecap);
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool cell = k < E && e_level[k] != 22;
-    const unsigned b = __ballot_sync(0xffffffffu, cell);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&ctl->n_cells, __popc(b));
-}
 
 __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     x &= 0x1249249249249249ull;
@@ -699,9 +691,6 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
     k_box_ranges<<<ceil_div(n > C.nbox + 1 ? n : C.nbox + 1, 256), 256, 0, s>>>(
         P.box, ctl, n, C.nbox, T.box_first);
     k_box_roots<<<ceil_div(C.nbox, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
-    const int ne = T.cap_e;
-    cudaMemsetAsync(&ctl->n_cells, 0, sizeof(int), s);
-    k_count_cells<<<ceil_div(ne, 256), 256, 0, s>>>(T.e_level, ctl, ne);
 }
 
 void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
