@@ -57,6 +57,7 @@ def test_tree_cells_and_moments(rb, orc, L, N, seed):
     rs = {(d, frozenset(m.tolist())): (M, c, Q) for d, m, M, c, Q in ref}
     assert len(gs) == len(got)
     assert set(gs) == set(rs)
+    assert sim.stats()["cells"] == len(rs)   # entries minus one leaf per particle
     # the GPU sums children bottom-up, the oracle sums members in insertion
     # order: both are within n u (n <= 6000 terms, u = 1.1e-16) of the exact sums
     for k, (M, c, Q) in rs.items():
