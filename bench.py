@@ -86,9 +86,12 @@ def measured_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    """nvidia-smi sampling (every 20 ms, timestamped) of SM clocks and throttle
+    reasons.  The sampler starts before the warm-up, so it is running when the
+    timed window opens; window(t0, t1) marks that window in host time and
+    summary() keeps the samples taken inside it."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -96,6 +99,7 @@ class Clocks:
         self.gpu = gpu
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -103,11 +107,14 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
+
+    def window(self, t0: float, t1: float):
+        self.t0, self.t1 = t0, t1
 
     def __exit__(self, *a):
         if self.proc:
@@ -117,6 +124,17 @@ class Clocks:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    @staticmethod
+    def _epoch(stamp: str):
+        import datetime
+
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def summary(self):
         if not self.proc or not self.path:
             return None
@@ -124,17 +142,23 @@ class Clocks:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows
+        if self.t0 is not None:
+            inside = [r for r in rows if (t := self._epoch(r[0])) is not None and self.t0 <= t <= self.t1]
+        use = inside if inside else rows
+        sm = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in use if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in use for k in range(4) if r[6 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inside), "samples_whole_run": len(rows),
+                "window_s": (self.t1 - self.t0) if self.t0 is not None else None}
 
 
 def max_over_ranks(t_ms: float, dist, device) -> float:
@@ -181,6 +205,7 @@ def run_ours(args):
     sim.set_particles(P)
     tuned = rb.rb_autotune(sim.h)
     rb.rb_set_profiling(sim.h, True)
+    clk = Clocks(local).__enter__()   # sampling from before the warm-up
     sim.step(args.warmup)
 
     def barrier():
@@ -196,23 +221,25 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
-    with Clocks(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            sim.step(1)
-            st = sim.stats()
-            walk_ms.append(st["ms_stage"]["gravity_walk"])
-            walk_flops.append(FLOP_CELL * st["cell_interactions"] + FLOP_LEAF * st["leaf_interactions"]
-                              + FLOP_MAC * st["mac_tests"])
-            for k, v in st["ms_stage"].items():
-                stage_sum[k] = stage_sum.get(k, 0.0) + v
-            launches += st["kernels_per_step"]
-            pairs.append(st["pairs_found"])
-            corr.append(st["corrections"])
-            counts.append((st["cell_interactions"], st["leaf_interactions"], st["mac_tests"],
-                           st["warp_iterations"]))
-        e1.record(stream)
-        barrier()
+    tw0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+        st = sim.stats()
+        walk_ms.append(st["ms_stage"]["gravity_walk"])
+        walk_flops.append(FLOP_CELL * st["cell_interactions"] + FLOP_LEAF * st["leaf_interactions"]
+                          + FLOP_MAC * st["mac_tests"])
+        for k, v in st["ms_stage"].items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+        launches += st["kernels_per_step"]
+        pairs.append(st["pairs_found"])
+        corr.append(st["corrections"])
+        counts.append((st["cell_interactions"], st["leaf_interactions"], st["mac_tests"],
+                       st["warp_iterations"]))
+    e1.record(stream)
+    barrier()
+    clk.window(tw0, time.time())
+    clk.__exit__()
     t_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     clocks = clk.summary()
     value = whole_job_value(world, N_SHEET, args.steps, t_ms)
