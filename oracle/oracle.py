@@ -134,6 +134,9 @@ def load():
     lib.orc_collide_tree_sel.restype = C.c_int64
     lib.orc_collide_tree_sel.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _I64, C.c_int64,
                                          _I64, C.c_int64, _U64]
+    lib.orc_tree_collide_sel.restype = C.c_int64
+    lib.orc_tree_collide_sel.argtypes = [_VP, _PP, C.c_double, C.c_int64, _D, _D, _D, _D, _I64,
+                                         C.c_int64, _I64, C.c_int64, _U64]
     lib.orc_resolve.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _D, _D, _D, _I64,
                                 C.c_int64, _U64]
     lib.orc_drift.argtypes = [_PP, C.c_int64, _D, _D, _D, _D, _D, _D]
@@ -221,6 +224,21 @@ class Tree:
                         com[3 * c: 3 * c + 3].copy(), Q[6 * c: 6 * c + 6].copy()))
             off += int(count[c])
         return out
+
+    def collide(self, p: Params, t: float, r, ids, targets, cap=None):
+        """Sect. 5.2 search from the listed targets on this tree (unsorted keys);
+        the tree must be built over the positions the search uses."""
+        x, y, z = self._keep[:3]
+        r = _d(r)
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        sel = np.ascontiguousarray(targets, dtype=np.int64)
+        cap = cap or 16 * len(sel) + 16
+        keys = np.zeros(cap, dtype=np.uint64)
+        k = load().orc_tree_collide_sel(self.h, C.byref(p.c()), t, self.n, x, y, z, r, ids, len(sel),
+                                        sel, cap, keys)
+        if k > cap:
+            return self.collide(p, t, r, ids, targets, int(k))
+        return keys[:k].copy()
 
     def gravity(self, p: Params, t: float, targets=None, potential=False, counts=False):
         """Barnes-Hut accelerations (and potential, interaction counts)."""

@@ -713,15 +713,16 @@ int64_t orc_collide_tree(const orc_params* p, double t, int64_t n, const double*
 /* The same Eq. 3 search run only from the listed targets (pairs that one of
  * them records as the lower-id member); used to time the search on a
  * sample.  Returns the number of pairs found (first `cap` stored, unsorted). */
-int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const double* x,
-                             const double* y, const double* z, const double* r, const int64_t* id,
-                             int64_t nt, const int64_t* tsel, int64_t cap, uint64_t* keys) {
+/* Sect. 5.2 search from the listed targets on a tree already built over the
+ * same positions (Eq. 3 uses only the cells' geometry, so a tree built with
+ * any masses serves). */
+int64_t orc_tree_collide_sel(const orc_tree* tr, const orc_params* p, double t, int64_t n,
+                             const double* x, const double* y, const double* z, const double* r,
+                             const int64_t* id, int64_t nt, const int64_t* tsel, int64_t cap,
+                             uint64_t* keys) {
     double off[3 * ORC_MAXIMG], dvy[ORC_MAXIMG];
     int code[ORC_MAXIMG];
     int ni = orc_images(p, t, ORC_MAXIMG, off, dvy, code);
-    double* m1 = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
-    for (int64_t i = 0; i < n; i++) m1[i] = 1.0;
-    orc_tree* tr = orc_tree_build(n, x, y, z, m1, p->L[0]);
     double rmax = 0.0;
     for (int64_t i = 0; i < n; i++) rmax = r[i] > rmax ? r[i] : rmax;
     orc_pairbuf pb = {keys, 0, cap};
@@ -732,9 +733,19 @@ int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const dou
             if (n > 0) orc_csearch(tr, 0, pt, i, r[i], rmax, r, id, off + 3 * g, code[g], &pb);
         }
     }
+    return pb.k;
+}
+
+int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const double* x,
+                             const double* y, const double* z, const double* r, const int64_t* id,
+                             int64_t nt, const int64_t* tsel, int64_t cap, uint64_t* keys) {
+    double* m1 = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t i = 0; i < n; i++) m1[i] = 1.0;
+    orc_tree* tr = orc_tree_build(n, x, y, z, m1, p->L[0]);
+    int64_t k = orc_tree_collide_sel(tr, p, t, n, x, y, z, r, id, nt, tsel, cap, keys);
     orc_tree_free(tr);
     free(m1);
-    return pb.k;
+    return k;
 }
 
 /* ------------------------------------------------------------------------ */

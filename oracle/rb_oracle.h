@@ -75,6 +75,10 @@ int64_t orc_collide_tree(const orc_params* p, double t, int64_t n, const double*
 int64_t orc_collide_tree_sel(const orc_params* p, double t, int64_t n, const double* x,
                              const double* y, const double* z, const double* r, const int64_t* id,
                              int64_t nt, const int64_t* tsel, int64_t cap, uint64_t* keys);
+int64_t orc_tree_collide_sel(const orc_tree* tr, const orc_params* p, double t, int64_t n,
+                             const double* x, const double* y, const double* z, const double* r,
+                             const int64_t* id, int64_t nt, const int64_t* tsel, int64_t cap,
+                             uint64_t* keys);
 /* plane sweep (Sect. 5.3): straight-line criterion over tau in [-dt/2, dt/2] */
 int64_t orc_collide_line_brute(const orc_params* p, double t, int64_t n, const double* x,
                                const double* y, const double* z, const double* vx, const double* vy,

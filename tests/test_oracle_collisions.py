@@ -146,3 +146,19 @@ def test_target_subset_search_is_a_subset_of_the_full_search(orc):
     a, _, _ = orc.decode_pairs(full)
     assert part.tolist() == full[np.isin(a, sel)].tolist()
     assert np.sort(orc.collide_tree_targets(p, 5.0, x, y, z, r, ids, ids)).tolist() == full.tolist()
+
+
+def test_search_on_a_gravity_tree_equals_the_own_tree_search(orc):
+    """Eq. 3 reads only the cells' geometry: the search from targets on a
+    tree built with the particles' real masses finds exactly the pairs of
+    the search that builds its own tree."""
+    L = 30.0
+    x, y, z, r = _dense(11, L=L)
+    ids = np.arange(len(x), dtype=np.int64)
+    m = np.random.default_rng(3).uniform(0.5, 2.0, len(x))
+    p = orc.Params(omega=0.02, L=(L, L, L), nghost=(1, 1, 0), boundary=2)
+    sel = np.arange(1, len(x), 2)
+    own = np.sort(orc.collide_tree_targets(p, 5.0, x, y, z, r, ids, sel))
+    reuse = np.sort(orc.Tree(x, y, z, m, L).collide(p, 5.0, r, ids, sel))
+    assert len(own) > 10
+    assert reuse.tolist() == own.tolist()
