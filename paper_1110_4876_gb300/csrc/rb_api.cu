@@ -193,6 +193,7 @@ int box_params(rb_sim* s) {
         p.L = s->hb[b].L[0];
         p.Lx = s->hb[b].L[0]; p.Ly = s->hb[b].L[1]; p.Lz = s->hb[b].L[2];
         p.key_scale = (1.0 / p.L) * 2097152.0;   // exact scaling of the rounded reciprocal
+        p.hx = 0.5 * p.Lx; p.hy = 0.5 * p.Ly; p.hz = 0.5 * p.Lz;
         p.shear_speed = s->cfg.boundary == RB_BC_SHEAR ? (1.5 * s->cfg.omega) * p.Lx : 0.0;
         p.base_id = b < (int)s->base.size() ? (int)s->base[b] : 0;
         p.n_active = s->n_active < 0 ? 0x7fffffff : (int)std::min<int64_t>(s->n_active, 0x7fffffff);

@@ -31,9 +31,9 @@ struct BoxP {
     double Lx, Ly, Lz;   // box sides (periodic lengths)
     double shear_speed;  // (1.5 * Omega) * Lx for shear-periodic boxes, else 0
     double key_scale;    // (1 / L, rounded) x 2^21, for the fast path of the integer coordinates
+    double hx, hy, hz;   // half sides Lx / 2, Ly / 2, Lz / 2 (exact)
     int base_id;         // global id of the box's particle 0
     int n_active;        // particles with id - base_id >= n_active exert no gravity
-    double pad;
 };
 
 // Constants of a simulation, passed by value to kernels.

@@ -31,20 +31,42 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 }
 
 // Integer coordinate floor(((x - lo) / L) * 2^21), clamped to [0, 2^21 - 1].
-// The quotient is first taken as (x - lo) * (1/L), within 2^-51 of the
-// correctly rounded quotient, i.e. within 2^-30 on the 2^21 grid; unless
-// that lands within 1e-7 of a grid line (about one coordinate in 10^7), the
-// floor is the same and the FP64 division is skipped.  scale = (1/L) 2^21:
-// scaling by a power of two commutes with rounding, so one multiply does.
+// k = (x - lo) * scale, with scale = (1/L, rounded) x 2^21 (a power-of-two
+// scaling, so no further rounding), lies within 2^-30 of the oracle's
+// fl((x - lo) / L) x 2^21; wherever k is at least 2^-23 from every grid line
+// both have the same floor.  For k in [1, 2^21) the floor and that distance
+// are read from k's bits with integer operations: on GB300 an FP64
+// instruction holds the SM's FP64 pipe 16 cycles per warp, and this kernel's
+// time is its FP64 instructions.  Other k and the few near a grid line take
+// the FP64 division.
 __device__ __forceinline__ uint32_t icoord(double x, double lo, double L, double scale) {
     const double d = __dsub_rn(x, lo);
-    double k = __dmul_rn(d, scale);
-    const double f = floor(k);
-    if (k - f < 1e-7 || f + 1.0 - k < 1e-7) k = __dmul_rn(__ddiv_rn(d, L), 2097152.0);
-    k = floor(k);
+    const uint64_t b = (uint64_t)__double_as_longlong(__dmul_rn(d, scale));
+    const int e = (int)(b >> 52) - 1023;   // unbiased exponent (sign set or NaN: e > 20)
+    if (e >= 0 && e <= 20) {
+        const int sh = 52 - e;             // fraction bits of k
+        const uint64_t m = (b & 0xfffffffffffffull) | (1ull << 52);
+        const uint64_t one = 1ull << sh, fr = m & (one - 1), tol = 1ull << (sh - 23);
+        if (fr >= tol && one - fr >= tol) return (uint32_t)(m >> sh);
+    }
+    double k = floor(__dmul_rn(__ddiv_rn(d, L), 2097152.0));
     if (!(k >= 0.0)) k = 0.0;
     if (k > 2097151.0) k = 2097151.0;
     return (uint32_t)k;
+}
+
+// Order-preserving integer image of a double: for a, b not NaN (and -0 not
+// compared with +0), a < b exactly when dord(a) < dord(b), and for h > 0,
+// dord(-h) = ~dord(h).  The boundary tests compare this way, without FP64
+// instructions.  A NaN coordinate compares as beyond every bound; the
+// non-finite check after the wrap reports it either way.
+__device__ __forceinline__ int64_t dord(double v) {
+    const int64_t b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
 }
 
 __device__ __forceinline__ double time_at(const Ctl* ctl, const SimC& C, int hs) {
@@ -78,32 +100,40 @@ constexpr int kMaxWraps = 1 << 12;
 // boundary.  *runaway is set when the wraps did not bring it back.
 __device__ __forceinline__ bool wrap_one(const SimC& C, const BoxP& bp, const Ctl* ctl, int hs, double& x,
                                          double& y, double& z, double& vy, bool* runaway) {
-    const double hx = 0.5 * bp.Lx, hy = 0.5 * bp.Ly, hz = 0.5 * bp.Lz;
-    if (C.boundary == 0)
-        return !(x < -hx || x >= hx || y < -hy || y >= hy || z < -hz || z >= hz);
+    const int64_t ux = dord(bp.hx), uy = dord(bp.hy), uz = dord(bp.hz);   // ~u is -h
+    if (C.boundary == 0) {
+        const int64_t ox = dord(x), oy = dord(y), oz = dord(z);
+        return !(ox < ~ux || ox >= ux || oy < ~uy || oy >= uy || oz < ~uz || oz >= uz);
+    }
     const double vs = bp.shear_speed;
+    const int64_t ox = dord(x);
+    const bool up = ox >= ux, down = ox < ~ux;
     // the shear offset only for the few particles that cross in x
-    const double s =
-        (x >= hx || x < -hx) && vs != 0.0 ? fmod(__dmul_rn(vs, time_at(ctl, C, hs)), bp.Ly) : 0.0;
-    if (x >= hx) {
+    const double s = (up || down) && (__double_as_longlong(vs) << 1) != 0
+                         ? fmod(__dmul_rn(vs, time_at(ctl, C, hs)), bp.Ly)
+                         : 0.0;
+    if (up) {
         x = __dsub_rn(x, bp.Lx);
         y = __dadd_rn(y, s);
         vy = __dadd_rn(vy, vs);
-    } else if (x < -hx) {
+    } else if (down) {
         x = __dadd_rn(x, bp.Lx);
         y = __dsub_rn(y, s);
         vy = __dsub_rn(vy, vs);
     }
-    for (int k = 0; k < kMaxWraps && y >= hy; k++) y = __dsub_rn(y, bp.Ly);
-    for (int k = 0; k < kMaxWraps && y < -hy; k++) y = __dadd_rn(y, bp.Ly);
-    if (y >= hy || y < -hy) *runaway = true;
+    for (int k = 0; k < kMaxWraps && dord(y) >= uy; k++) y = __dsub_rn(y, bp.Ly);
+    for (int k = 0; k < kMaxWraps && dord(y) < ~uy; k++) y = __dadd_rn(y, bp.Ly);
+    const int64_t oy = dord(y);
+    if (oy >= uy || oy < ~uy) *runaway = true;
     if (C.z_periodic) {
-        for (int k = 0; k < kMaxWraps && z >= hz; k++) z = __dsub_rn(z, bp.Lz);
-        for (int k = 0; k < kMaxWraps && z < -hz; k++) z = __dadd_rn(z, bp.Lz);
-        if (z >= hz || z < -hz) *runaway = true;
+        for (int k = 0; k < kMaxWraps && dord(z) >= uz; k++) z = __dsub_rn(z, bp.Lz);
+        for (int k = 0; k < kMaxWraps && dord(z) < ~uz; k++) z = __dadd_rn(z, bp.Lz);
+        const int64_t oz = dord(z);
+        if (oz >= uz || oz < ~uz) *runaway = true;
         return true;
     }
-    return !(z < -hz || z >= hz);
+    const int64_t oz = dord(z);
+    return !(oz < ~uz || oz >= uz);
 }
 
 struct DriftArgs {
@@ -140,14 +170,14 @@ __global__ void __launch_bounds__(256) k_drift_keys(DriftArgs A, SimC C) {
             drift_one(C, x, y, z, vx, vy, vz);
             live = wrap_one(C, bp, A.ctl, A.hs + d, x, y, z, vy, &runaway);
         }
-        if (runaway || !(isfinite(x) && isfinite(y) && isfinite(z))) {
+        if (runaway || !(finite_bits(x) && finite_bits(y) && finite_bits(z))) {
             atomicOr(&A.ctl->err, kErrNonFinite);
             live = false;
         }
         A.P.x[i] = x; A.P.y[i] = y; A.P.z[i] = z;
         A.P.vx[i] = vx; A.P.vy[i] = vy; A.P.vz[i] = vz;
         if (live) {
-            const double lo = -0.5 * bp.L;
+            const double lo = -bp.hx;   // the root cube's side L is Lx
             key = (spread3(icoord(x, lo, bp.L, bp.key_scale)) << 2) |
                   (spread3(icoord(y, lo, bp.L, bp.key_scale)) << 1) |
                   spread3(icoord(z, lo, bp.L, bp.key_scale));
