@@ -268,6 +268,11 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                     sub_hilo(phy, ply, oh.y, ol.y, thy, tly);
                     sub_hilo(phz, plz, oh.z, ol.z, thz, tlz);
                 }
+                // negated target (x, y) pairs for the packed FP32 adds (two
+                // adds per instruction on sm_103a, and the walk is bound by
+                // instruction issue): a - t = a + (-t) exactly, so they give
+                // the scalar differences bit for bit
+                const float2 nth = make_float2(-thx, -thy), ntl = make_float2(-tlx, -tly);
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
                 float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // sums of the last <= 16 iterations
@@ -284,8 +289,9 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                     const float4 ra = __ldg(&A.ra[e]);
                     const float4 rb = __ldg(&A.rb[e]);
                     const bool act = next == e;
-                    const float dx = (ra.x - thx) + (rb.x - tlx);
-                    const float dy = (ra.y - thy) + (rb.y - tly);
+                    const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(ra.x, ra.y), nth),
+                                                  __fadd2_rn(make_float2(rb.x, rb.y), ntl));
+                    const float dx = dxy.x, dy = dxy.y;
                     const float dz = (ra.z - thz) + (rb.z - tlz);
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (__float_as_int(ra.w) < 0) {
@@ -737,6 +743,7 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                     sub_hilo(phy, ply, oh.y, ol.y, thy, tly);
                     sub_hilo(phz, plz, oh.z, ol.z, thz, tlz);
                 }
+                const float2 nth = make_float2(-thx, -thy), ntl = make_float2(-tlx, -tly);
                 int next = (valid && root >= 0) ? root : kEnd;
                 for (;;) {
                     if (next >= wend) next = kEnd;
@@ -751,8 +758,9 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                             const int j = ~__float_as_int(ra.w);
                             if (j > i) {
                                 const float4 rb = __ldg(&A.rb[e]);
-                                const float dx = (ra.x - thx) + (rb.x - tlx);
-                                const float dy = (ra.y - thy) + (rb.y - tly);
+                                const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(ra.x, ra.y), nth),
+                                                              __fadd2_rn(make_float2(rb.x, rb.y), ntl));
+                                const float dx = dxy.x, dy = dxy.y;
                                 const float dz = (ra.z - thz) + (rb.z - tlz);
                                 const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                                 const float sr = prf + rb.w;
@@ -787,8 +795,12 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                             // positions; opened unless farther than R_i + R_max, or
                             // unless every particle below sits at a slot <= i (those
                             // pairs are examined from the other particle)
-                            const float ex = fmaxf(fmaxf((ra.x - thx) - tlx, (thx - rb.x) + tlx), 0.f);
-                            const float ey = fmaxf(fmaxf((ra.y - thy) - tly, (thy - rb.y) + tly), 0.f);
+                            // (t - b) + l = -((b - t) - l) exactly, so the upper side
+                            // comes negated out of the same packed adds
+                            const float2 u = __fadd2_rn(__fadd2_rn(make_float2(ra.x, ra.y), nth), ntl);
+                            const float2 v = __fadd2_rn(__fadd2_rn(make_float2(rb.x, rb.y), nth), ntl);
+                            const float ex = fmaxf(fmaxf(u.x, -v.x), 0.f);
+                            const float ey = fmaxf(fmaxf(u.y, -v.y), 0.f);
                             const float ez = fmaxf(fmaxf((ra.z - thz) - tlz, (thz - rb.z) + tlz), 0.f);
                             const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                             const float lim = (prf + A.rmaxf) * 1.0001f +
@@ -796,8 +808,9 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                             next = (__float_as_int(ra.w) > i && d2 < lim * lim) ? e + 1
                                                                                 : __float_as_int(rb.w);
                         } else {
-                            const float dx = (ra.x - thx) + (rb.x - tlx);
-                            const float dy = (ra.y - thy) + (rb.y - tly);
+                            const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(ra.x, ra.y), nth),
+                                                          __fadd2_rn(make_float2(rb.x, rb.y), ntl));
+                            const float dx = dxy.x, dy = dxy.y;
                             const float dz = (ra.z - thz) + (rb.z - tlz);
                             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                             const float lim = (prf + ra.w) * 1.00002f;
