@@ -834,9 +834,9 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
             }
 }
 
-template <bool kAABB>
 // At most 40 registers (6 blocks of 256 threads per SM): the search is
 // latency-bound, and 48 resident warps per SM instead of 40 took 4% off it.
+template <bool kAABB>
 __global__ void __launch_bounds__(kMaxWalkBlock, 6) k_collide(CollArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
