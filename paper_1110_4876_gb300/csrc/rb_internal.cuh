@@ -117,7 +117,12 @@ struct Tree {
     int8_t* e_level;            // depth of a cell; 22 marks a particle leaf
     int32_t* leaf_of;           // per particle: its leaf entry
     double *M, *cx, *cy, *cz, *Q;   // FP64 moments per entry (Q: 6 x cap, xx yy zz xy xz yz)
-    Rec4 ra, rb, rq0, rq1;          // FP32 walk records (pairs ra/rb, rq0/rq1 interleaved)
+    // FP32 walk records (pairs ra/rb, rq0/rq1 interleaved).  Gravity: ra =
+    // (x_hi, y_hi, z_hi, z_lo), rb = (x_lo, y_lo, -m for a leaf or
+    // (w / theta)^2 for a cell, skip entry), so the hi/lo pairs that the walk
+    // subtracts from the target sit in aligned register pairs.  The collision
+    // records written over them later in the step have their own layout.
+    Rec4 ra, rb, rq0, rq1;
     Rec4 rc_hi, rc_lo;              // FP32 cell corner (hi/lo) + width, inside test
     double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
     int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)

@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(256) k_leaf_records(GravRecArgs A) {
         split_hilo(x, hx, lx);
         split_hilo(y, hy, ly);
         split_hilo(z, hz, lz);
-        A.ra[e] = make_float4(hx, hy, hz, -(float)m);
-        A.rb[e] = make_float4(lx, ly, lz, __int_as_float(e + 1));
+        A.ra[e] = make_float4(hx, hy, hz, lz);
+        A.rb[e] = make_float4(lx, ly, -(float)m, __int_as_float(e + 1));
     }
 }
 
@@ -333,10 +333,10 @@ __device__ __forceinline__ void mom_add(const GravRecArgs& A, int c, double ox, 
         const float4 h = A.ra[c], l = A.rb[c];
         const float fx = (h.x - h0.x) + (l.x - l0.x);
         const float fy = (h.y - h0.y) + (l.y - l0.y);
-        const float fz = (h.z - h0.z) + (l.z - l0.z);
+        const float fz = (h.z - h0.z) + (h.w - h0.w);
         float fm;
         if (leaf) {
-            fm = -h.w;
+            fm = -l.z;
         } else {
             const float4 c0 = A.rq0[c], c1 = A.rq1[c];
             fm = c0.x;
@@ -427,8 +427,8 @@ __device__ __forceinline__ void mom_finish(const GravRecArgs& A, int k, int dept
         split_hilo(cy, hy, ly);
         split_hilo(cz, hz, lz);
         const float crit = group ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
-        A.ra[k] = make_float4(hx, hy, hz, crit);
-        A.rb[k] = make_float4(lx, ly, lz, __int_as_float(end));
+        A.ra[k] = make_float4(hx, hy, hz, lz);
+        A.rb[k] = make_float4(lx, ly, crit, __int_as_float(end));
         if (kF32Q) {
             A.rq0[k] = make_float4((float)S.M, S.qf[0], S.qf[1], S.qf[2]);
             A.rq1[k] = make_float4(S.qf[3], S.qf[4], S.qf[5], 0.f);

@@ -273,6 +273,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                 // instruction issue): a - t = a + (-t) exactly, so they give
                 // the scalar differences bit for bit
                 const float2 nth = make_float2(-thx, -thy), ntl = make_float2(-tlx, -tly);
+                const float2 ntz = make_float2(-thz, -tlz);   // z: (hi, lo) of the target
                 const int self = (gx == 0 && gy == 0 && gz == 0) ? self_leaf : -1;
                 int next = (valid && root >= 0) ? root : kEnd;
                 float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;   // sums of the last <= 16 iterations
@@ -292,13 +293,15 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                     const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(ra.x, ra.y), nth),
                                                   __fadd2_rn(make_float2(rb.x, rb.y), ntl));
                     const float dx = dxy.x, dy = dxy.y;
-                    const float dz = (ra.z - thz) + (rb.z - tlz);
+                    const float2 zz = __fadd2_rn(make_float2(ra.z, ra.w), ntz);
+                    const float dz = zz.x + zz.y;
+                    const float crit = rb.z;   // leaf: -m; cell: (w / theta)^2
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    if (__float_as_int(ra.w) < 0) {
+                    if (__float_as_int(crit) < 0) {
                         // particle leaf: exact term of Eq. 1
                         if (act) {
                             if (e != self) {
-                                const float m = -ra.w;
+                                const float m = -crit;
                                 const float inv = rsqrt_nr(kSoft ? r2 + A.soft2f : r2);
                                 const float f = m * (inv * inv * inv);
                                 fx = fmaf(f, dx, fx);
@@ -311,8 +314,8 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                         }
                     } else if (act) {
                         nmac++;
-                        bool acc = ra.w < r2;
-                        if (fabsf(ra.w - r2) <= 1e-5f * r2) {
+                        bool acc = crit < r2;
+                        if (fabsf(crit - r2) <= 1e-5f * r2) {
                             // the FP64 target point x - o, as the oracle forms it
                             acc = mac64(ld_d4(&A.d_a[e]), A.theta2, __dsub_rn(A.x[ii], itab[gi].ox),
                                         __dsub_rn(A.y[ii], itab[gi].oy), __dsub_rn(A.z[ii], itab[gi].oz));
@@ -362,7 +365,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                             fz = fmaf(fc, dz, fz);
                             ncell++;
                             next = __float_as_int(rb.w);
-                            if (kLearn && ra.w > A.band_scale * r2) {
+                            if (kLearn && crit > A.band_scale * r2) {
                                 // network inputs (the oracle's definition, in FP32 from the
                                 // walk records): r = p - com = -d
                                 const float4 ch = __ldg(&A.rc_hi[e]);
@@ -380,7 +383,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                                 fin[4] = __log2f((float)__ldg(&A.e_count[e])) * 0.30102999566f;
                                 fin[5] = ((ra.x - ch.x) + (rb.x - cl.x)) * rw - 0.5f;
                                 fin[6] = ((ra.y - ch.y) + (rb.y - cl.y)) * rw - 0.5f;
-                                fin[7] = ((ra.z - ch.z) + (rb.z - cl.z)) * rw - 0.5f;
+                                fin[7] = ((ra.z - ch.z) + (ra.w - cl.z)) * rw - 0.5f;
                                 fin[8] = hx * ux + hy * uy + hz * uz;
                                 fin[9] = sqrtf(ux * ux + uy * uy + uz * uz);
                                 fin[10] = qxx * qxx + qyy * qyy + qzz * qzz +
@@ -390,7 +393,7 @@ __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp:
                                 funit = q0.x * inv2;
                                 want = true;
                             }
-                            if (kRecord && ra.w > A.band_scale * r2) {
+                            if (kRecord && crit > A.band_scale * r2) {
                                 const uint32_t code = (gx + 7) | ((gy + 7) << 4) | ((gz + 7) << 8);
                                 rec = A.thresh == 0xffffffffu ||
                                       req_hash((uint32_t)i, (uint32_t)e, code, A.seed) < A.thresh;
