@@ -80,3 +80,37 @@ def test_step_pairs_at_edge_sizes(rb, orc, n):
         found += len(ref)
     if n > 2:
         assert found > 0
+
+
+@pytest.mark.parametrize("boundary", [0, 1, 2])
+def test_positions_on_the_box_faces(rb, orc, boundary):
+    """Particles at rest exactly on the box faces, one ulp inside and outside
+    them, and on Morton grid lines: one drift-only step (open, periodic and
+    shear-periodic boxes) keeps, wraps or removes each of them exactly as the
+    oracle does, bit for bit."""
+    L = 16.0
+    h = L / 2
+    edge = np.array([-h, h, np.nextafter(-h, 0.0), np.nextafter(h, 0.0), np.nextafter(-h, -np.inf),
+                     np.nextafter(h, np.inf), 0.0, -0.0, L / 2 ** 21 - h, np.nextafter(L / 2 ** 21 - h, 0.0)])
+    g = np.random.default_rng(31)
+    k = len(edge)
+    x = np.concatenate([edge, g.choice(edge, 3 * k), g.uniform(-h, h, 40)])
+    n = len(x)
+    y = np.concatenate([g.uniform(-h, h, k), g.choice(edge, 3 * k), g.choice(edge, 40)])
+    z = np.concatenate([g.uniform(-1, 1, k + 3 * k), g.choice(edge[[0, 2, 3, 6, 7, 8, 9]], 40)])
+    zero = np.zeros(n)
+    bc = (rb.RB_BC_OPEN, rb.RB_BC_PERIODIC, rb.RB_BC_SHEAR)[boundary]
+    sim = rb.Sim(G=1.0, omega=1e-3, box=(L, L, L), nghost=(1, 1, 0), boundary=bc,
+                 integrator=rb.RB_INT_LEAPFROG, dt=0.01, gravity=0, collisions=0)
+    sim.set_particles((x, y, z, zero, zero, zero, np.ones(n), zero))
+    sim.step(1)
+    got = sim.particles()
+    p = orc.Params(omega=1e-3, L=(L, L, L), nghost=(1, 1, 0), boundary=boundary, integrator=0, dt=0.01,
+                   gravity=0, collisions=0)
+    st = orc.State(p, x, y, z, zero, zero, zero, np.ones(n), zero)
+    st.step(1)
+    assert got["id"].tolist() == st.id.tolist()
+    for key in ("x", "y", "z", "vy"):
+        assert np.array_equal(got[key], getattr(st, key)), key
+    if boundary:
+        assert np.any(got["x"] == -h) and not np.any(got["x"] >= h)
