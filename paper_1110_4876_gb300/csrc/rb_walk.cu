@@ -837,10 +837,12 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
             }
 }
 
-// At most 40 registers (6 blocks of 256 threads per SM): the search is
-// latency-bound, and 48 resident warps per SM instead of 40 took 4% off it.
+// At most 32 registers (8 blocks of 256 threads per SM, every warp slot
+// resident): the search is latency-bound, and going from 40 resident warps
+// per SM (48 registers) to 48 (40) and 64 (32, with a few spilled values)
+// took 4% and another 2% off it.
 template <bool kAABB>
-__global__ void __launch_bounds__(kMaxWalkBlock, 6) k_collide(CollArgs A) {
+__global__ void __launch_bounds__(kMaxWalkBlock, 8) k_collide(CollArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
     for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile))
