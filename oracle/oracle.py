@@ -148,6 +148,7 @@ def load():
                              _D, _I64, _VP, _VP, _VP, C.c_int64, _VP, C.POINTER(C.c_int64)]
     lib.orc_energy.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _D, _D, _D,
                                C.POINTER(C.c_double), _D]
+    lib.orc_energy_terms.argtypes = [_PP, C.c_double, C.c_int64, _D, _D, _D, _D, _D, _D, _D, _D]
     _lib = lib
     return lib
 
@@ -370,6 +371,20 @@ class State:
         load().orc_energy(C.byref(self.p.c()), t, self.n, self.x, self.y, self.z, self.vx,
                           self.vy, self.vz, self.m, C.byref(E), P)
         return E.value, P
+
+    def energy_terms(self, t=None):
+        """(K, U, W, P): kinetic, SEI tidal + vertical, gravitational (half
+        the sum of m phi) and the momentum vector (Sect. 6.2)."""
+        return energy_terms(self.p, time_at(self.p, 2 * self.step_index) if t is None else t,
+                            self.x, self.y, self.z, self.vx, self.vy, self.vz, self.m)
+
+
+def energy_terms(p: Params, t: float, x, y, z, vx, vy, vz, m):
+    """(K, U, W, P) of Sect. 6.2 for the given particles at time t."""
+    out = np.zeros(6)
+    arrs = [_d(a) for a in (x, y, z, vx, vy, vz, m)]
+    load().orc_energy_terms(C.byref(p.c()), t, len(arrs[0]), *arrs, out)
+    return out[0], out[1], out[2], out[3:].copy()
 
 
 def drift(p: Params, x, y, z, vx, vy, vz):

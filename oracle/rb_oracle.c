@@ -893,10 +893,12 @@ int64_t orc_collide_sweep(const orc_params* p, double t, int64_t n, const double
 /* Resolution of the collision queue (Sect. 5, Eq. 2; reading R8): pairs in
  * ascending key order; a pair is skipped unless the particles approach; the
  * relative normal velocity is multiplied by -eps and momentum is conserved.
- * Later pairs see the velocities left by earlier ones.  With u = v_b - v_a
- * and r = x_b - x_a, the normal velocity changes by -(1 + eps) (u.r)/|r|, so
- * v_a gains (1 + eps) (m_b/M) (u.r)/|r|^2 r and v_b loses the same with m_a
- * (M = m_a + m_b): the impulse along n = r/|r| written without forming n. */
+ * Later pairs see the velocities left by earlier ones.  The steps follow the
+ * equation: with r = x_b - x_a (ghost offset included) and u = v_b - v_a
+ * (ghost shear velocity included), n = r/|r|, v_n = u.n, the change of the
+ * normal velocity is Delta = -(1 + eps) v_n, and the two particles share it
+ * in inverse proportion to their masses (M = m_a + m_b):
+ * v_a -= (m_b/M) Delta n, v_b += (m_a/M) Delta n. */
 void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, const double* y,
                  const double* z, double* vx, double* vy, double* vz, const double* m,
                  const int64_t* id, int64_t npairs, const uint64_t* keys) {
@@ -916,19 +918,20 @@ void orc_resolve(const orc_params* p, double t, int64_t n, const double* x, cons
         double rx = (x[b] + o[0]) - x[a], ry = (y[b] + o[1]) - y[a], rz = (z[b] + o[2]) - z[a];
         double ux = vx[b] - vx[a], uy = (vy[b] + dvg) - vy[a], uz = vz[b] - vz[a];
         double rv = (rx * ux + ry * uy) + rz * uz;
-        if (rv >= 0.0) continue; /* not approaching */
-        double r2 = (rx * rx + ry * ry) + rz * rz;
+        if (rv >= 0.0) continue; /* not approaching (Sect. 5.1) */
+        double rr = sqrt((rx * rx + ry * ry) + rz * rz);
+        double nx = rx / rr, ny = ry / rr, nz = rz / rr;
+        double vn = (ux * nx + uy * ny) + uz * nz;
         double e = p->eps;
-        if (p->eps_law == 1) { /* reading V1: |v_n| = |u.r| / |r| */
-            double vn = rv / sqrt(r2);
+        if (p->eps_law == 1) { /* reading V1 */
             double q = pow(fabs(vn) / p->eps_vc, -p->eps_p);
             e = q < 1.0 ? q : 1.0;
         }
+        double dlt = -(1.0 + e) * vn;
         double mt = m[a] + m[b];
-        double g = ((1.0 + e) * rv) / (r2 * mt);
-        double ga = g * m[b], gb = g * m[a];
-        vx[a] = vx[a] + ga * rx; vy[a] = vy[a] + ga * ry; vz[a] = vz[a] + ga * rz;
-        vx[b] = vx[b] - gb * rx; vy[b] = vy[b] - gb * ry; vz[b] = vz[b] - gb * rz;
+        double fa = (m[b] / mt) * dlt, fb = (m[a] / mt) * dlt;
+        vx[a] = vx[a] - fa * nx; vy[a] = vy[a] - fa * ny; vz[a] = vz[a] - fa * nz;
+        vx[b] = vx[b] + fb * nx; vy[b] = vy[b] + fb * ny; vz[b] = vz[b] + fb * nz;
     }
     free(slot);
 }
@@ -1013,12 +1016,14 @@ int orc_step(const orc_params* p, int64_t step, int64_t* n, double* x, double* y
     return 0;
 }
 
-/* Energy and momentum (Sect. 6.2): E = K + W (+ the Hill tidal and vertical
- * terms for SEI), P = sum m v.  W = (1/2) sum m_i phi_i with phi from the same
- * gravity module as the step (tree potential at theta, or direct sum). */
-void orc_energy(const orc_params* p, double t, int64_t n, const double* x, const double* y,
-                const double* z, const double* vx, const double* vy, const double* vz,
-                const double* m, double* E, double* P) {
+/* Energy and momentum terms (Sect. 6.2): K = sum m |v|^2 / 2, the Hill
+ * tidal and vertical term U = sum m (Omega_z^2 z^2 / 2 - 3/2 Omega^2 x^2)
+ * for SEI (0 for leap-frog), W = (1/2) sum m_i phi_i with phi from the same
+ * gravity module as the step (tree potential at theta, or direct sum), and
+ * P = sum m v.  terms[0..5] = K, U, W, P_x, P_y, P_z. */
+void orc_energy_terms(const orc_params* p, double t, int64_t n, const double* x, const double* y,
+                      const double* z, const double* vx, const double* vy, const double* vz,
+                      const double* m, double* terms) {
     double K = 0.0, U = 0.0, W = 0.0, px = 0.0, py = 0.0, pz = 0.0;
     double O = p->omega, Oz = p->omega_z > 0.0 ? p->omega_z : p->omega;
     for (int64_t i = 0; i < n; i++) {
@@ -1036,6 +1041,16 @@ void orc_energy(const orc_params* p, double t, int64_t n, const double* x, const
         for (int64_t i = 0; i < n; i++) W = W + 0.5 * m[i] * buf[3 * n + i];
         free(buf);
     }
-    *E = K + U + W;
-    P[0] = px; P[1] = py; P[2] = pz;
+    terms[0] = K; terms[1] = U; terms[2] = W;
+    terms[3] = px; terms[4] = py; terms[5] = pz;
+}
+
+/* Energy and momentum (Sect. 6.2): E = K + U + W, P = sum m v. */
+void orc_energy(const orc_params* p, double t, int64_t n, const double* x, const double* y,
+                const double* z, const double* vx, const double* vy, const double* vz,
+                const double* m, double* E, double* P) {
+    double tm[6];
+    orc_energy_terms(p, t, n, x, y, z, vx, vy, vz, m, tm);
+    *E = tm[0] + tm[1] + tm[2];
+    P[0] = tm[3]; P[1] = tm[4]; P[2] = tm[5];
 }

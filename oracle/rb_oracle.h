@@ -106,5 +106,9 @@ int  orc_step(const orc_params* p, int64_t step, int64_t* n, double* x, double* 
 void orc_energy(const orc_params* p, double t, int64_t n, const double* x, const double* y,
                 const double* z, const double* vx, const double* vy, const double* vz,
                 const double* m, double* E, double* P);
+/* terms = K, U (SEI tidal + vertical), W, P_x, P_y, P_z */
+void orc_energy_terms(const orc_params* p, double t, int64_t n, const double* x, const double* y,
+                      const double* z, const double* vx, const double* vy, const double* vz,
+                      const double* m, double* terms);
 
 #endif

@@ -162,3 +162,43 @@ def test_search_on_a_gravity_tree_equals_the_own_tree_search(orc):
     reuse = np.sort(orc.Tree(x, y, z, m, L).collide(p, 5.0, r, ids, sel))
     assert len(own) > 10
     assert reuse.tolist() == own.tolist()
+
+
+def test_oblique_collision_hand_values(orc):
+    """Eq. 2 on an oblique pair of unequal masses, against values worked out
+    by hand: r = (1.2, 1.6, 0), n = (0.6, 0.8, 0), u = v_b - v_a =
+    (-2, -1, -0.5), v_n = -2, Delta = -(1 + 0.5) v_n = 3, M = 4;
+    v_a -= (3/4) Delta n, v_b += (1/4) Delta n."""
+    p = orc.Params(L=(10.0,) * 3, eps=0.5)
+    x = np.array([0.0, 1.2]); y = np.array([0.0, 1.6]); z = np.zeros(2)
+    vx = np.array([1.0, -1.0]); vy = np.array([0.0, -1.0]); vz = np.array([0.5, 0.0])
+    m = np.array([1.0, 3.0])
+    keys = orc.collide_brute(p, 0.0, x, y, z, np.full(2, 1.1), np.array([0, 1]))
+    assert len(keys) == 1
+    nv = np.stack(orc.resolve(p, 0.0, x, y, z, vx, vy, vz, m, np.array([0, 1]), keys), axis=1)
+    want = np.array([[-0.35, -1.8, 0.5], [-0.55, -0.4, 0.0]])
+    np.testing.assert_allclose(nv, want, rtol=0, atol=4e-16 * 4)
+
+
+def test_collision_through_the_sheared_image_hand_values(orc):
+    """Eq. 2 across the x boundary of a shearing box (Sect. 2.3, reading R6)
+    at t = 0 (shear offset 0): b's image at gx = -1 sits at r = (-1.2, 1.6, 0)
+    from a and moves with the image's extra y velocity -1.5 Omega L_x gx =
+    +1.5, so u = (1, -1, 0), n = (-0.6, 0.8, 0), v_n = -1.4 and
+    Delta = 2.1 for eps = 0.5; equal masses share it: each velocity changes by
+    1.05 n.  The power law of reading V1 with v_c = 0.35 and p = 0.5 gives
+    eps = (1.4 / 0.35)^-0.5 = 0.5, so it must give the same velocities."""
+    L, om = 10.0, 0.1
+    x = np.array([-4.5, 4.3]); y = np.array([0.0, 1.6]); z = np.zeros(2)
+    vx = np.array([0.0, 1.0]); vy = np.array([0.0, -2.5]); vz = np.zeros(2)
+    m = np.ones(2)
+    want = np.array([[0.63, -0.84, 0.0], [0.37, -1.66, 0.0]])
+    for law in (0, 1):
+        p = orc.Params(L=(L,) * 3, omega=om, nghost=(1, 1, 0), boundary=2, eps=0.5, eps_law=law,
+                       eps_vc=0.35, eps_p=0.5)
+        keys = orc.collide_brute(p, 0.0, x, y, z, np.full(2, 1.1), np.array([0, 1]))
+        assert len(keys) == 1
+        a, b, c = orc.decode_pairs(keys)
+        assert (int(a[0]), int(b[0]), int(c[0])) == (0, 1, 6 | (7 << 4) | (7 << 8))
+        nv = np.stack(orc.resolve(p, 0.0, x, y, z, vx, vy, vz, m, np.array([0, 1]), keys), axis=1)
+        np.testing.assert_allclose(nv, want, rtol=0, atol=1e-14)
