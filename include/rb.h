@@ -153,6 +153,11 @@ int rb_get_particles(rb_sim* sim, int box, int64_t cap, int64_t* n_out, double* 
  * SEI), W = (1/2) sum m_i phi_i with phi from an FP64 tree walk at theta over
  * the ghost images (0 when gravity is off); P = sum m v (host array of 3). */
 int rb_energy(rb_sim* sim, int box, double* E, double P[3]);
+/* The terms rb_energy adds up (Sect. 6.2), for checking each on its own:
+ * terms (host array of 6) = K = sum m |v|^2 / 2, U = the SEI tidal and
+ * vertical term (0 for leap-frog), W = (1/2) sum m_i phi_i, P_x, P_y, P_z.
+ * Errors: as rb_energy. */
+int rb_energy_terms(rb_sim* sim, int box, double terms[6]);
 
 /* Test and measurement hooks. */
 
@@ -278,10 +283,11 @@ int rb_mlp_grad(const float* w, const float* X, const float* Y, int64_t n, float
  * vz, and phi (may be NULL: W = 0; x and z may be NULL unless integrator is
  * RB_INT_SEI).  Output: out, a caller-owned device array of 7 doubles, filled
  * with sum m|v|^2/2, the SEI tidal and vertical term
- * sum m (omega_z^2 z^2 / 2 - 3/2 omega^2 x^2) (0 for leap-frog),
- * sum m phi / 2, the three momentum components and n, the same terms
- * rb_energy adds up.  Runs asynchronously on cuda_stream (NULL: the legacy
- * default stream).
+ * sum m (omega_z^2 z^2 / 2 - 3/2 omega^2 x^2) (0 for leap-frog; omega_z <= 0
+ * means omega_z = omega, as in rb_create), sum m phi / 2, the three momentum
+ * components and n, the same terms rb_energy adds up.  Runs asynchronously on
+ * cuda_stream (NULL: the legacy default stream), which must belong to the
+ * current device; the arrays must be on that device too.
  * Scratch: a fixed 448 KiB array of per-block partial sums in the library's
  * own device memory, present on every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device
@@ -289,15 +295,20 @@ int rb_mlp_grad(const float* w, const float* X, const float* Y, int64_t n, float
  * before any stream capture.  Every call overwrites the partial sums it
  * reads; calls that overlap on the GPU share the array and race.
  * Errors: RB_ERR_ARG for n < 0 or n > 16,777,216 (the partial-sum array holds
- * one slot per 2048 particles) or a missing array, with a message in
- * rb_last_error(NULL); RB_ERR_CUDA if the address lookup or a launch fails.
+ * one slot per 2048 particles), a missing array or a stream of another device,
+ * with a message in rb_last_error(NULL); RB_ERR_CUDA if the address lookup or
+ * a launch fails (a launch error left by earlier work on the calling thread is
+ * cleared before the launches).
  * It calls no cudaMalloc, cudaFree or allocating library routine. */
 int rb_energy_sums_noalloc(int64_t n, const double* m, const double* x, const double* z,
                            const double* vx, const double* vy, const double* vz,
                            const double* phi, int integrator, double omega, double omega_z,
                            double* out, void* cuda_stream);
-/* Description of the last error of `sim` (or of the last failed
- * rb_create when sim is NULL); static storage owned by the library. */
+/* Description of the last error of `sim`, or with sim NULL of the last
+ * failed rb_create or rb_energy_sums_noalloc on the calling thread (that
+ * message is kept per host thread, so threads that fail at the same time do
+ * not overwrite each other's).  Storage owned by the library, valid until the
+ * next failing call of the same simulation or thread. */
 const char* rb_last_error(const rb_sim* sim);
 
 #ifdef __cplusplus

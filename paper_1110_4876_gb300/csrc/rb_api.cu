@@ -986,8 +986,8 @@ int rb_get_pairs(rb_sim* s, int box, int64_t cap, int64_t* n, int64_t* id_a, int
     return k > cap ? fail(s, RB_ERR_ARG, "capacity too small") : RB_OK;
 }
 
-int rb_energy(rb_sim* s, int box, double* E, double P[3]) {
-    if (bad_box(s, box) || !E || !P) return fail(s, RB_ERR_ARG, "bad arguments");
+// K, U (SEI tidal + vertical), W, P of box `box` into h[0..6] (h[6] = n).
+static int energy_sums(rb_sim* s, int box, double h[7]) {
     int rc = ensure_ready(s);
     if (rc) return rc;
     const double* phi = nullptr;
@@ -996,11 +996,27 @@ int rb_energy(rb_sim* s, int box, double* E, double P[3]) {
         phi = s->phi;
     }
     energy_terms(s->P[s->cur], s->ctl, s->C, phi, box, s->e_part, kEnergyParts, s->e_out, s->stream);
-    double h[8];
     RB_CUDA(s, cudaMemcpyAsync(h, s->e_out, sizeof(double) * 7, cudaMemcpyDeviceToHost, s->stream));
     RB_CUDA(s, cudaStreamSynchronize(s->stream));
+    return RB_OK;
+}
+
+int rb_energy(rb_sim* s, int box, double* E, double P[3]) {
+    if (bad_box(s, box) || !E || !P) return fail(s, RB_ERR_ARG, "bad arguments");
+    double h[8];
+    int rc = energy_sums(s, box, h);
+    if (rc) return rc;
     *E = h[0] + h[1] + h[2];
     P[0] = h[3]; P[1] = h[4]; P[2] = h[5];
+    return RB_OK;
+}
+
+int rb_energy_terms(rb_sim* s, int box, double terms[6]) {
+    if (bad_box(s, box) || !terms) return fail(s, RB_ERR_ARG, "bad arguments");
+    double h[8];
+    int rc = energy_sums(s, box, h);
+    if (rc) return rc;
+    for (int k = 0; k < 6; k++) terms[k] = h[k];
     return RB_OK;
 }
 

@@ -32,17 +32,18 @@ static __device__ __align__(256) double g_energy_scratch[7 * kMaxBlocks];
 double* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
-// Device address of the scratch array for the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
-cudaError_t scratch_for_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// Device address of the scratch array on device `dev`, which must be the
+// current device (looked up once per device; the host-side symbol itself is
+// not a device address).  The cached address belongs to the context that
+// was current at the lookup: a caller that resets the device
+// (cudaDeviceReset) and keeps using the library in a new context gets a
+// stale address, which this library does not detect.
+cudaError_t scratch_for_device(int dev, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_energy_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = static_cast<double*>(p);
     }
@@ -115,19 +116,50 @@ extern "C" int rb_energy_sums_noalloc(int64_t n, const double* m, const double* 
         rb::set_global_error("rb_energy_sums_noalloc: null array");
         return RB_ERR_ARG;
     }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        rb::set_global_error(std::string("rb_energy_sums_noalloc: cudaGetDevice: ") +
+                             cudaGetErrorString(e));
+        return RB_ERR_CUDA;
+    }
+    if (s) {
+        int sdev = -1;
+        e = cudaStreamGetDevice(s, &sdev);
+        if (e != cudaSuccess) {
+            rb::set_global_error(std::string("rb_energy_sums_noalloc: cudaStreamGetDevice: ") +
+                                 cudaGetErrorString(e));
+            return RB_ERR_CUDA;
+        }
+        if (sdev != dev) {
+            rb::set_global_error("rb_energy_sums_noalloc: cuda_stream belongs to another device "
+                                 "than the current one");
+            return RB_ERR_ARG;
+        }
+    }
     double* scratch = nullptr;
-    const cudaError_t e = scratch_for_current_device(&scratch);
+    e = scratch_for_device(dev, &scratch);
     if (e != cudaSuccess) {
         rb::set_global_error(std::string("rb_energy_sums_noalloc: cudaGetSymbolAddress: ") +
                              cudaGetErrorString(e));
         return RB_ERR_CUDA;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int nblocks = n > 0 ? (int)((n + kTile - 1) / kTile) : 1;
     const double oz = omega_z > 0.0 ? omega_z : omega;
+    // A launch error left over from earlier work on this thread (by this
+    // library or another) is cleared first, so that the check below reports
+    // only these two launches.
+    (void)cudaGetLastError();
     k_energy_noalloc<<<nblocks, kThreads, 0, s>>>((int)n, m, x, z, vx, vy, vz, phi,
                                                   integrator == RB_INT_SEI, omega * omega, oz * oz,
                                                   scratch);
     k_energy_noalloc_final<<<1, 32, 0, s>>>(scratch, nblocks, out);
-    return cudaGetLastError() == cudaSuccess ? RB_OK : RB_ERR_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        rb::set_global_error(std::string("rb_energy_sums_noalloc: kernel launch: ") +
+                             cudaGetErrorString(e));
+        return RB_ERR_CUDA;
+    }
+    return RB_OK;
 }

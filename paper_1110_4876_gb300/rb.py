@@ -24,6 +24,7 @@ RB_EPS_CONSTANT, RB_EPS_POWER = 0, 1
 
 EXPORTS = [
     "rb_create", "rb_set_box", "rb_set_particles", "rb_step", "rb_get_particles", "rb_energy",
+    "rb_energy_terms",
     "rb_compute_gravity", "rb_get_accelerations", "rb_get_counts", "rb_get_tree",
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
@@ -90,6 +91,7 @@ def load():
     lib.rb_step.argtypes = [_P, i64]
     lib.rb_get_particles.argtypes = [_P, i32, i64, C.POINTER(i64)] + [_VP] * 9
     lib.rb_energy.argtypes = [_P, i32, C.POINTER(C.c_double), _D]
+    lib.rb_energy_terms.argtypes = [_P, i32, _D]
     lib.rb_compute_gravity.argtypes = [_P]
     lib.rb_get_accelerations.argtypes = [_P, i32, i64, _VP, _VP, _VP]
     lib.rb_get_counts.argtypes = [_P, i32, i64, _VP, _VP, _VP]
@@ -205,6 +207,13 @@ def rb_energy(sim, box: int = 0):
     P = np.zeros(3)
     _check(load().rb_energy(sim, box, C.byref(E), P), sim)
     return E.value, P
+
+
+def rb_energy_terms(sim, box: int = 0):
+    """(K, U, W, P): the terms rb_energy adds up."""
+    t = np.zeros(6)
+    _check(load().rb_energy_terms(sim, box, t), sim)
+    return t[0], t[1], t[2], t[3:].copy()
 
 
 def rb_compute_gravity(sim):
@@ -438,6 +447,9 @@ class Sim:
 
     def energy(self, box: int = 0):
         return rb_energy(self.h, box)
+
+    def energy_terms(self, box: int = 0):
+        return rb_energy_terms(self.h, box)
 
     def stats(self):
         return rb_stats(self.h)

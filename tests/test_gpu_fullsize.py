@@ -42,16 +42,20 @@ def sheet1m():
 
 def test_sheet_1m_forces_sampled(rb, orc, sheet1m):
     """FP32 walk at N = 1M on 2048 sampled targets against the oracle's FP64
-    tree at the same theta (max_rel <= 1e-5) and counts of the FP64 walk."""
+    tree at the same theta (max_rel <= 1e-5); both walks' per-target counts
+    of accepted cells and particle terms equal the oracle's."""
     P, L = sheet1m, 2050.0
     sel = np.random.default_rng(3).choice(P.n, 2048, replace=False)
     tree = orc.Tree(P.x, P.y, P.z, P.m, L)
     a_ref, (rc, rl, rm) = tree.gravity(params(orc, L), 0.0, targets=sel, counts=True)
     sim = rb.Sim(**cfg(rb, L, walk=1))
     sim.set_particles(P)
-    a32 = sim.gravity()
+    a32, (c32, l32, _) = sim.gravity(counts=True)
     e = orc.force_errors(a32[sel], a_ref)
     assert e[2] <= 1e-5, e
+    # the guarded FP32 opening test accepts exactly the oracle's cells
+    np.testing.assert_array_equal(c32[sel], rc)
+    np.testing.assert_array_equal(l32[sel], rl)
     sim64 = rb.Sim(**cfg(rb, L, walk=0))
     sim64.set_particles(P)
     a64, (nc, nl, nm) = sim64.gravity(counts=True)
@@ -108,11 +112,16 @@ def test_mid_sheet_steps_fp32_vs_fp64(rb, orc):
     assert np.max(np.abs(g32["vz"] - g64["vz"])) <= 1e-3 * np.max(np.abs(g64["vz"]))
 
 
-def test_ensemble_256_boxes_per_box_agreement(rb, orc):
-    """256 boxes of uneven N advanced together: sampled boxes agree with the
-    oracle (forces on the first tree, pairs after one step)."""
+@pytest.mark.parametrize("walk,tol", [(0, 1e-12), (1, 1e-5)])
+def test_ensemble_256_boxes_per_box_agreement(rb, orc, walk, tol):
+    """256 boxes of uneven N advanced together with the FP64 walk and with
+    the FP32 walk that the ensemble benchmark times (block shape from the
+    autotuner): sampled boxes agree with the oracle's tree at the same theta
+    (forces within tol, identical accepted-cell and particle-term counts) and
+    their pair sets after one step equal the oracle's search on the GPU's
+    positions."""
     boxes = I.ensemble_boxes(256)
-    sims = rb.Sim(nbox=256, **cfg(rb, boxes[0][1], walk=0))
+    sims = rb.Sim(nbox=256, **cfg(rb, boxes[0][1], walk=walk))
     parts = []
     for b, (nb, Lb, seed) in enumerate(boxes):
         Pb = I.sheet(Lb, nb, seed + 7919)
@@ -120,14 +129,19 @@ def test_ensemble_256_boxes_per_box_agreement(rb, orc):
         sims.set_box(b, (Lb, Lb, Lb))
         sims.set_particles(Pb, box=b)
     from paper_1110_4876_gb300 import rb as _rb
+    _rb.rb_autotune(sims.h, 0)
     _rb.rb_compute_gravity(sims.h)
     for b in (0, 17, 101, 255):
         Lb, Pb = parts[b]
         a = _rb.rb_get_accelerations(sims.h, b)
-        a_ref = orc.tree_gravity(params(orc, Lb), 0.0, Pb.x, Pb.y, Pb.z, Pb.m)
-        assert orc.force_errors(a, a_ref)[2] <= 1e-12, b
+        nc, nl, _ = _rb.rb_get_counts(sims.h, b)
+        a_ref, (rc, rl, _) = orc.tree_gravity(params(orc, Lb), 0.0, Pb.x, Pb.y, Pb.z, Pb.m,
+                                              counts=True)
+        assert orc.force_errors(a, a_ref)[2] <= tol, b
+        np.testing.assert_array_equal(nc, rc)
+        np.testing.assert_array_equal(nl, rl)
     sims.step(1)
-    for b in (3, 64, 200):
+    for b in (3, 64, 200, 255):
         Lb, Pb = parts[b]
         g = sims.particles(b)
         a, bb, c = _rb.rb_get_pairs(sims.h, b)

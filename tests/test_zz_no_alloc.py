@@ -56,6 +56,39 @@ def test_noalloc_energy_matches_rb_energy(rb):
     np.testing.assert_array_equal(results[0], results[1])
 
 
+def test_noalloc_leapfrog_and_potential_terms(rb):
+    """Leap-frog without x and z (the tidal term is 0) and a device array phi:
+    the kinetic and momentum sums equal rb_energy's on a leap-frog box, and
+    the W slot equals (1/2) sum m phi summed on the host, on two calls."""
+    torch = pytest.importorskip("torch")
+    L, N = 650.0, 70_001
+    P = I.sheet(L, N, 4)
+    sim = rb.Sim(G=1.0, box=(L, L, L), boundary=rb.RB_BC_PERIODIC, integrator=rb.RB_INT_LEAPFROG,
+                 dt=1e-3, gravity=0, collisions=0)
+    sim.set_particles(P)
+    E_ref, P_ref = sim.energy()
+    phi = -np.random.default_rng(5).uniform(0.5, 2.0, N)
+    W_ref = float(np.sum(0.5 * P.m * phi))
+    dev = torch.device("cuda:0")
+    arr = {k: torch.tensor(getattr(P, k), dtype=torch.float64, device=dev)
+           for k in ("m", "vx", "vy", "vz")}
+    dphi = torch.tensor(phi, dtype=torch.float64, device=dev)
+    out = torch.full((7,), float("nan"), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        rb.rb_energy_sums_noalloc(N, arr["m"].data_ptr(), None, None, arr["vx"].data_ptr(),
+                                  arr["vy"].data_ptr(), arr["vz"].data_ptr(), dphi.data_ptr(),
+                                  rb.RB_INT_LEAPFROG, 0.0, 0.0, out.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        r = out.cpu().numpy()
+        assert r[6] == N and r[1] == 0.0
+        assert abs(r[0] - E_ref) <= 1e-12 * abs(E_ref)
+        assert abs(r[2] - W_ref) <= 1e-12 * abs(W_ref)
+        scale = np.sum(P.m * np.abs(P.vy))
+        np.testing.assert_allclose(r[3:6], P_ref, rtol=0, atol=1e-12 * scale)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(rb):
     with pytest.raises(rb.RbError) as ei:
         rb.rb_energy_sums_noalloc(16_777_217, None, None, None, None, None, None, None,
