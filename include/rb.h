@@ -104,8 +104,11 @@ typedef struct rb_stats_t {
      * 9 collision search, 10 pair sort, 11 resolution */
     double  ms_stage[12];
     int64_t corrections;      /* learned walk: band cells corrected by the network in the last walk */
-    int64_t warp_iterations;  /* FP32 walk: entries processed by warps (32 targets each) in the
-                                 last walk; (leaf + mac) / (32 x this) is the lane utilisation */
+    int64_t warp_iterations;  /* FP32 walk: warp iterations of the last walk (union walk: entries
+                                 processed, 32 targets each; group walk: frontier rounds, list
+                                 entries and mixed-subtree iterations) */
+    int64_t walk_group;       /* FP32 walk shape: 0 union walk, 4 group walk (4-lane subgroups
+                                 for the mixed subtrees) */
 } rb_stats_t;
 
 typedef struct rb_sim rb_sim; /* opaque, owned by the library */
@@ -208,16 +211,22 @@ int rb_stats(rb_sim* sim, rb_stats_t* out);
 /* on = 1: record CUDA events between the stages of every step (event nodes
  * inside the step graph) so rb_stats reports per-stage device times. */
 int rb_set_profiling(rb_sim* sim, int on);
-/* Time the gravity walk and the tree collision search at 64, 128 and 256
- * threads per block on the current positions (best of 3 after a warm-up each)
- * and keep the fastest; results are cached per (particle-count bucket, theta,
- * walk mode, batched) for the process, and use_cache = 1 takes a cached
- * choice without timing.  Positions and velocities are not changed. */
+/* Time the gravity walk and the tree collision search on the current
+ * positions at 64, 128 and 256 threads per block and, for the plain FP32
+ * walk, at each warp shape (walk_group 0 and 4; best of 3 after a warm-up
+ * each) and keep the fastest; results are cached per (particle-count bucket,
+ * theta, walk mode, batched) for the process, and use_cache = 1 takes a
+ * cached choice without timing.  Positions and velocities are not changed. */
 int rb_autotune(rb_sim* sim, int use_cache);
 /* Set the launch shapes directly: walk_block and search_block 64, 128 or 256
- * threads per block.  Results do not depend on them (each lane runs its own
- * walk).  Errors: RB_ERR_ARG for any other value. */
-int rb_set_launch_shape(rb_sim* sim, int walk_block, int search_block);
+ * threads per block; walk_group (plain FP32 walk) 0 for the union walk, in
+ * which each warp walks the union of its 32 targets' walks, or 4 for the
+ * group walk, in which cells that all 32 targets of a warp provably accept
+ * or open are decided once (Sect. 4.2 opening test against the bounding box
+ * of the targets; accepted cells go to an interaction list staged in shared
+ * memory) and the remaining subtrees are walked by subgroups of 4 lanes.  Results do not depend on them (each target's accepted cells
+ * are those of its own walk).  Errors: RB_ERR_ARG for any other value. */
+int rb_set_launch_shape(rb_sim* sim, int walk_block, int search_block, int walk_group);
 /* Test particles (Sect. 4: particles that feel gravity without exerting it):
  * in every box, particles with id >= n_active keep their mass for collisions
  * and kinetic energy but are not sources of Eq. 1.  n_active < 0 (the

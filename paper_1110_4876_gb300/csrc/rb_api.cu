@@ -92,6 +92,7 @@ struct rb_sim {
     std::vector<void*> mlp_allocs;
     // launch shapes (threads per block) of the gravity walk and the search
     int walk_block = 128, search_block = 128;
+    int walk_group = 0;   // FP32 walk: 0 union walk; 4 group walk (4-lane subgroups for mixed subtrees)
     bool tuned = false;
 };
 
@@ -439,7 +440,7 @@ int record_step(rb_sim* s, int p) {
                          true, st, nullptr, s->walk_block, &L);
         } else {
             gravity_walk(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk, 1, walk_out(s), false,
-                         true, st, nullptr, s->walk_block);
+                         true, st, nullptr, s->walk_block, nullptr, s->walk_group);
         }
         mark(s, 5);
         drift_keys(s->P[c], s->T, s->ctl, s->d_boxes, s->C, s->ncap, 1, 2, s->acc_x, s->acc_y,
@@ -603,11 +604,15 @@ int gravity_now(rb_sim* s, bool potential) {
                      true, s->stream, nullptr, s->walk_block, &L);
     } else {
         gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64 ? RB_WALK_FP64 : s->cfg.walk, 0,
-                     walk_out(s), potential, true, s->stream, nullptr, s->walk_block);
+                     walk_out(s), potential, true, s->stream, nullptr, s->walk_block, nullptr,
+                     s->walk_group);
     }
     s->acc_set = s->cur;
     RB_CUDA(s, cudaGetLastError());
-    return read_ctl(s);
+    if (int rc = read_ctl(s)) return rc;
+    if (s->hctl.err & kErrWalk)
+        return fail(s, RB_ERR_STATE, "gravity walk: an entry index outside the tree (malformed tree)");
+    return RB_OK;
 }
 
 template <typename T>
@@ -845,6 +850,8 @@ int rb_step(rb_sim* s, int64_t nsteps) {
         if (s->hctl.err & kErrNonFinite)
             return fail(s, RB_ERR_NONFINITE, "a position became non-finite (or left the box by more than "
                                              "4096 box lengths in one drift half)");
+        if (s->hctl.err & kErrWalk)
+            return fail(s, RB_ERR_STATE, "gravity walk: an entry index outside the tree (malformed tree)");
         if (s->hctl.err & kErrSweepLong)
             return fail(s, RB_ERR_CAPACITY, "plane sweep: a trajectory overlaps more than 65536 others in x "
                                             "(use the tree detector)");
@@ -1077,6 +1084,7 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     out->kernels_per_step = s->kernels_per_step;
     out->walk_block = s->walk_block;
     out->search_block = s->search_block;
+    out->walk_group = s->walk_group;
     for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
     out->corrections = s->cfg.walk == RB_WALK_FP32_LEARNED ? c.req_count : 0;
     out->warp_iterations = (int64_t)c.n_iter;
@@ -1099,7 +1107,10 @@ struct TuneKey {
         return batched < o.batched;
     }
 };
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+struct TuneShape {
+    int walk_block, search_block, walk_group;
+};
+std::map<TuneKey, TuneShape> g_tune_cache;
 std::mutex g_tune_mutex;
 
 TuneKey tune_key(const rb_sim* s) {
@@ -1139,30 +1150,37 @@ int rb_autotune(rb_sim* s, int use_cache) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            s->walk_block = it->second.first;
-            s->search_block = it->second.second;
+            s->walk_block = it->second.walk_block;
+            s->search_block = it->second.search_block;
+            s->walk_group = it->second.walk_group;
             s->tuned = true;
             drop_graphs(s);
             return RB_OK;
         }
     }
     const int cand[3] = {64, 128, 256};
-    int wb = s->walk_block, sb = s->search_block;
+    int wb = s->walk_block, sb = s->search_block, wg = s->walk_group;
     if (s->cfg.gravity) {
         rebuild_now(s);
         const bool fp64 = s->cfg.walk == RB_WALK_FP64;
         build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream, true);
         const bool learned = s->cfg.walk == RB_WALK_FP32_LEARNED && s->mlp_loaded;
         const WalkLearn L = learn_args(s);
+        // the plain FP32 walk also chooses its warp shape: the union walk
+        // over 32 targets, or the group walk with 4-lane subgroups
+        const bool grouped = !fp64 && !learned;
+        const int gcand[2] = {0, 4};
         float best = 1e30f;
-        for (int b : cand) {
-            const float ms = time_best(s, [&] {
-                gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C,
-                             fp64 ? RB_WALK_FP64 : RB_WALK_FP32, 0, walk_out(s), false, false, s->stream,
-                             nullptr, b, learned ? &L : nullptr);
-            });
-            if (ms < best) { best = ms; wb = b; }
-        }
+        for (int b : cand)
+            for (int g : gcand) {
+                if (!grouped && g != gcand[0]) continue;
+                const float ms = time_best(s, [&] {
+                    gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C,
+                                 fp64 ? RB_WALK_FP64 : RB_WALK_FP32, 0, walk_out(s), false, false,
+                                 s->stream, nullptr, b, learned ? &L : nullptr, g);
+                });
+                if (ms < best) { best = ms; wb = b; wg = grouped ? g : wg; }
+            }
         s->acc_set = -1;   // the tuning walks left no consistent acceleration record
     }
     if (s->cfg.collisions == RB_COLL_TREE) {
@@ -1191,22 +1209,27 @@ int rb_autotune(rb_sim* s, int use_cache) {
     RB_CUDA(s, cudaGetLastError());
     s->walk_block = wb;
     s->search_block = sb;
+    s->walk_group = wg;
     s->tuned = true;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = {wb, sb};
+        g_tune_cache[key] = {wb, sb, wg};
     }
     drop_graphs(s);
     return RB_OK;
 }
 
-int rb_set_launch_shape(rb_sim* s, int walk_block, int search_block) {
+int rb_set_launch_shape(rb_sim* s, int walk_block, int search_block, int walk_group) {
     if (!s) return fail(s, RB_ERR_ARG, "null sim");
     const bool ok = (walk_block == 64 || walk_block == 128 || walk_block == 256) &&
-                    (search_block == 64 || search_block == 128 || search_block == 256);
-    if (!ok) return fail(s, RB_ERR_ARG, "launch shapes: 64, 128 or 256 threads per block");
+                    (search_block == 64 || search_block == 128 || search_block == 256) &&
+                    (walk_group == 0 || walk_group == 4);
+    if (!ok)
+        return fail(s, RB_ERR_ARG,
+                    "launch shapes: 64, 128 or 256 threads per block; walk group 0 or 4");
     s->walk_block = walk_block;
     s->search_block = search_block;
+    s->walk_group = walk_group;
     s->tuned = true;
     drop_graphs(s);
     return RB_OK;

@@ -82,6 +82,7 @@ constexpr int kErrNonFinite = 1;
 constexpr int kErrPairOverflow = 2;
 constexpr int kErrSweepLong = 4;    // a plane-sweep item met more than kMaxSweepScan extents
 constexpr int kErrResolveStall = 8; // the resolution queue stopped filling (bounded wait gave up)
+constexpr int kErrWalk = 16;        // a walk met an entry index outside the tree (malformed tree)
 constexpr int kMaxSweepScan = 1 << 16;
 
 // One ghost image of one box at the time of a walk or search (Sect. 2.3):
@@ -273,10 +274,13 @@ constexpr int kMaxTileQueues = 512;
 // Queries the residency of every walk and search kernel once (outside any
 // stream capture); returns the number of SMs.
 int walk_prepare();
+// group (plain FP32 walk only): 0 runs the union walk over the warp's 32
+// targets; 4 runs the group walk, whose mixed subtrees are walked by
+// subgroups of 4 lanes.  Accepted sets do not depend on block or group.
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
                   bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128,
-                  const WalkLearn* learn = nullptr);
+                  const WalkLearn* learn = nullptr, int group = 0);
 // aabb: the records of build_collision_aabb, with rmax the largest radius.
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                       const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128,

@@ -34,6 +34,8 @@ struct GravArgs {
     Rec4 ra, rb, rq0, rq1, rc_hi, rc_lo;
     const double4_32a *d_a, *d_q0, *d_q1, *d_c;
     const int32_t *e_skip, *leaf_of, *box_root;
+    const int32_t* e_child;     // per cell entry: child entry of each octant (group walk)
+    const uint32_t* e_cmask;    // per cell entry: octants holding a child (0: depth-21 group)
     const BoxP* boxes;
     Ctl* ctl;
     WalkOut out;
@@ -533,6 +535,479 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32(GravArgs A) {
         walk32<kQuad, kInside, kPot, kSoft, kRecord, false, kOne>(A, nullptr, nullptr, t << 5, n);
 }
 
+// ---------------------------------------------------------------------------
+// Group walk (FP32, plain): exact per-target accepted sets, far field decided
+// once per warp.
+//
+// For each ghost image the warp first walks the tree as a group: the lanes
+// take up to 32 frontier cells at a time and test each against the bounding
+// box of the warp's 32 target points.  A cell that every target point
+// provably accepts (its opening test w < theta R holds for the box's nearest
+// point with a 1e-4 margin, so each lane's own FP32 test would accept it
+// outside the FP64 guard band) goes to the warp's interaction list; a cell
+// that every target provably opens (the test fails for the box's farthest
+// point) has its children pushed to the frontier; a leaf reached this way is
+// an exact term for every target but its own particle.  Any other cell is
+// "mixed": its subtree is walked afterwards target by target with the same
+// per-lane opening test (FP32, re-decided in FP64 near the threshold, inside
+// rule) as the union walk, so each target visits exactly the cells its own
+// Barnes-Hut walk visits (Sect. 4.2) and the accepted sets equal the oracle's.
+//
+// The list is evaluated by all 32 lanes with broadcast record loads; the
+// mixed subtrees are walked by subgroups of kS lanes, each subgroup taking
+// the smallest next entry of its own lanes (a union walk over kS targets, far
+// fewer idle lanes than over 32), the subgroups advancing through the mixed
+// list independently.
+constexpr int kGFront = 192;   // frontier cells per warp
+constexpr int kGList = 64;     // accepted list per warp (evaluated when nearly full)
+constexpr int kGMix = 96;      // mixed subtrees per warp (walked when nearly full)
+
+struct GroupSmem {
+    float4 rec[kGList][4];   // accepted list: the entries' records ra, rb, rq0, rq1
+    int front[kGFront];
+    int2 mix[kGMix];         // (entry, image)
+    float box[10];           // current image: bounding box (x0 x1 y0 y1 z0 z1), extent, reference point
+};
+
+// Per-lane state of the group walk of one tile.
+struct GLane {
+    float sx, sy, sz, cx, cy, cz;         // Kahan sums and their compensation
+    float fx, fy, fz;                     // plain sums of the last <= 16 terms
+    int ncell, nleaf, nmac, nrecheck;
+    int iters;                            // warp iterations (warp-uniform)
+    int fcount;                           // terms since the last flush (warp-uniform)
+};
+
+__device__ __forceinline__ void glane_flush(GLane& L) {
+    kadd(L.sx, L.cx, L.fx);
+    kadd(L.sy, L.cy, L.fy);
+    kadd(L.sz, L.cz, L.fz);
+    L.fx = L.fy = L.fz = 0.f;
+}
+
+__device__ __forceinline__ void glane_count(GLane& L) {
+    if (++L.fcount == 16) {
+        glane_flush(L);
+        L.fcount = 0;
+    }
+}
+
+// Monopole + quadrupole term of an accepted cell (reading R3), the same
+// arithmetic as the union walk's; a particle leaf is the cell with Q = 0.
+template <bool kQuad, bool kSoft>
+__device__ __forceinline__ void cell_term(float dx, float dy, float dz, float r2, const float4& q0,
+                                          const float4& q1, float soft2f, float& fx, float& fy,
+                                          float& fz) {
+    const float inv = rsqrt_nr(r2);
+    const float inv2 = inv * inv;
+    const float invs = kSoft ? rsqrt_nr(r2 + soft2f) : inv;
+    float fc = q0.x * (kSoft ? invs * invs * invs : inv2 * inv);
+    if (kQuad) {
+        const float qx = fmaf(q1.y, dz, fmaf(q1.x, dy, q0.y * dx));
+        const float qy = fmaf(q1.z, dz, fmaf(q0.z, dy, q1.x * dx));
+        const float qz = fmaf(q0.w, dz, fmaf(q1.z, dy, q1.y * dx));
+        const float dqd = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
+        const float inv5 = inv2 * inv2 * inv;
+        fc = fmaf(2.5f, dqd * (inv5 * inv2), fc);
+        fx = fmaf(-inv5, qx, fx);
+        fy = fmaf(-inv5, qy, fy);
+        fz = fmaf(-inv5, qz, fz);
+    }
+    fx = fmaf(fc, dx, fx);
+    fy = fmaf(fc, dy, fy);
+    fz = fmaf(fc, dz, fz);
+}
+
+// Record minus target for the negated target point (nxy: x, y hi; lxy: x, y
+// lo; nz: z hi, lo).
+__device__ __forceinline__ void rec_diff(const float4& ra, const float4& rb, float2 nxy, float2 lxy,
+                                         float2 nz, float& dx, float& dy, float& dz, float& r2) {
+    const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(ra.x, ra.y), nxy),
+                                  __fadd2_rn(make_float2(rb.x, rb.y), lxy));
+    dx = dxy.x;
+    dy = dxy.y;
+    const float2 zz = __fadd2_rn(make_float2(ra.z, ra.w), nz);
+    dz = zz.x + zz.y;
+    r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// The negated target point x - o of image img as hi/lo floats, formed from
+// the particle's FP64 position and the image table's hi/lo offset.
+__device__ __forceinline__ void neg_target(const GravArgs& A, int ii, const ImgTab& T, float2& nxy,
+                                           float2& lxy, float2& nz) {
+    float ph, pl, th, tl, th2, tl2, th3, tl3;
+    split_d(A.x[ii], ph, pl);
+    sub_hilo(ph, pl, T.hi.x, T.lo.x, th, tl);
+    split_d(A.y[ii], ph, pl);
+    sub_hilo(ph, pl, T.hi.y, T.lo.y, th2, tl2);
+    split_d(A.z[ii], ph, pl);
+    sub_hilo(ph, pl, T.hi.z, T.lo.z, th3, tl3);
+    nxy = make_float2(-th, -th2);
+    lxy = make_float2(-tl, -tl2);
+    nz = make_float2(-th3, -tl3);
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// All 32 lanes evaluate the staged records rec[0 .. lc) for their own
+// target point; `self` is this lane's own leaf in the central image (else
+// -1).  A leaf's record holds -m and its entry + 1 in rb.z and rb.w.
+template <bool kQuad, bool kSoft>
+__device__ __forceinline__ void eval_list(const GravArgs& A, const float4 (*rec)[4], int lc, int ii,
+                                          const ImgTab& T, int self, GLane& L) {
+    float2 nxy, lxy, nz;
+    neg_target(A, ii, T, nxy, lxy, nz);
+    for (int j = 0; j < lc; j++) {
+        const float4 ra = rec[j][0];
+        const float4 rb = rec[j][1];
+        float dx, dy, dz, r2;
+        rec_diff(ra, rb, nxy, lxy, nz, dx, dy, dz, r2);
+        const float crit = rb.z;
+        if (__float_as_int(crit) < 0) {
+            // particle leaf reached through cells every target opened
+            if (__float_as_int(rb.w) - 1 != self) {
+                const float m = -crit;
+                const float inv = rsqrt_nr(kSoft ? r2 + A.soft2f : r2);
+                const float f = m * (inv * inv * inv);
+                L.fx = fmaf(f, dx, L.fx);
+                L.fy = fmaf(f, dy, L.fy);
+                L.fz = fmaf(f, dz, L.fz);
+                L.nleaf++;
+            }
+        } else {
+            cell_term<kQuad, kSoft>(dx, dy, dz, r2, rec[j][2], rec[j][3], A.soft2f, L.fx, L.fy, L.fz);
+        }
+        glane_count(L);
+    }
+    L.iters += lc;
+}
+
+// The per-target walks of the mixed subtrees mix[0 .. mc), by subgroups of
+// kS lanes.  Each subgroup walks every subtree for its own lanes: the union
+// of its lanes' stackless walks from the subtree's root to its skip entry,
+// with the union walk's per-lane opening test.
+template <bool kQuad, bool kInside, bool kSoft, int kS>
+__device__ __forceinline__ void mixed_walks(const GravArgs& A, const int2* mix, int mc, const ImgTab* itab,
+                                            int ii, int self_leaf, int gcentre, GLane& L) {
+    int mi = -1, endc = 0, next = kEnd, img = -1, self = -1;
+    float2 nxy = make_float2(0.f, 0.f), lxy = nxy, nz = nxy;
+    for (;;) {
+        int e = next;
+#pragma unroll
+        for (int o = 1; o < kS; o <<= 1) e = min(e, __shfl_xor_sync(kFull, e, o));
+        if (e >= endc) {
+            // this subgroup is done with its subtree: take the next one
+            ++mi;
+            if (mi < mc) {
+                const int2 m = mix[mi];
+                e = m.x;
+                next = m.x;
+                endc = __ldg(&A.e_skip[m.x]);
+                if (m.y != img) {
+                    img = m.y;
+                    neg_target(A, ii, itab[img], nxy, lxy, nz);
+                    self = img == gcentre ? self_leaf : -1;
+                }
+            } else {
+                e = kEnd;
+                endc = kEnd;
+                next = kEnd;
+                mi = mc;
+            }
+        }
+        if (__all_sync(kFull, e == kEnd)) break;
+        if (e != kEnd && e >= A.ecap) {
+            // cannot happen for a well-formed tree: record it and stop
+            atomicOr(&A.ctl->err, kErrWalk);
+            e = kEnd;
+            endc = kEnd;
+            next = kEnd;
+            mi = mc;
+        }
+        if (e != kEnd) {
+            const float4 ra = __ldg(&A.ra[e]);
+            const float4 rb = __ldg(&A.rb[e]);
+            float dx, dy, dz, r2;
+            rec_diff(ra, rb, nxy, lxy, nz, dx, dy, dz, r2);
+            const float crit = rb.z;
+            const bool leaf = __float_as_int(crit) < 0;
+            bool acc = false;
+            if (next == e) {
+                if (leaf) {
+                    acc = e != self;
+                    if (acc) L.nleaf++;
+                    next = e + 1;
+                } else {
+                    L.nmac++;
+                    acc = crit < r2;
+                    if (fabsf(crit - r2) <= 1e-5f * r2) {
+                        // the FP64 target point x - o, as the oracle forms it
+                        acc = mac64(ld_d4(&A.d_a[e]), A.theta2, __dsub_rn(A.x[ii], itab[img].ox),
+                                    __dsub_rn(A.y[ii], itab[img].oy), __dsub_rn(A.z[ii], itab[img].oz));
+                        L.nrecheck++;
+                    }
+                    if (kInside && acc) {
+                        const float4 ch = __ldg(&A.rc_hi[e]);
+                        const float4 cl = __ldg(&A.rc_lo[e]);
+                        const float ux = (-nxy.x - ch.x) + (-lxy.x - cl.x);
+                        const float uy = (-nxy.y - ch.y) + (-lxy.y - cl.y);
+                        const float uz = (-nz.x - ch.z) + (-nz.y - cl.z);
+                        const float w = ch.w, tol = 1e-5f * ch.w;
+                        const float mx = fminf(fminf(ux, w - ux), fminf(fminf(uy, w - uy), fminf(uz, w - uz)));
+                        if (fabsf(mx) <= tol) {
+                            acc = !inside64(ld_d4(&A.d_c[e]), __dsub_rn(A.x[ii], itab[img].ox),
+                                            __dsub_rn(A.y[ii], itab[img].oy),
+                                            __dsub_rn(A.z[ii], itab[img].oz));
+                            L.nrecheck++;
+                        } else if (mx > 0.f) {
+                            acc = false;
+                        }
+                    }
+                    if (acc) {
+                        L.ncell++;
+                        next = __float_as_int(rb.w);
+                    } else {
+                        next = e + 1;
+                    }
+                }
+            }
+            if (acc) {
+                float4 q0, q1;
+                if (leaf) {
+                    q0 = make_float4(-crit, 0.f, 0.f, 0.f);
+                    q1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    q0 = __ldg(&A.rq0[e]);
+                    q1 = __ldg(&A.rq1[e]);
+                }
+                cell_term<kQuad, kSoft>(dx, dy, dz, r2, q0, q1, A.soft2f, L.fx, L.fy, L.fz);
+            }
+        }
+        L.iters++;
+        glane_count(L);
+    }
+}
+
+// One tile of 32 consecutive targets, all in one box.  Images are taken in
+// turn; each image's group walk fills the list (evaluated when nearly full
+// and when the image is done) and the mixed list (walked when nearly full
+// and after the last image).
+template <bool kQuad, bool kInside, bool kSoft, int kS>
+__device__ __forceinline__ void walk32g(const GravArgs& A, GroupSmem& G, int wbase, int n) {
+    const int lane = threadIdx.x & 31;
+    const int i = wbase + lane;
+    const bool valid = i < n;
+    const int ii = valid ? i : n - 1;
+    const int box = A.box[ii];
+    const int root = A.box_root[box];
+    const int self_leaf = A.leaf_of[ii];
+    GLane L;
+    L.sx = L.sy = L.sz = L.cx = L.cy = L.cz = 0.f;
+    L.fx = L.fy = L.fz = 0.f;
+    L.ncell = L.nleaf = L.nmac = L.nrecheck = 0;
+    L.iters = 0;
+    L.fcount = 0;
+    const ImgTab* itab = A.img + (size_t)box * A.nimg;
+    const int gcentre = (A.ngx * (2 * A.ngy + 1) + A.ngy) * (2 * A.ngz + 1) + A.ngz;
+    int gi = -1;               // current image
+    int fc = 0, lc = 0, mc = 0;
+    const bool any = root >= 0;
+    for (;;) {
+        const bool last = fc == 0 && gi + 1 >= A.nimg;
+        if (lc > kGList - 32 || (fc == 0 && lc > 0)) {
+            eval_list<kQuad, kSoft>(A, G.rec, lc, ii, itab[gi], gi == gcentre ? self_leaf : -1, L);
+            lc = 0;
+        }
+        if (mc > kGMix - 32 || (last && mc > 0)) {
+            mixed_walks<kQuad, kInside, kSoft, kS>(A, G.mix, mc, itab, ii, self_leaf, gcentre, L);
+            mc = 0;
+        }
+        if (last || !any) break;
+        if (fc == 0) {
+            // next image: its target points and their bounding box, relative
+            // to lane 0's target (hi parts): u = (t_hi - r) + t_lo
+            gi++;
+            float2 nxy, lxy, nz;
+            neg_target(A, ii, itab[gi], nxy, lxy, nz);
+            const float rx = __shfl_sync(kFull, -nxy.x, 0);
+            const float ry = __shfl_sync(kFull, -nxy.y, 0);
+            const float rz = __shfl_sync(kFull, -nz.x, 0);
+            const float ux = (-nxy.x - rx) - lxy.x, uy = (-nxy.y - ry) - lxy.y, uz = (-nz.x - rz) - nz.y;
+            const float bx0 = warp_min(ux), bx1 = warp_max(ux);
+            const float by0 = warp_min(uy), by1 = warp_max(uy);
+            const float bz0 = warp_min(uz), bz1 = warp_max(uz);
+            __syncwarp();
+            if (lane == 0) {
+                G.front[0] = root;
+                G.box[0] = bx0; G.box[1] = bx1; G.box[2] = by0; G.box[3] = by1;
+                G.box[4] = bz0; G.box[5] = bz1;
+                G.box[6] = fmaxf(fmaxf(fmaxf(-bx0, bx1), fmaxf(-by0, by1)), fmaxf(-bz0, bz1));
+                G.box[7] = rx; G.box[8] = ry; G.box[9] = rz;
+            }
+            fc = 1;
+        }
+        __syncwarp();
+        const int k = min(32, fc);
+        int item = lane < k ? G.front[fc - k + lane] : -1;
+        if (item >= A.ecap) {
+            // cannot happen for a well-formed tree: record it and drop the cell
+            atomicOr(&A.ctl->err, kErrWalk);
+            item = -1;
+        }
+        fc -= k;
+        __syncwarp();   // the popped slots are written over below
+        // 0 none, 1 accepted cell, 2 open, 3 mixed, 4 leaf
+        int cls = 0;
+        uint32_t cm = 0;
+        float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+        if (item >= 0) {
+            ra = __ldg(&A.ra[item]);
+            rb = __ldg(&A.rb[item]);
+            const float crit = rb.z;
+            if (__float_as_int(crit) < 0) {
+                cls = 4;
+            } else {
+                const float bx0 = G.box[0], bx1 = G.box[1], by0 = G.box[2], by1 = G.box[3];
+                const float bz0 = G.box[4], bz1 = G.box[5], ext = G.box[6];
+                const float rx = G.box[7], ry = G.box[8], rz = G.box[9];
+                // centre of mass relative to the reference point
+                const float Dx = (ra.x - rx) + rb.x, Dy = (ra.y - ry) + rb.y, Dz = (ra.z - rz) + ra.w;
+                // rounding of D and of the box corners stays below 2^-21
+                // (|D| + extent); distances are widened / shortened by it
+                const float err = 4.76837158e-7f * (fabsf(Dx) + fabsf(Dy) + fabsf(Dz) + ext);
+                const float ax = fmaxf(fmaxf(fmaxf(bx0 - Dx, Dx - bx1), 0.f) - err, 0.f);
+                const float ay = fmaxf(fmaxf(fmaxf(by0 - Dy, Dy - by1), 0.f) - err, 0.f);
+                const float az = fmaxf(fmaxf(fmaxf(bz0 - Dz, Dz - bz1), 0.f) - err, 0.f);
+                const float hx = fmaxf(Dx - bx0, bx1 - Dx) + err;
+                const float hy = fmaxf(Dy - by0, by1 - Dy) + err;
+                const float hz = fmaxf(Dz - bz0, bz1 - Dz) + err;
+                const float rmin2 = fmaf(az, az, fmaf(ay, ay, ax * ax));
+                const float rmax2 = fmaf(hz, hz, fmaf(hy, hy, hx * hx));
+                if (crit < rmin2 * (1.f - 1e-4f)) {
+                    cls = 1;
+                    if (kInside) {
+                        // the box must also be clear of the cell's cube
+                        const float4 ch = __ldg(&A.rc_hi[item]);
+                        const float4 cl = __ldg(&A.rc_lo[item]);
+                        const float w = ch.w, tol = 1e-5f * w + err;
+                        const float cx0 = (ch.x - rx) + cl.x, cy0 = (ch.y - ry) + cl.y,
+                                    cz0 = (ch.z - rz) + cl.z;
+                        const bool apart = bx1 < cx0 - tol || bx0 > cx0 + w + tol ||
+                                           by1 < cy0 - tol || by0 > cy0 + w + tol ||
+                                           bz1 < cz0 - tol || bz0 > cz0 + w + tol;
+                        if (!apart) cls = 3;
+                    }
+                } else if (crit > rmax2 * (1.f + 1e-4f)) {
+                    cm = __ldg(&A.e_cmask[item]);
+                    cls = cm ? 2 : 3;   // a depth-21 group has no child table
+                } else {
+                    cls = 3;
+                }
+            }
+        }
+        // children of opened cells onto the frontier (a cell whose children
+        // do not fit is walked as a mixed subtree instead)
+        const int nch = cls == 2 ? __popc(cm) : 0;
+        int pre = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, pre, o);
+            if (lane >= o) pre += t;
+        }
+        if (cls == 2 && fc + pre > kGFront) cls = 3;
+        const unsigned mopen = __ballot_sync(kFull, cls == 2);
+        if (cls == 2) {
+            int pos = fc + pre - nch;
+            const int* ch = A.e_child + 8 * (size_t)item;
+            for (uint32_t b = cm; b; b &= b - 1) G.front[pos++] = __ldg(&ch[__ffs(b) - 1]);
+        }
+        // the pushes are contiguous up to the first cell that did not fit
+        const int lastopen = mopen ? 31 - __clz(mopen) : 0;
+        const int pushed = mopen ? __shfl_sync(kFull, pre, lastopen) : 0;
+        const unsigned macc = __ballot_sync(kFull, cls == 1);
+        const unsigned mlist = macc | __ballot_sync(kFull, cls == 4);
+        const unsigned mmix = __ballot_sync(kFull, cls == 3);
+        const unsigned below = (1u << lane) - 1u;
+        if (cls == 1 || cls == 4) {
+            // stage the record: the list is evaluated from shared memory
+            float4* r = G.rec[lc + __popc(mlist & below)];
+            r[0] = ra;
+            r[1] = rb;
+            if (cls == 1) {
+                r[2] = __ldg(&A.rq0[item]);
+                r[3] = __ldg(&A.rq1[item]);
+            }
+        }
+        if (cls == 3) G.mix[mc + __popc(mmix & below)] = make_int2(item, gi);
+        // opening tests decided for the whole group count for every target:
+        // accepted and opened cells (leaves count when evaluated)
+        L.ncell += __popc(macc);
+        L.nmac += __popc(macc) + __popc(mopen);
+        fc += pushed;
+        lc += __popc(mlist);
+        mc += __popc(mmix);
+        L.iters++;
+        __syncwarp();
+    }
+    glane_flush(L);
+    if (valid) {
+        A.out.ax[i] = A.G * ((double)L.sx - (double)L.cx);
+        A.out.ay[i] = A.G * ((double)L.sy - (double)L.cy);
+        A.out.az[i] = A.G * ((double)L.sz - (double)L.cz);
+        if (A.out.ncell) {
+            A.out.ncell[i] = L.ncell;
+            A.out.nleaf[i] = L.nleaf;
+            A.out.nmac[i] = L.nmac;
+        }
+    }
+    unsigned long long c0 = valid ? L.ncell : 0, c1 = valid ? L.nleaf : 0, c2 = valid ? L.nmac : 0,
+                       c3 = valid ? L.nrecheck : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_down_sync(kFull, c0, o);
+        c1 += __shfl_down_sync(kFull, c1, o);
+        c2 += __shfl_down_sync(kFull, c2, o);
+        c3 += __shfl_down_sync(kFull, c3, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.ctl->n_cell, c0);
+        atomicAdd(&A.ctl->n_leaf, c1);
+        atomicAdd(&A.ctl->n_mac, c2);
+        atomicAdd(&A.ctl->n_recheck, c3);
+        atomicAdd(&A.ctl->n_iter, (unsigned long long)L.iters);
+    }
+}
+
+// Plain FP32 walk with group decisions.  kOne: a single box; otherwise a
+// tile whose targets lie in more than one box takes the union walk.
+template <bool kQuad, bool kInside, bool kSoft, bool kOne, int kS>
+__global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32g(GravArgs A) {
+    __shared__ GroupSmem gs[kMaxWalkBlock / 32];
+    GroupSmem& G = gs[threadIdx.x >> 5];
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
+    for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile)) {
+        if (!kOne) {
+            const int i = (t << 5) + (threadIdx.x & 31);
+            const int b = A.box[i < n ? i : n - 1];
+            if (!__all_sync(kFull, b == __shfl_sync(kFull, b, 0))) {
+                walk32<kQuad, kInside, false, kSoft, false, false, false>(A, nullptr, nullptr, t << 5, n);
+                continue;
+            }
+        }
+        walk32g<kQuad, kInside, kSoft, kS>(A, G, t << 5, n);
+    }
+}
+
 // Learned walk: the network's weights and one queue per warp in shared
 // memory; up to 128 registers per thread for the MMA fragments.
 template <bool kInside, bool kSoft>
@@ -939,6 +1414,13 @@ int walk_prepare() {
     prepare_one(k_walk64<true, false, true>); prepare_one(k_walk64<true, false, false>);
     prepare_one(k_walk64<false, true, true>); prepare_one(k_walk64<false, true, false>);
     prepare_one(k_walk64<false, false, true>); prepare_one(k_walk64<false, false, false>);
+#define RB_PREP_G(Q, I, S) \
+    prepare_one(k_walk32g<Q, I, S, true, 4>); prepare_one(k_walk32g<Q, I, S, false, 4>)
+    RB_PREP_G(true, true, true); RB_PREP_G(true, true, false);
+    RB_PREP_G(true, false, true); RB_PREP_G(true, false, false);
+    RB_PREP_G(false, true, true); RB_PREP_G(false, true, false);
+    RB_PREP_G(false, false, true); RB_PREP_G(false, false, false);
+#undef RB_PREP_G
     prepare_one(k_collide<true>);
     prepare_one(k_collide<false>);
     return g_nsm;
@@ -947,8 +1429,9 @@ int walk_prepare() {
 void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                   int walk_mode, int half_step_offset, const WalkOut& out, bool potential,
                   bool counts, cudaStream_t s, const WalkRecord* rec, int block,
-                  const WalkLearn* learn) {
+                  const WalkLearn* learn, int group) {
     block = (block == 64 || block == 256) ? block : 128;
+    group = group == 4 ? 4 : 0;
     if (T.cap_n <= 0) return;
     GravArgs A;
     A.ecap = T.cap_e;
@@ -967,6 +1450,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     A.d_q1 = reinterpret_cast<const double4_32a*>(T.d_q1);
     A.d_c = reinterpret_cast<const double4_32a*>(T.d_c);
     A.e_skip = T.e_skip; A.leaf_of = T.leaf_of; A.box_root = T.box_root;
+    A.e_child = T.e_child; A.e_cmask = T.e_cmask;
     A.boxes = boxes; A.ctl = ctl;
     A.out = out;
     if (!counts) { A.out.ncell = nullptr; A.out.nleaf = nullptr; A.out.nmac = nullptr; }
@@ -984,10 +1468,17 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s, T.tq, T.nq);
     // every kernel below runs the persistent grid that fits on the GPU
 #define RB_LAUNCH(...) __VA_ARGS__<<<persistent_grid(__VA_ARGS__, block, T.cap_n), block, 0, s>>>(A)
-#define RB_W32(Q, I, PO, S)                                          \
-    do {                                                             \
-        if (C.nbox == 1) RB_LAUNCH(k_walk32<Q, I, PO, S, false, true>); \
-        else RB_LAUNCH(k_walk32<Q, I, PO, S>);                        \
+#define RB_W32G(Q, I, S, ONE) RB_LAUNCH(k_walk32g<Q, I, S, ONE, 4>)
+#define RB_W32(Q, I, PO, S)                                                \
+    do {                                                                   \
+        if (group == 0) {                                                  \
+            if (C.nbox == 1) RB_LAUNCH(k_walk32<Q, I, PO, S, false, true>); \
+            else RB_LAUNCH(k_walk32<Q, I, PO, S>);                          \
+        } else if (C.nbox == 1) {                                          \
+            RB_W32G(Q, I, S, true);                                        \
+        } else {                                                           \
+            RB_W32G(Q, I, S, false);                                       \
+        }                                                                  \
     } while (0)
 #define RB_W64(Q, I, PO) RB_LAUNCH(k_walk64<Q, I, PO>)
     if (learn && !potential) {
@@ -1027,6 +1518,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
         }
     }
 #undef RB_W32
+#undef RB_W32G
 #undef RB_W64
 }
 

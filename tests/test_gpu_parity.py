@@ -85,11 +85,15 @@ def test_fp64_walk_matches_oracle_tree(rb, orc, theta):
     np.testing.assert_array_equal(nl, rl)
 
 
+@pytest.mark.parametrize("group", [0, 4])
 @pytest.mark.parametrize("theta,quad", [(0.5, 1), (0.5, 0), (0.3, 1)])
-def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad):
+def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad, group):
+    """Both warp shapes of the FP32 walk: the union walk and the group walk
+    (group decisions, staged interaction list, 4-lane mixed subtrees)."""
     L, N = 160.0, 6000
     P = I.sheet(L, N, 7)
     sim = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP32, theta=theta, quadrupole=quad))
+    rb.rb_set_launch_shape(sim.h, 128, 128, group)
     sim.set_particles(P)
     a, (nc, nl, nm) = sim.gravity(counts=True)
     p = sheet_params(orc, L, theta, quadrupole=quad)
@@ -105,23 +109,24 @@ def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad):
     assert sim.stats()["fp64_rechecks"] > 0
 
 
-@pytest.mark.parametrize("walk", [0, 1])
-def test_plummer_open_inside_rule(rb, orc, walk):
-    """theta = 0.7 > 1/sqrt(3): the target-inside-cell rule is active."""
+@pytest.mark.parametrize("walk,group", [(0, 0), (1, 0), (1, 4)])
+def test_plummer_open_inside_rule(rb, orc, walk, group):
+    """theta = 0.7 > 1/sqrt(3): the target-inside-cell rule is active (the
+    group walk must also keep its group decisions clear of the cell cube)."""
     N = 5000
     P = I.plummer(N, 3)
     cfg = dict(G=1.0, box=(128.0,) * 3, boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG,
                theta=0.7, softening=1e-3, dt=1e-3, gravity=1, collisions=0, walk=walk)
     sim = rb.Sim(**cfg)
+    rb.rb_set_launch_shape(sim.h, 128, 128, group)
     sim.set_particles(P)
     a, (nc, nl, nm) = sim.gravity(counts=True)
     p = orc.Params(G=1.0, L=(128.0,) * 3, theta=0.7, soft=1e-3, dt=1e-3, gravity=1)
     a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, P.x, P.y, P.z, P.m, counts=True)
     e = orc.force_errors(a, a_ref)
     assert e[2] <= (FP64_TOL if walk == 0 else FP32_TOL), e
-    if walk == 0:
-        np.testing.assert_array_equal(nc, rc)
-        np.testing.assert_array_equal(nl, rl)
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
 
 
 @pytest.mark.parametrize("boundary,seed", [(0, 1), (1, 2), (2, 3)])

@@ -1,5 +1,10 @@
-"""The autotuner picks walk/search launch shapes by timing them, and the
-shape does not change any result: every lane runs its own walk."""
+"""The autotuner picks the walk/search launch shapes by timing them.  The
+block sizes do not change any result; the FP32 walk's warp shape (union walk
+or group walk with 4-lane subgroups) changes only the order in which
+each target's FP32 terms are summed: its accepted cells and particle terms
+are the same (counts equal), and forces agree to FP32 rounding: each shape is
+within 1e-5 of the FP64 tree (the parity tests), so two shapes are within
+2e-5 of each other (per-particle denominator floored at 1e-3 of the rms)."""
 import numpy as np
 import pytest
 
@@ -8,7 +13,13 @@ from paper_1110_4876_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def test_autotune_keeps_results_bit_identical():
+def _rel(a, b):
+    n = np.linalg.norm(b, axis=1)
+    den = np.maximum(n, 1e-3 * np.sqrt(np.mean(n ** 2)))
+    return float(np.max(np.linalg.norm(a - b, axis=1) / den))
+
+
+def test_autotune_keeps_results():
     from paper_1110_4876_gb300 import build, rb
 
     build.build()
@@ -18,16 +29,19 @@ def test_autotune_keeps_results_bit_identical():
                integrator=rb.RB_INT_SEI, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
     a = rb.Sim(**cfg)
     a.set_particles(P)
-    acc0 = a.gravity()
+    acc0, cnt0 = a.gravity(counts=True)
     pairs0 = a.pairs()
-    wb, sb = rb.rb_autotune(a.h, use_cache=False)
-    assert wb in (64, 128, 256) and sb in (64, 128, 256)
-    assert np.array_equal(a.gravity(), acc0)
+    wb, sb, wg = rb.rb_autotune(a.h, use_cache=False)
+    assert wb in (64, 128, 256) and sb in (64, 128, 256) and wg in (0, 4)
+    acc1, cnt1 = a.gravity(counts=True)
+    assert _rel(acc1, acc0) <= 2e-5
+    for c0, c1 in zip(cnt0[:2], cnt1[:2]):
+        np.testing.assert_array_equal(c0, c1)
     assert all(np.array_equal(x, y) for x, y in zip(a.pairs(), pairs0))
     # a second simulation of the same kind takes the cached choice
     b = rb.Sim(**cfg)
     b.set_particles(P)
-    assert rb.rb_autotune(b.h, use_cache=True) == (wb, sb)
+    assert rb.rb_autotune(b.h, use_cache=True) == (wb, sb, wg)
     a.step(2)
     b.step(2)
     pa, pb = a.particles(), b.particles()
@@ -35,26 +49,37 @@ def test_autotune_keeps_results_bit_identical():
         assert np.array_equal(pa[k], pb[k])
 
 
-def test_every_launch_shape_gives_the_same_forces_and_pairs():
-    """Every block size of the walk and of the search."""
+@pytest.mark.parametrize("theta", [0.5, 0.7])
+def test_every_launch_shape_gives_the_same_forces_and_pairs(theta):
+    """Every block size of the walk and of the search, every warp shape of
+    the FP32 walk (theta = 0.7 also exercises the inside rule)."""
     from paper_1110_4876_gb300 import build, rb
 
     build.build()
     L, N = 160.0, 6000
     P = I.sheet(L, N, 7)
     cfg = dict(G=I.G_SI, omega=I.OMEGA, box=(L, L, L), nghost=(1, 1, 0), boundary=rb.RB_BC_SHEAR,
-               integrator=rb.RB_INT_SEI, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+               integrator=rb.RB_INT_SEI, theta=theta, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
     sim = rb.Sim(**cfg)
     sim.set_particles(P)
-    ref_a, ref_p = None, None
-    for wb in (64, 128, 256):
-        for sb in (64, 128, 256):
-            rb.rb_set_launch_shape(sim.h, wb, sb)
-            acc = sim.gravity()
-            pairs = rb.pair_keys(*sim.pairs())
-            if ref_a is None:
-                ref_a, ref_p = acc, pairs
-            assert np.array_equal(acc, ref_a), (wb, sb)
-            assert np.array_equal(pairs, ref_p), (wb, sb)
+    ref_a, ref_c, ref_p = None, None, None
+    for wg in (0, 4):
+        shape_a = None
+        for wb in (64, 128, 256):
+            for sb in (64, 128, 256):
+                rb.rb_set_launch_shape(sim.h, wb, sb, wg)
+                acc, cnt = sim.gravity(counts=True)
+                pairs = rb.pair_keys(*sim.pairs())
+                if ref_a is None:
+                    ref_a, ref_c, ref_p = acc, cnt, pairs
+                if shape_a is None:
+                    shape_a = acc
+                assert np.array_equal(acc, shape_a), (wg, wb, sb)
+                assert _rel(acc, ref_a) <= 2e-5, (wg, wb, sb)
+                for c, r in zip(cnt, ref_c):
+                    np.testing.assert_array_equal(c, r)
+                assert np.array_equal(pairs, ref_p), (wg, wb, sb)
     with pytest.raises(rb.RbError):
-        rb.rb_set_launch_shape(sim.h, 96, 128)
+        rb.rb_set_launch_shape(sim.h, 96, 128, 8)
+    with pytest.raises(rb.RbError):
+        rb.rb_set_launch_shape(sim.h, 128, 128, 8)
