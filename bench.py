@@ -37,8 +37,14 @@ UNIT = "particle-steps/s"
 N_SHEET = 1_000_000
 L_SHEET = 2050.0
 SEED = 5
-SMS = 152
 FP32_LANES_PER_SM = 128
+# algorithmic bytes per particle of one tree build (sort + gather, topology,
+# moments): each 8-bit radix pass reads and writes an 8-byte key and a 4-byte
+# value; the gather reads and writes the 64-byte FP64 state plus id and box
+# (8 B) and writes the slot of each id (4 B); the topology reads each key
+# once; each tree cell writes ~160 B of FP64 and FP32 records
+BUILD_PASSES = 8
+BYTES_PASS, BYTES_GATHER, BYTES_KEYS, BYTES_CELL = 24, 148, 8, 160
 # algorithmic FP32 flops per interaction (FMA = 2, add/mul = 1, rsqrt = 0)
 FLOP_CELL, FLOP_LEAF, FLOP_MAC = 60, 20, 10
 FLOP_MLP = 2 * (12 * 64 + 2 * 64 * 64 + 64 * 3)
@@ -217,7 +223,7 @@ def run_ours(args):
     # ---- device-resident throughput (inputs already in HBM) ----
     walk_ms, walk_flops, stage_sum = [], [], {}
     launches = 0
-    pairs, corr, counts = [], [], []
+    pairs, corr, counts, cells = [], [], [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -236,6 +242,7 @@ def run_ours(args):
         corr.append(st["corrections"])
         counts.append((st["cell_interactions"], st["leaf_interactions"], st["mac_tests"],
                        st["warp_iterations"]))
+        cells.append(st["cells"])
     e1.record(stream)
     barrier()
     clk.window(tw0, time.time())
@@ -280,18 +287,20 @@ def run_ours(args):
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     wms = statistics.mean(walk_ms)
     if not wms > 0.0:
         raise RuntimeError("the gravity walk stage time was not recorded")
     achieved = statistics.mean(walk_flops) / (wms / 1e3) / 1e12
     kname = ("k_walk32_learn (gravity walk with the in-walk MLP; FP32 flops only)"
              if args.walk == "learned" else "k_walk32 (gravity walk)")
+    traffic, traffic_note = profiled_traffic("gravity_walk_sheet1m.md", WALK_SOURCES)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": walk_traffic(), "peak_source":
-                    f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
-                    "(MEASURED_PEAKS.json sm_max_mhz)",
+                "traffic": traffic, "traffic_source": traffic_note, "peak_source":
+                    f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
+                    "(MEASURED_PEAKS.json sm_max_mhz; the device's SM count)",
                 "flops_per_launch": statistics.mean(walk_flops), "ms_per_launch": wms}
     ncell, nleaf, nmac, niter = (statistics.mean(c[k] for c in counts) for k in range(4))
     roofline["per_particle"] = {"cells": ncell / N_SHEET, "leaves": nleaf / N_SHEET,
@@ -322,6 +331,7 @@ def run_ours(args):
                    "pairs_per_step": statistics.mean(pairs),
                    "walk_block, search_block, walk_group": list(tuned)},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+        "roofline_build": build_roofline(stage_sum, args.steps, cells, peaks),
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
     }
     if args.cpu_baseline and world == 1:
@@ -332,17 +342,61 @@ def run_ours(args):
     return line
 
 
-def walk_traffic():
-    """DRAM bytes per gravity-walk launch from the committed ncu summary."""
-    path = os.path.join(ROOT, "profiles", "gravity_walk_sheet1m.md")
+WALK_SOURCES = ("paper_1110_4876_gb300/csrc/rb_walk.cu", "paper_1110_4876_gb300/csrc/rb_internal.cuh")
+BUILD_SOURCES = ("paper_1110_4876_gb300/csrc/rb_sort.cu", "paper_1110_4876_gb300/csrc/rb_step.cu",
+                 "paper_1110_4876_gb300/csrc/rb_tree.cu", "paper_1110_4876_gb300/csrc/rb_internal.cuh")
+
+
+def source_hash(paths) -> str:
+    """sha256 over the kernel sources (the build that a capture measured)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary: str, sources, field: str = "dram_bytes_per_launch"):
+    """DRAM bytes (per launch, or per build) from a committed ncu summary, if
+    it was taken on the current kernel sources (its `source_sha256:` line
+    equals the hash of `sources`); else None.  Returns (bytes or None, note)."""
+    path = os.path.join(ROOT, "profiles", summary)
+    fields = {}
     try:
         with open(path) as f:
             for line in f:
-                if line.startswith("dram_bytes_per_launch:"):
-                    return float(line.split(":")[1])
+                if ":" in line and line.split(":", 1)[0] in (field, "source_sha256"):
+                    k, v = line.split(":", 1)
+                    fields[k] = v.strip()
     except OSError:
-        pass
-    return None
+        return None, f"no capture summary profiles/{summary}"
+    now = source_hash(sources)
+    if fields.get("source_sha256") != now or field not in fields:
+        return None, f"profiles/{summary} was taken on other kernel sources (now {now}): null"
+    return float(fields[field]), f"ncu capture in profiles/{summary} (sources {now})"
+
+
+def build_roofline(stage_sum, steps, cells, peaks):
+    """HBM roofline of the tree build (sort + gather, topology, moments) from
+    the event-timed stages: algorithmic bytes per step / stage time."""
+    n = N_SHEET
+    ncells = statistics.mean(cells) if cells else 0.0
+    per_particle = BUILD_PASSES * BYTES_PASS + BYTES_GATHER + BYTES_KEYS
+    nbytes = n * per_particle + ncells * BYTES_CELL
+    ms = sum(stage_sum.get(k, 0.0) for k in ("sort_gather", "tree", "moments")) / steps
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
+    traffic, note = profiled_traffic("tree_build_sheet1m.md", BUILD_SOURCES, "dram_bytes_per_build")
+    return {"bound": "hbm", "kernels": "k_rs_up/k_digit_rows/k_rs_down (8 passes), k_permute, topology, "
+                                       "k_moments_level (per depth)",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None, "traffic": traffic, "traffic_source": note,
+            "bytes_per_step": nbytes, "ms_per_step": ms, "cells_per_particle": ncells / n,
+            "bytes_model": f"{BUILD_PASSES} radix passes x {BYTES_PASS} B + gather {BYTES_GATHER} B + "
+                           f"keys {BYTES_KEYS} B per particle + {BYTES_CELL} B per cell",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
 
 
 def oracle_sample(P, samples: int, seed: int = 0):
@@ -381,25 +435,47 @@ def oracle_sample(P, samples: int, seed: int = 0):
     return per, detail, oracle.nthreads(), p, sel
 
 
-def cpu_baseline(sim, cfg, P, args):
-    """The oracle on this host's cores (bounded sample) and the force error of
-    the GPU walk against the oracle's direct sum on 256 targets."""
+def oracle_full_step(P):
+    """One whole oracle step of the workload on the host cores: drift, tree
+    build, gravity walk of every particle over the ghost images, kick, drift,
+    collision tree search and resolution.  Returns (seconds, pairs, threads)."""
     import oracle
+    from paper_1110_4876_gb300 import inputs as I
+
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L_SHEET,) * 3, nghost=(1, 1, 0), boundary=2,
+                      integrator=1, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    st = oracle.State(p, *P.arrays())
+    t = time.perf_counter()
+    st.step(1)
+    return time.perf_counter() - t, len(st.last_pairs), oracle.nthreads()
+
+
+def cpu_baseline(sim, cfg, P, args):
+    """The oracle on this host's cores (one whole step of the workload) and
+    the force error of the GPU walk against the oracle's direct sum and its
+    tree at the same theta on 4096 seeded targets."""
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
     from paper_1110_4876_gb300 import rb
 
-    per, detail, cores, p, _ = oracle_sample(P, args.cpu_samples)
-    base = {"value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": detail}
+    secs, npairs, cores = oracle_full_step(P)
+    base = {"value": P.n / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one whole oracle step of the N={P.n:,} sheet ({secs:.1f} s on {cores} threads): "
+                      f"drift, tree build, gravity walk of every particle over 9 images, kick, drift, "
+                      f"tree collision search ({npairs} pairs), resolution"}
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L_SHEET,) * 3, nghost=(1, 1, 0), boundary=2,
+                      integrator=1, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
     # force error of the benchmarked walk at the initial state
     sim_f = make_sim(rb, cfg)
     sim_f.set_particles(P)
     a_gpu = sim_f.gravity()
-    sel = np.random.default_rng(1).choice(P.n, 256, replace=False)
+    sel = np.random.default_rng(1).choice(P.n, 4096, replace=False)
     a_dir = oracle.direct_gravity(p, 0.0, P.x, P.y, P.z, P.m, targets=sel)
     a_tree = oracle.Tree(P.x, P.y, P.z, P.m, L_SHEET).gravity(p, 0.0, targets=sel)
     es, rr, mr = oracle.force_errors(a_gpu[sel], a_dir)
     _, _, mt = oracle.force_errors(a_gpu[sel], a_tree)
     fe = {"vs_direct_sum": {"e_sum": es, "rms_rel": rr, "max_rel": mr},
-          "vs_oracle_tree_same_theta": {"max_rel": mt}, "targets": 256,
+          "vs_oracle_tree_same_theta": {"max_rel": mt}, "targets": 4096,
           "floor": "per-particle denominator floored at 1e-3 rms|a|"}
     return base, fe
 
@@ -674,6 +750,10 @@ def run_reference(args):
     value = 1.0 / per
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * N_SHEET * 1e3,
+            "ms_per_step_basis": "extrapolated: each timed step is a bounded sample (drifts and "
+                                 "tree builds on all particles, walk and search from random "
+                                 "targets) whose per-particle cost is scaled to N; a whole oracle "
+                                 "step is timed by the default run's cpu_baseline",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded shearing-sheet generator)",
             "config": {"workload": workload_name("fp64 oracle"), "particles": N_SHEET},

@@ -990,7 +990,7 @@ __device__ __forceinline__ void walk32g(const GravArgs& A, GroupSmem& G, int wba
 // Plain FP32 walk with group decisions.  kOne: a single box; otherwise a
 // tile whose targets lie in more than one box takes the union walk.
 template <bool kQuad, bool kInside, bool kSoft, bool kOne, int kS>
-__global__ void __launch_bounds__(kMaxWalkBlock, 4) k_walk32g(GravArgs A) {
+__global__ void __launch_bounds__(kMaxWalkBlock, 4) k_gwalk32(GravArgs A) {
     __shared__ GroupSmem gs[kMaxWalkBlock / 32];
     GroupSmem& G = gs[threadIdx.x >> 5];
     const int n = min(A.ctl->n_live, A.ncap);
@@ -1415,7 +1415,7 @@ int walk_prepare() {
     prepare_one(k_walk64<false, true, true>); prepare_one(k_walk64<false, true, false>);
     prepare_one(k_walk64<false, false, true>); prepare_one(k_walk64<false, false, false>);
 #define RB_PREP_G(Q, I, S) \
-    prepare_one(k_walk32g<Q, I, S, true, 4>); prepare_one(k_walk32g<Q, I, S, false, 4>)
+    prepare_one(k_gwalk32<Q, I, S, true, 4>); prepare_one(k_gwalk32<Q, I, S, false, 4>)
     RB_PREP_G(true, true, true); RB_PREP_G(true, true, false);
     RB_PREP_G(true, false, true); RB_PREP_G(true, false, false);
     RB_PREP_G(false, true, true); RB_PREP_G(false, true, false);
@@ -1468,7 +1468,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s, T.tq, T.nq);
     // every kernel below runs the persistent grid that fits on the GPU
 #define RB_LAUNCH(...) __VA_ARGS__<<<persistent_grid(__VA_ARGS__, block, T.cap_n), block, 0, s>>>(A)
-#define RB_W32G(Q, I, S, ONE) RB_LAUNCH(k_walk32g<Q, I, S, ONE, 4>)
+#define RB_W32G(Q, I, S, ONE) RB_LAUNCH(k_gwalk32<Q, I, S, ONE, 4>)
 #define RB_W32(Q, I, PO, S)                                                \
     do {                                                                   \
         if (group == 0) {                                                  \
