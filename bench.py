@@ -506,13 +506,17 @@ def run_ensemble(args):
         ens.set_box(b, (Lb, Lb, Lb))
         ens.set_particles(P, box=b)
     tuned = rb.rb_autotune(ens.h)
+    clk = Clocks(torch.cuda.current_device()).__enter__()
     ens.step(args.warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    tw0 = time.time()
     e0.record(stream)
     ens.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk.window(tw0, time.time())
+    clk.__exit__()
     t_batched = e0.elapsed_time(e1) / 1e3
     # per-stage split of the batched step, from a separate profiled pass
     rb.rb_set_profiling(ens.h, True)
@@ -544,6 +548,7 @@ def run_ensemble(args):
             "steps": args.steps, "warmup": args.warmup, "walk_block, search_block, walk_group": list(tuned),
             "pairs_per_step": pairs / args.steps,
             "stage_ms_per_step (profiled pass)": {k: v / args.steps for k, v in stage_sum.items()},
+            "clocks (batched timed region)": clk.summary(),
             "dtype": "f64" if args.walk == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "256 shearing boxes, N_b log-uniform [500, 20000], surface "
                                    "density log-uniform [200, 1000] kg/m^2, theta=0.5, SEI, eps=0.5"}}
@@ -593,6 +598,8 @@ def run_compare(args):
 
     rb.load()
     stream = torch.cuda.Stream()
+    clk = Clocks(torch.cuda.current_device()).__enter__()
+    t_clk = time.time()
     P = I.sheet(L_SHEET, N_SHEET, SEED)
     sel = np.random.default_rng(1).choice(P.n, 4096, replace=False)
     p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L_SHEET,) * 3, nghost=(1, 1, 0), boundary=2,
@@ -614,10 +621,13 @@ def run_compare(args):
         rows[name] = {"particle_steps_per_s": N_SHEET / (ms / 1e3), "ms_per_step": ms,
                       "walk_ms": wms, "force_error_vs_direct": err}
         del sim
+    clk.window(t_clk, time.time())
+    clk.__exit__()
     line = {"metric": "particle-steps/s and force error vs direct sum per walk form (1M sheet)",
             "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "forms": rows,
             "direct_sum": {"targets": 4096, "images": 9, "seconds": t_dir, "cores": oracle.nthreads()},
             "data": "synthetic", "config": {"workload": workload_name("fp32")}}
+    line["clocks (whole run)"] = clk.summary()
     print(json.dumps(line), flush=True)
     return line
 
@@ -635,6 +645,8 @@ def run_plummer(args):
 
     rb.load()
     stream = torch.cuda.Stream()
+    clk = Clocks(torch.cuda.current_device()).__enter__()
+    t_clk = time.time()
     n = 1 << 20
     P = I.plummer(n, 3)
     sel = np.random.default_rng(1).choice(P.n, 4096, replace=False)
@@ -656,12 +668,15 @@ def run_plummer(args):
             rows[f"{walk} theta={theta}"] = {"particle_steps_per_s": n / (ms / 1e3), "ms_per_step": ms,
                                              "walk_ms": wms, "force_error_vs_direct": err}
             del sim
+    clk.window(t_clk, time.time())
+    clk.__exit__()
     line = {"metric": "particle-steps/s and force error vs direct sum, Plummer N=2^20", "unit": UNIT,
             "steps": args.steps, "warmup": args.warmup, "forms": rows,
             "direct_sum": {"targets": 4096, "seconds": t_dir, "cores": oracle.nthreads()},
             "data": "synthetic (seeded Plummer sampler)",
             "config": {"workload": "Plummer G=M=a=1, N=1,048,576, open box 128, leap-frog dt=1e-3, "
                                    "softening 1e-3, quadrupole, no collisions"}}
+    line["clocks (whole run)"] = clk.summary()
     print(json.dumps(line), flush=True)
     return line
 
@@ -680,6 +695,8 @@ def run_sweep(args):
 
     rb.load()
     stream = torch.cuda.Stream()
+    clk = Clocks(torch.cuda.current_device()).__enter__()
+    t_clk = time.time()
     rows = {}
     n = args.particles
     Ly = 20.0
@@ -723,12 +740,120 @@ def run_sweep(args):
                                      P.n / (ms / 1e3), "ms_per_step": ms, "detection_ms": det_ms,
                                      "pairs_per_step": pairs / args.steps}
             del sim
+    clk.window(t_clk, time.time())
+    clk.__exit__()
     line = {"metric": "particle-steps/s of collision-only steps, plane sweep vs tree search",
             "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "cases": rows,
             "data": "synthetic (seeded shearing-sheet generator)",
             "config": {"workload": f"no self-gravity, SEI, shear, eps=0.5; elongated box "
                                    f"{Lx:.0f} x {Ly:g} m with N={n:,}; square box "
                                    f"{L_SHEET:g} x {L_SHEET:g} m with N={N_SHEET:,}"}}
+    line["clocks (whole run)"] = clk.summary()
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def _pairs_match(job):
+    """Worker (spawned process): the oracle's Eq. 3 search on the GPU's
+    end-of-step positions, compared with the GPU step's pair keys."""
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
+
+    k, L, t, x, y, z, r, ids, keys = job
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L,) * 3, nghost=(1, 1, 0), boundary=2, integrator=1,
+                      theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    ref = oracle.collide_tree(p, t, x, y, z, r, ids)
+    return k, bool(np.array_equal(ref, keys)), len(keys), len(ref)
+
+
+def run_precision(args):
+    """The mid shearing sheet (N = 100,000, box 650 m, SEI, theta = 0.5,
+    collisions eps = 0.5) for --precision-steps steps with the FP32 walk and
+    with the FP64 walk: force errors against the oracle's FP64 tree (same
+    theta) and its direct sum on 4096 seeded targets at the first, middle
+    and last step; the collision pair set of every step against the
+    oracle's search on the GPU's positions; the energy (Sect. 6.2) every 10
+    steps.  One JSON line."""
+    import multiprocessing
+
+    nwork = max(1, min(32, (os.cpu_count() or 2) - 1))
+    pool = multiprocessing.get_context("spawn").Pool(nwork)   # before any GPU call
+    import torch
+
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    L, n, nsteps = 650.0, 100_000, args.precision_steps
+    P = I.sheet(L, n, 2)
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L,) * 3, nghost=(1, 1, 0), boundary=2, integrator=1,
+                      theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    sel = np.random.default_rng(1).choice(n, 4096, replace=False)
+    marks = sorted({0, nsteps // 2, nsteps})
+    clk = Clocks(torch.cuda.current_device()).__enter__()
+    t_start = time.time()
+    forms = {}
+    for walk in ("fp32", "fp64"):
+        cfg = sheet_config(rb, walk)
+        cfg["box"] = (L, L, L)
+        sim = rb.Sim(stream=stream.cuda_stream, **cfg)
+        sim.set_particles(P)
+        rb.rb_autotune(sim.h)
+        sim.set_particles(P)
+
+        def errors(step):
+            g = sim.particles()
+            a = sim.gravity()
+            t = oracle.time_at(p, 2 * step)
+            a_tree = oracle.Tree(g["x"], g["y"], g["z"], g["m"], L).gravity(p, t, targets=sel)
+            a_dir = oracle.direct_gravity(p, t, g["x"], g["y"], g["z"], g["m"], targets=sel)
+            return {"vs_oracle_tree_same_theta": _errors(a[sel], a_tree),
+                    "vs_direct_sum": _errors(a[sel], a_dir)}
+
+        err = {0: errors(0)}
+        E0, _ = sim.energy()
+        energy = [(0, E0)]
+        pending, results, step_ms = [], [], []
+        for k in range(1, nsteps + 1):
+            sim.step(1)
+            step_ms.append(sim.stats()["ms_last_step"])
+            g = sim.particles()
+            keys = rb.pair_keys(*sim.pairs(detect=False))
+            pending.append(pool.apply_async(_pairs_match, ((k, L, oracle.time_at(p, 2 * k), g["x"], g["y"],
+                                                            g["z"], g["r"], g["id"], keys),)))
+            while len(pending) > 4 * nwork:
+                results.append(pending.pop(0).get())
+            if k % 10 == 0:
+                energy.append((k, sim.energy()[0]))
+            if k in marks:
+                err[k] = errors(k)
+        results += [r.get() for r in pending]
+        equal = sum(1 for r in results if r[1])
+        forms[walk] = {
+            "ms_per_step_device": statistics.mean(step_ms),
+            "particle_steps_per_s_device": n / (statistics.mean(step_ms) / 1e3),
+            "force_error": {f"step {k}": v for k, v in sorted(err.items())},
+            "pair_sets": {"steps_checked": len(results), "steps_equal": equal,
+                          "pairs_per_step": statistics.mean(r[2] for r in results),
+                          "first_mismatch": next((r[0] for r in sorted(results) if not r[1]), None)},
+            "energy": {"every": 10, "E0": E0,
+                       "rel_drift": [(k, (E - E0) / abs(E0)) for k, E in energy]},
+        }
+        del sim
+    clk.window(t_start, time.time())
+    clk.__exit__()
+    pool.close()
+    pool.join()
+    line = {"metric": "precision run: force error, pair-set equality and energy per walk form",
+            "unit": "(see fields)", "steps": nsteps, "forms": forms, "clocks": clk.summary(),
+            "data": "synthetic (seeded shearing-sheet generator)",
+            "config": {"workload": f"shearing sheet N={n:,} box {L:g}x{L:g} m, 1 ghost ring, SEI, "
+                                   f"theta=0.5 quadrupole, collisions eps=0.5, {nsteps} steps",
+                       "targets": 4096, "oracle_workers": nwork,
+                       "energy": "E = K + SEI tidal/vertical term + W (Sect. 6.2), W from the FP64 "
+                                 "tree potential; collisions with eps = 0.5 dissipate energy"}}
     print(json.dumps(line), flush=True)
     return line
 
@@ -787,6 +912,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="plane sweep vs tree search on collision-only elongated and square sheets")
     ap.add_argument("--cases", default="elongated,square", help="--sweep cases to run")
+    ap.add_argument("--precision", action="store_true",
+                    help="100k sheet, FP32 and FP64 walks: force errors, per-step pair sets, energy")
+    ap.add_argument("--precision-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -801,6 +929,8 @@ def main():
         run_plummer(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.precision:
+        run_precision(args)
     else:
         run_ours(args)
 
