@@ -858,6 +858,93 @@ def run_precision(args):
     return line
 
 
+def _at_error(rows, target):
+    """Throughput where a form's e_sum crosses `target`, interpolating
+    log(e_sum) and throughput linearly in theta; None if it never does."""
+    pts = sorted((r["theta"], r["force_error_vs_direct"]["e_sum"], r["particle_steps_per_s"]) for r in rows)
+    for (t0, e0, v0), (t1, e1, v1) in zip(pts, pts[1:]):
+        if e0 <= target <= e1 and e1 > e0:
+            f = (math.log(target) - math.log(e0)) / (math.log(e1) - math.log(e0))
+            return {"theta": t0 + f * (t1 - t0), "particle_steps_per_s": v0 + f * (v1 - v0)}
+    if pts and abs(pts[0][1] - target) <= 1e-12 * target:
+        return {"theta": pts[0][0], "particle_steps_per_s": pts[0][2]}
+    return None
+
+
+def run_learned_sweep(args):
+    """The learned far-field correction against the plain FP32 walk on the
+    1M sheet: the network trained once on ~10M residuals (two snapshots of
+    the small and mid sheets), then e_sum / rms / max force error against
+    the oracle's direct sum on 4096 targets and particle-steps/s of the full
+    step for the plain walk at theta 0.5 ... 0.8 and the learned walk
+    (fallback 0.5) at theta 0.6, 0.7, 0.8; and each form's throughput where
+    its error equals the plain theta = 0.5 error.  One JSON line."""
+    import torch
+
+    import oracle
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import learned
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    clk = Clocks(torch.cuda.current_device()).__enter__()
+    t_clk = time.time()
+    t = time.perf_counter()
+    X, Y = learned.samples()
+    t_samples = time.perf_counter() - t
+    t = time.perf_counter()
+    w, hist = rb.rb_mlp_train(X, Y, learned.init_weights(3), epochs=12, batch=2048, lr=1e-3, seed=1,
+                              stream=stream.cuda_stream)
+    t_train = time.perf_counter() - t
+    batches = 12 * math.ceil(len(X) / 2048)
+    P = I.sheet(L_SHEET, N_SHEET, SEED)
+    sel = np.random.default_rng(1).choice(P.n, 4096, replace=False)
+    p = oracle.Params(G=I.G_SI, omega=I.OMEGA, L=(L_SHEET,) * 3, nghost=(1, 1, 0), boundary=2,
+                      integrator=1, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    a_dir = oracle.direct_gravity(p, 0.0, P.x, P.y, P.z, P.m, targets=sel)
+    forms = {"plain": [], "learned": []}
+    for form, thetas in (("plain", (0.5, 0.55, 0.6, 0.65, 0.7, 0.75, 0.8)), ("learned", (0.6, 0.7, 0.8))):
+        for theta in thetas:
+            cfg = sheet_config(rb, "fp32" if form == "plain" else "learned")
+            cfg["theta"] = theta
+            sim = rb.Sim(stream=stream.cuda_stream, **cfg)
+            if form == "learned":
+                rb.rb_load_mlp(sim.h, w, 0.5)
+            sim.set_particles(P)
+            a = sim.gravity()
+            err = _errors(a[sel], a_dir)
+            corr = sim.stats()["corrections"]
+            sim.set_particles(P)
+            ms, wms = _timed(sim, stream, args.steps, args.warmup)
+            forms[form].append({"theta": theta, "particle_steps_per_s": N_SHEET / (ms / 1e3),
+                                "ms_per_step": ms, "walk_ms": wms, "force_error_vs_direct": err,
+                                "corrected_cells_per_particle": corr / N_SHEET if form == "learned" else 0})
+            del sim
+    target = forms["plain"][0]["force_error_vs_direct"]["e_sum"]
+    clk.window(t_clk, time.time())
+    clk.__exit__()
+    line = {"metric": "learned far-field correction vs plain FP32 walk: force error and particle-steps/s",
+            "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "forms": forms,
+            "equal_error": {"target_e_sum (plain theta=0.5)": target,
+                            "plain": _at_error(forms["plain"], target),
+                            "learned": _at_error(forms["learned"], target)},
+            "training": {"rows": len(X), "epochs": 12, "batch": 2048, "batches": batches,
+                         "sampling_s": t_samples, "training_s": t_train,
+                         "ms_per_batch": 1e3 * t_train / batches,
+                         "loss_per_epoch": [float(v) for v in hist],
+                         "recipe": "residuals of cells accepted at theta 0.8 with w/R > 0.5, two "
+                                   "snapshots (0 and 50 steps) of the 100 m / 2400 and 650 m / "
+                                   "100,000 sheets, kept fractions 1 and 0.42"},
+            "clocks (whole run)": clk.summary(),
+            "data": "synthetic (seeded shearing-sheet generator)",
+            "config": {"workload": workload_name("fp32").replace("theta=0.5 quadrupole, fp32 walk",
+                                                                 "theta swept, quadrupole"),
+                       "targets": 4096}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -915,6 +1002,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="100k sheet, FP32 and FP64 walks: force errors, per-step pair sets, energy")
     ap.add_argument("--precision-steps", type=int, default=1000)
+    ap.add_argument("--learned-sweep", action="store_true",
+                    help="learned vs plain FP32 walk over theta on the 1M sheet, at equal error")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -931,6 +1020,8 @@ def main():
         run_sweep(args)
     elif args.precision:
         run_precision(args)
+    elif args.learned_sweep:
+        run_learned_sweep(args)
     else:
         run_ours(args)
 

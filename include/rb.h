@@ -282,6 +282,13 @@ int rb_mlp_train(const float* X, const float* Y, int64_t n, int epochs, int batc
  * FP32 accumulation). */
 int rb_mlp_grad(const float* w, const float* X, const float* Y, int64_t n, float* grad, float* loss,
                 void* cuda_stream);
+/* Debug form of rb_mlp_grad: the same gradient and loss with every operand,
+ * activation and sum in FP32 (no BF16 rounding; products summed in index
+ * order, rows in row order, so the result is deterministic), for checking
+ * the backward pass element by element against an FP64 reference.
+ * 1 <= n <= 4096 (it keeps one gradient per row); RB_ERR_ARG otherwise. */
+int rb_mlp_grad_fp32(const float* w, const float* X, const float* Y, int64_t n, float* grad,
+                     float* loss, void* cuda_stream);
 
 /* Energy and momentum sums without any device allocation.  The paper has no
  * counterpart: this entry point serves callers that cannot call cudaMalloc,

@@ -1439,6 +1439,47 @@ int rb_mlp_grad(const float* w, const float* X, const float* Y, int64_t n, float
     return RB_OK;
 }
 
+int rb_mlp_grad_fp32(const float* w, const float* X, const float* Y, int64_t n, float* grad,
+                     float* loss, void* cuda_stream) {
+    if (!w || !X || !Y || n < 1 || n > 4096 || !grad) {
+        g_create_error = "rb_mlp_grad_fp32: bad arguments (1 <= n <= 4096)";
+        return RB_ERR_ARG;
+    }
+    MlpBufs B;
+    B.s = static_cast<cudaStream_t>(cuda_stream);
+    if (!B.s) {
+        cudaStreamCreateWithFlags(&B.s, cudaStreamNonBlocking);
+        B.own = true;
+    }
+    float* dw = B.alloc<float>(RB_MLP_PARAMS);
+    float* dX = B.alloc<float>(12 * n);
+    float* dY = B.alloc<float>(3 * n);
+    float* dG = B.alloc<float>((size_t)n * RB_MLP_PARAMS);
+    float* dl = B.alloc<float>(n);
+    float* dg = B.alloc<float>(RB_MLP_PARAMS);
+    float* dloss = B.alloc<float>(1);
+    if (!dw || !dX || !dY || !dG || !dl || !dg || !dloss) {
+        g_create_error = "rb_mlp_grad_fp32: device allocation failed";
+        return RB_ERR_CUDA;
+    }
+    cudaMemcpyAsync(dw, w, sizeof(float) * RB_MLP_PARAMS, cudaMemcpyHostToDevice, B.s);
+    cudaMemcpyAsync(dX, X, sizeof(float) * 12 * n, cudaMemcpyHostToDevice, B.s);
+    cudaMemcpyAsync(dY, Y, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, B.s);
+    if (mlp::grad_f32_async(dw, dX, dY, (int)n, dG, dl, dg, dloss, B.s) != cudaSuccess) {
+        g_create_error = "rb_mlp_grad_fp32: launch failed";
+        return RB_ERR_CUDA;
+    }
+    float lsum = 0.f;
+    cudaMemcpyAsync(grad, dg, sizeof(float) * RB_MLP_PARAMS, cudaMemcpyDeviceToHost, B.s);
+    cudaMemcpyAsync(&lsum, dloss, sizeof(float), cudaMemcpyDeviceToHost, B.s);
+    if (cudaStreamSynchronize(B.s) != cudaSuccess) {
+        g_create_error = "rb_mlp_grad_fp32: CUDA error";
+        return RB_ERR_CUDA;
+    }
+    if (loss) *loss = lsum;
+    return RB_OK;
+}
+
 int rb_mlp_train(const float* X, const float* Y, int64_t n, int epochs, int batch, double lr,
                  uint64_t seed, const float* w_init, float* w_out, float* loss_hist,
                  void* cuda_stream) {

@@ -348,6 +348,10 @@ cudaError_t grad_async(const void* wbf, const float* wf, const float* X, const f
                        cudaStream_t s);
 void adam_async(float* w, float* m, float* v, const float* grad, void* wbf, float lr, int step,
                 cudaStream_t s);
+// FP32 debug gradient on canonical (unpadded) weights: G holds n x 9347
+// per-row gradients, lrow n per-row squared errors.
+cudaError_t grad_f32_async(const float* w, const float* X, const float* Y, int n, float* G, float* lrow,
+                           float* grad, float* loss, cudaStream_t s);
 void to_bf16_async(const float* w, void* wbf, cudaStream_t s);
 void label_async(const ReqArgs& A, float* X, float* Y, int64_t* meta, int max_req, cudaStream_t s);
 }  // namespace mlp

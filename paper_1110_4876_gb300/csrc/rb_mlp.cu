@@ -341,6 +341,98 @@ __global__ void k_mlp_to_bf16(const float* __restrict__ w, __nv_bfloat16* __rest
     if (i < kPad) wbf[i] = __float2bfloat16_rn(w[i]);
 }
 
+// ---- FP32 debug gradient (canonical layout, no BF16 rounding) ----
+// One thread per row: forward and backward of the network in plain FP32
+// (inputs, weights, activations and accumulation), products summed in index
+// order; the row's gradient of the mean squared error goes to G[row][9347].
+// A second launch sums the rows in row order, one thread per parameter, so
+// the result does not depend on scheduling.
+constexpr int kCW1 = 0, kCB1 = 12 * 64, kCW2 = kCB1 + 64, kCB2 = kCW2 + 64 * 64, kCW3 = kCB2 + 64,
+              kCB3 = kCW3 + 64 * 64, kCW4 = kCB3 + 64, kCB4 = kCW4 + 64 * 3, kCN = kCB4 + 3;
+static_assert(kCN == 9347, "canonical parameter count");
+
+__device__ __forceinline__ float gelu_grad_f32(float z) {
+    const float t = tanhf(kGeluC * (z + 0.044715f * z * z * z));
+    return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * kGeluC * (1.f + 3.f * 0.044715f * z * z);
+}
+
+__global__ void __launch_bounds__(64) k_mlp_grad_rows_f32(const float* __restrict__ w,
+                                                           const float* __restrict__ X,
+                                                           const float* __restrict__ Y, int n,
+                                                           float* __restrict__ G,
+                                                           float* __restrict__ lrow) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float x[12], z1[64], z2[64], z3[64], h1[64], h2[64], h3[64], pr[3], dy[3];
+    for (int k = 0; k < 12; k++) x[k] = X[(size_t)r * 12 + k];
+    const int inW[3] = {kCW1, kCW2, kCW3}, inB[3] = {kCB1, kCB2, kCB3}, fan[3] = {12, 64, 64};
+    float* zs[3] = {z1, z2, z3};
+    float* hs[3] = {h1, h2, h3};
+    const float* in = x;
+    for (int L = 0; L < 3; L++) {
+        for (int j = 0; j < 64; j++) {
+            float a = w[inB[L] + j];
+            for (int k = 0; k < fan[L]; k++) a = fmaf(in[k], w[inW[L] + k * 64 + j], a);
+            zs[L][j] = a;
+            hs[L][j] = gelu(a);
+        }
+        in = hs[L];
+    }
+    float ls = 0.f;
+    for (int c = 0; c < 3; c++) {
+        float a = w[kCB4 + c];
+        for (int k = 0; k < 64; k++) a = fmaf(h3[k], w[kCW4 + k * 3 + c], a);
+        pr[c] = a;
+        const float d = a - Y[(size_t)r * 3 + c];
+        ls = fmaf(d, d, ls);
+        dy[c] = 2.f * d / (3.f * (float)n);
+    }
+    lrow[r] = ls;
+    float* g = G + (size_t)r * kCN;
+    for (int c = 0; c < 3; c++) g[kCB4 + c] = dy[c];
+    for (int k = 0; k < 64; k++)
+        for (int c = 0; c < 3; c++) g[kCW4 + k * 3 + c] = h3[k] * dy[c];
+    // layer 3: dZ3 = (W4 dy) * gelu'(Z3), kept in z3
+    for (int j = 0; j < 64; j++) {
+        float a = 0.f;
+        for (int c = 0; c < 3; c++) a = fmaf(w[kCW4 + j * 3 + c], dy[c], a);
+        z3[j] = a * gelu_grad_f32(z3[j]);
+    }
+    // layers 3, 2, 1: weight and bias gradients, then the previous layer's dZ
+    const float* dz = z3;
+    for (int L = 2; L >= 0; L--) {
+        const float* prev = L == 0 ? x : hs[L - 1];
+        for (int j = 0; j < 64; j++) g[inB[L] + j] = dz[j];
+        for (int k = 0; k < fan[L]; k++)
+            for (int j = 0; j < 64; j++) g[inW[L] + k * 64 + j] = prev[k] * dz[j];
+        if (L > 0) {
+            float* zp = zs[L - 1];
+            for (int k = 0; k < 64; k++) {
+                float a = 0.f;
+                for (int j = 0; j < 64; j++) a = fmaf(w[inW[L] + k * 64 + j], dz[j], a);
+                zp[k] = a * gelu_grad_f32(zp[k]);
+            }
+            dz = zp;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mlp_grad_sum_f32(const float* __restrict__ G,
+                                                          const float* __restrict__ lrow, int n,
+                                                          float* __restrict__ grad, float* __restrict__ loss) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < kCN) {
+        float a = 0.f;
+        for (int r = 0; r < n; r++) a += G[(size_t)r * kCN + j];
+        grad[j] = a;
+    }
+    if (j == 0) {
+        float l = 0.f;
+        for (int r = 0; r < n; r++) l += lrow[r];
+        *loss = l / (3.f * (float)n);
+    }
+}
+
 // ---- requests (target slot, image, cell entry) ----
 
 struct CellView {
@@ -559,6 +651,13 @@ cudaError_t grad_async(const void* wbf, const float* wf, const float* X, const f
     const int blocks = std::max(1, std::min((tiles + kWarps - 1) / kWarps, 2 * 152));
     k_mlp_grad<<<blocks, kWarps * 32, sizeof(TrainSmem), s>>>(
         static_cast<const __nv_bfloat16*>(wbf), wf, X, Y, idx, n, n_total, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_f32_async(const float* w, const float* X, const float* Y, int n, float* G, float* lrow,
+                           float* grad, float* loss, cudaStream_t s) {
+    k_mlp_grad_rows_f32<<<(n + 63) / 64, 64, 0, s>>>(w, X, Y, n, G, lrow);
+    k_mlp_grad_sum_f32<<<(kCN + 255) / 256, 256, 0, s>>>(G, lrow, n, grad, loss);
     return cudaGetLastError();
 }
 

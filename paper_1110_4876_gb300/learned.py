@@ -1,9 +1,9 @@
 """Training recipe of the learned far-field correction.
 
-Residual samples are drawn with librb from the small (100 m, 2400 particles)
-and mid (650 m, 100 000 particles) shearing sheets: every cell accepted at
-theta = 0.8 with w/R > 0.5 is a candidate, and a counter-based hash keeps a
-fraction of them.  The network is then trained on the GPU by librb's own
+Residual samples are drawn with librb from two snapshots each of the small
+(100 m, 2400 particles) and mid (650 m, 100 000 particles) shearing sheets:
+every cell accepted at theta = 0.8 with w/R > 0.5 is a candidate, and a
+counter-based hash keeps a fraction of them (about 10 million rows).  The network is then trained on the GPU by librb's own
 kernels (Adam, standardised inputs/outputs, zero-initialised last layer).
 Everything numeric runs in librb; this module only chooses the recipe.
 """
@@ -37,15 +37,27 @@ def sheet_config(walk: int, theta: float, L: float) -> dict:
                 collisions=0, walk=walk)
 
 
+# (box side, particles, seed, kept fraction, steps between snapshots): two
+# snapshots of each sheet, the initial state and one after 50 steps of
+# self-gravity, give ~10 million residuals
+RECIPE = ((100.0, 2400, 1, 1.0), (650.0, 100_000, 2, 0.42))
+SNAPSHOT_STEPS = (0, 50)
+
+
 def samples(seed: int = 7):
-    """(X, Y) residual samples from the small and mid sheets."""
+    """(X, Y) residual samples from snapshots of the small and mid sheets."""
     Xs, Ys = [], []
-    for L, N, s, prob in ((100.0, 2400, 1, 1.0), (650.0, 100_000, 2, 0.05)):
+    for L, N, s, prob in RECIPE:
         sim = rb.Sim(**sheet_config(rb.RB_WALK_FP32, THETA_WIDE, L))
         sim.set_particles(I.sheet(L, N, s))
-        X, Y, _ = rb.rb_mlp_samples(sim.h, THETA_WIDE, THETA_FALLBACK, prob, seed, 2_000_000)
-        Xs.append(X)
-        Ys.append(Y)
+        done = 0
+        for k, steps in enumerate(SNAPSHOT_STEPS):
+            sim.step(steps - done)
+            done = steps
+            X, Y, _ = rb.rb_mlp_samples(sim.h, THETA_WIDE, THETA_FALLBACK, prob, seed + k, 8_000_000,
+                                        with_meta=False)
+            Xs.append(X)
+            Ys.append(Y)
     return np.concatenate(Xs), np.concatenate(Ys)
 
 

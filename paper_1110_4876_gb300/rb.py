@@ -28,7 +28,7 @@ EXPORTS = [
     "rb_compute_gravity", "rb_get_accelerations", "rb_get_counts", "rb_get_tree",
     "rb_detect_collisions", "rb_get_pairs", "rb_set_time", "rb_get_time", "rb_stats",
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
-    "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_autotune",
+    "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_mlp_grad_fp32", "rb_autotune",
     "rb_set_pair_capacity", "rb_debug_hold_pair", "rb_set_launch_shape", "rb_set_n_active", "rb_set_restitution",
 ]
 RB_MLP_PARAMS = 9347
@@ -113,6 +113,7 @@ def load():
                                    C.POINTER(i64), _VP, _VP, _VP]
     lib.rb_mlp_train.argtypes = [_VP, _VP, i64, i32, i32, C.c_double, C.c_uint64, _VP, _VP, _VP, _VP]
     lib.rb_mlp_grad.argtypes = [_VP, _VP, _VP, i64, _VP, _VP, _VP]
+    lib.rb_mlp_grad_fp32.argtypes = [_VP, _VP, _VP, i64, _VP, _VP, _VP]
     lib.rb_energy_sums_noalloc.argtypes = [i64] + [_VP] * 7 + [i32, C.c_double, C.c_double, _VP,
                                                               _VP]
     lib.rb_destroy.argtypes = [_P]
@@ -359,16 +360,17 @@ def rb_load_mlp(sim, w, theta_fallback: float):
     _check(load().rb_load_mlp(sim, _ptr(w), len(w), theta_fallback), sim)
 
 
-def rb_mlp_samples(sim, theta_hi: float, theta_lo: float, prob: float, seed: int, cap: int):
-    """Training samples on the current positions: (X (n,12), Y (n,3), meta (n,5))."""
+def rb_mlp_samples(sim, theta_hi: float, theta_lo: float, prob: float, seed: int, cap: int,
+                   with_meta: bool = True):
+    """Training samples on the current positions: (X (n,12), Y (n,3), meta (n,5) or None)."""
     X = np.zeros((cap, 12), np.float32)
     Y = np.zeros((cap, 3), np.float32)
-    meta = np.zeros((cap, 5), np.int64)
+    meta = np.zeros((cap, 5), np.int64) if with_meta else None
     n = C.c_int64(0)
     _check(load().rb_mlp_samples(sim, theta_hi, theta_lo, prob, seed, cap, C.byref(n), _ptr(X),
                                  _ptr(Y), _ptr(meta)), sim)
     k = n.value
-    return X[:k], Y[:k], meta[:k]
+    return X[:k].copy(), Y[:k].copy(), (meta[:k] if with_meta else None)
 
 
 def rb_mlp_train(X, Y, w_init, epochs: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
@@ -392,6 +394,18 @@ def rb_mlp_grad(w, X, Y, stream=None):
     g = np.zeros(RB_MLP_PARAMS, np.float32)
     loss = C.c_float(0.0)
     _check(load().rb_mlp_grad(_ptr(w), _ptr(X), _ptr(Y), len(X), _ptr(g), C.byref(loss), stream),
+           None)
+    return g, loss.value
+
+
+def rb_mlp_grad_fp32(w, X, Y, stream=None):
+    """(gradient (9347,), mean squared error) from the FP32 debug kernels (n <= 4096)."""
+    X = _f32(X, (-1, 12))
+    Y = _f32(Y, (-1, 3))
+    w = _f32(w)
+    g = np.zeros(RB_MLP_PARAMS, np.float32)
+    loss = C.c_float(0.0)
+    _check(load().rb_mlp_grad_fp32(_ptr(w), _ptr(X), _ptr(Y), len(X), _ptr(g), C.byref(loss), stream),
            None)
     return g, loss.value
 

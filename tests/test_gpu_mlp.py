@@ -50,6 +50,51 @@ def test_gradients_match_oracle_backward(rb):
             k += size
 
 
+def _abs_envelope(theta, X, Y):
+    """Per gradient element, the sum over rows of the absolute values of the
+    terms the element adds up (|a|^T |d| for weights, sum |d| for biases),
+    from the FP64 forward and backward of oracle/mlp.py.  An FP32 evaluation
+    of an element is accurate relative to this sum, not to the net value,
+    which can nearly cancel."""
+    layers = omlp.unpack(theta)
+    P, (acts, pre) = omlp.forward(theta, X)
+    d = 2.0 * (P - Y) / (X.shape[0] * P.shape[1])
+    env = []
+    for li in range(len(layers) - 1, -1, -1):
+        W, _ = layers[li]
+        if li < len(layers) - 1:
+            d = d * omlp.gelu_grad(pre[li])
+        env.append((np.abs(acts[li]).T @ np.abs(d), np.abs(d).sum(axis=0)))
+        d = d @ W.T
+    env.reverse()
+    return np.concatenate([np.concatenate([eW.ravel(), eb]) for eW, eb in env])
+
+
+def test_fp32_debug_gradients_match_oracle_elementwise(rb):
+    """FP32 debug mode of the backward pass against the FP64 backward,
+    element by element.  Every FP32 operation rounds to within u = 6e-8; an
+    element's error is then a few u times the sum of the absolute values of
+    the row terms it adds up (256 rows, each a product of an activation and
+    an output gradient that went through 64-term sums and tanhf), so the
+    bound is 1e-6 of that sum (about 16 u, the random-walk size of 256
+    roundings), element by element.  The losses agree to 1e-6."""
+    g = np.random.default_rng(5)
+    theta = omlp.init(11)
+    X = g.normal(0, 1, (256, 12))
+    Y = g.normal(0, 0.3, (256, 3))
+    # the FP64 reference on the same FP32-rounded inputs and weights
+    t32, X32, Y32 = (a.astype(np.float32).astype(np.float64) for a in (theta, X, Y))
+    L_ref, grad_ref = omlp.backward(t32, X32, Y32)
+    env = _abs_envelope(t32, X32, Y32)
+    grad, L = rb.rb_mlp_grad_fp32(theta, X, Y)
+    assert L == pytest.approx(L_ref, rel=1e-6)
+    rel = np.abs(grad.astype(np.float64) - grad_ref) / env
+    print("worst error / absolute sum", float(np.max(rel)))
+    assert float(np.max(rel)) <= 1e-6
+    with pytest.raises(rb.RbError):
+        rb.rb_mlp_grad_fp32(theta, np.zeros((4097, 12)), np.zeros((4097, 3)))
+
+
 def _canonical_tree(orc, P, L):
     """Oracle canonical cells with parent/child links and direct members."""
     cells = sorted(orc.Tree(P.x, P.y, P.z, P.m, L).cells(), key=lambda c: c[0])
