@@ -945,6 +945,20 @@ def run_learned_sweep(args):
     return line
 
 
+def run_oracle_step(args):
+    """One whole oracle step of the 1M sheet on this host (OMP_NUM_THREADS
+    sets the threads), timed; one JSON line."""
+    from paper_1110_4876_gb300 import inputs as I
+
+    P = I.sheet(L_SHEET, N_SHEET, SEED)
+    secs, npairs, cores = oracle_full_step(P)
+    line = {"metric": "oracle step time (whole DKD step, FP64, host cores)", "unit": "s",
+            "value": secs, "particle_steps_per_s": P.n / secs, "threads": cores, "pairs": npairs,
+            "config": {"workload": workload_name("fp64 oracle"), "particles": P.n}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -1002,6 +1016,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="100k sheet, FP32 and FP64 walks: force errors, per-step pair sets, energy")
     ap.add_argument("--precision-steps", type=int, default=1000)
+    ap.add_argument("--oracle-step", action="store_true",
+                    help="time one whole oracle step of the 1M sheet on the host (OMP_NUM_THREADS)")
     ap.add_argument("--learned-sweep", action="store_true",
                     help="learned vs plain FP32 walk over theta on the 1M sheet, at equal error")
     args = ap.parse_args()
@@ -1022,6 +1038,8 @@ def main():
         run_precision(args)
     elif args.learned_sweep:
         run_learned_sweep(args)
+    elif args.oracle_step:
+        run_oracle_step(args)
     else:
         run_ours(args)
 
