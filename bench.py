@@ -329,7 +329,7 @@ def run_ours(args):
                                   else "")),
                    "l2": "no flush: working set (2 x 72 MB particle sets + ~0.4 GB tree) > 129 MB L2",
                    "pairs_per_step": statistics.mean(pairs),
-                   "walk_block, search_block, walk_group": list(tuned)},
+                   "walk_block, search_block, walk_group, tile_order": list(tuned)},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
         "roofline_build": build_roofline(stage_sum, args.steps, cells, peaks),
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
@@ -545,7 +545,7 @@ def run_ensemble(args):
     line = {"metric": "particle-steps/s (256-box shearing-sheet ensemble)", "unit": UNIT,
             "value": ntot * args.steps / t_batched, "looped_single_boxes": ntot * args.steps / t_looped,
             "speedup": t_looped / t_batched, "particles": ntot, "boxes": len(parts),
-            "steps": args.steps, "warmup": args.warmup, "walk_block, search_block, walk_group": list(tuned),
+            "steps": args.steps, "warmup": args.warmup, "walk_block, search_block, walk_group, tile_order": list(tuned),
             "pairs_per_step": pairs / args.steps,
             "stage_ms_per_step (profiled pass)": {k: v / args.steps for k, v in stage_sum.items()},
             "clocks (batched timed region)": clk.summary(),

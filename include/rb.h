@@ -59,6 +59,13 @@ enum { RB_COLL_NONE = 0, RB_COLL_TREE = 1, RB_COLL_SWEEP = 2 };
  * or a velocity-dependent one): cfg.eps_restitution, or the power law
  * eps(v_n) = min(1, (|v_n| / v_c)^(-p)) of the normal approach speed. */
 enum { RB_EPS_CONSTANT = 0, RB_EPS_POWER = 1 };
+/* Order in which the walks and the collision search take their targets, 32
+ * per warp (a launch shape: results per target do not depend on it, except
+ * for the FP32 summation order of the walk): the Morton order of the tree;
+ * a 2D Hilbert order of (x, y) on a 1024 x 1024 grid of the root cube (thin
+ * sheets: a warp's targets then span a compact patch of the sheet); a 3D
+ * Hilbert order on a 128^3 grid.  The box comes first in every order. */
+enum { RB_TILE_MORTON = 0, RB_TILE_HILBERT_XY = 1, RB_TILE_HILBERT_XYZ = 2 };
 
 typedef struct rb_config {
     double G;               /* gravitational constant of Eq. 1 */
@@ -109,6 +116,7 @@ typedef struct rb_stats_t {
                                  entries and mixed-subtree iterations) */
     int64_t walk_group;       /* FP32 walk shape: 0 union walk, 4 group walk (4-lane subgroups
                                  for the mixed subtrees) */
+    int64_t tile_order;       /* order in which walks and search take their targets (RB_TILE_*) */
 } rb_stats_t;
 
 typedef struct rb_sim rb_sim; /* opaque, owned by the library */
@@ -212,9 +220,10 @@ int rb_stats(rb_sim* sim, rb_stats_t* out);
  * inside the step graph) so rb_stats reports per-stage device times. */
 int rb_set_profiling(rb_sim* sim, int on);
 /* Time the gravity walk and the tree collision search on the current
- * positions at 64, 128 and 256 threads per block and, for the plain FP32
- * walk, at each warp shape (walk_group 0 and 4; best of 3 after a warm-up
- * each) and keep the fastest; results are cached per (particle-count bucket,
+ * positions at 64, 128 and 256 threads per block, for the plain FP32 walk at
+ * each warp shape (walk_group 0 and 4), and under each tile order (with the
+ * cost of the sort that builds it); best of 3 after a warm-up each, and keep
+ * the fastest combination; results are cached per (particle-count bucket,
  * theta, walk mode, batched) for the process, and use_cache = 1 takes a
  * cached choice without timing.  Positions and velocities are not changed. */
 int rb_autotune(rb_sim* sim, int use_cache);
@@ -224,9 +233,11 @@ int rb_autotune(rb_sim* sim, int use_cache);
  * group walk, in which cells that all 32 targets of a warp provably accept
  * or open are decided once (Sect. 4.2 opening test against the bounding box
  * of the targets; accepted cells go to an interaction list staged in shared
- * memory) and the remaining subtrees are walked by subgroups of 4 lanes.  Results do not depend on them (each target's accepted cells
- * are those of its own walk).  Errors: RB_ERR_ARG for any other value. */
-int rb_set_launch_shape(rb_sim* sim, int walk_block, int search_block, int walk_group);
+ * memory) and the remaining subtrees are walked by subgroups of 4 lanes;
+ * tile_order one of RB_TILE_*.  Each target's accepted cells do not depend
+ * on them (each target runs its own walk).  Errors: RB_ERR_ARG for any
+ * other value. */
+int rb_set_launch_shape(rb_sim* sim, int walk_block, int search_block, int walk_group, int tile_order);
 /* Test particles (Sect. 4: particles that feel gravity without exerting it):
  * in every box, particles with id >= n_active keep their mass for collisions
  * and kinetic energy but are not sources of Eq. 1.  n_active < 0 (the

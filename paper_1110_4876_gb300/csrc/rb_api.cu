@@ -93,6 +93,7 @@ struct rb_sim {
     // launch shapes (threads per block) of the gravity walk and the search
     int walk_block = 128, search_block = 128;
     int walk_group = 0;   // FP32 walk: 0 union walk; 4 group walk (4-lane subgroups for mixed subtrees)
+    int tile_order = kTileMorton;   // order in which walks and search take targets (kTile*)
     bool tuned = false;
 };
 
@@ -262,6 +263,8 @@ int upload(rb_sim* s) {
         T.cap_n = cap;
         T.cap_e = ecap;
         rc |= dalloc(s, &T.key, cap, L); rc |= dalloc(s, &T.key_alt, cap, L);
+        rc |= dalloc(s, &T.tkey, cap, L); rc |= dalloc(s, &T.tkey_alt, cap, L);
+        rc |= dalloc(s, &T.tval, cap, L); rc |= dalloc(s, &T.tval_alt, cap, L);
         rc |= dalloc(s, &T.idx, cap, L); rc |= dalloc(s, &T.idx_alt, cap, L);
         rc |= dalloc(s, &T.sbox, cap, L);
         rc |= dalloc(s, &T.hist, radix_hist_words(cap), L);
@@ -428,6 +431,7 @@ int record_step(rb_sim* s, int p) {
         c = 1 - c;
         mark(s, 2);
         build_topology(s->T, s->P[c], s->ctl, s->d_boxes, s->C, st);
+        build_tile_order(s->T, s->P[c], s->ctl, s->tile_order, s->box_bits, st);
         mark(s, 3);
         build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st, true);
         mark(s, 4);
@@ -479,6 +483,7 @@ int record_step(rb_sim* s, int p) {
         c = 1 - c;
         mark(s, 7);
         build_topology(s->T, s->P[c], s->ctl, s->d_boxes, s->C, st);
+        build_tile_order(s->T, s->P[c], s->ctl, s->tile_order, s->box_bits, st);
         mark(s, 8);
         build_collision_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
         mark(s, 9);
@@ -587,6 +592,7 @@ int rebuild_now(rb_sim* s) {
     sort_and_permute(s->P[c], s->P[1 - c], s->T, s->PR, s->ctl, s->C, s->ncap, s->box_bits, s->stream);
     s->cur = 1 - c;
     build_topology(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->stream);
+    build_tile_order(s->T, s->P[s->cur], s->ctl, s->tile_order, s->box_bits, s->stream);
     return RB_OK;
 }
 
@@ -1085,6 +1091,7 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     out->walk_block = s->walk_block;
     out->search_block = s->search_block;
     out->walk_group = s->walk_group;
+    out->tile_order = s->tile_order;
     for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
     out->corrections = s->cfg.walk == RB_WALK_FP32_LEARNED ? c.req_count : 0;
     out->warp_iterations = (int64_t)c.n_iter;
@@ -1108,7 +1115,7 @@ struct TuneKey {
     }
 };
 struct TuneShape {
-    int walk_block, search_block, walk_group;
+    int walk_block, search_block, walk_group, tile_order;
 };
 std::map<TuneKey, TuneShape> g_tune_cache;
 std::mutex g_tune_mutex;
@@ -1153,83 +1160,111 @@ int rb_autotune(rb_sim* s, int use_cache) {
             s->walk_block = it->second.walk_block;
             s->search_block = it->second.search_block;
             s->walk_group = it->second.walk_group;
+            s->tile_order = it->second.tile_order;
             s->tuned = true;
             drop_graphs(s);
             return RB_OK;
         }
     }
     const int cand[3] = {64, 128, 256};
-    int wb = s->walk_block, sb = s->search_block, wg = s->walk_group;
-    if (s->cfg.gravity) {
-        rebuild_now(s);
-        const bool fp64 = s->cfg.walk == RB_WALK_FP64;
-        build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream, true);
-        const bool learned = s->cfg.walk == RB_WALK_FP32_LEARNED && s->mlp_loaded;
-        const WalkLearn L = learn_args(s);
-        // the plain FP32 walk also chooses its warp shape: the union walk
-        // over 32 targets, or the group walk with 4-lane subgroups
-        const bool grouped = !fp64 && !learned;
-        const int gcand[2] = {0, 4};
-        float best = 1e30f;
-        for (int b : cand)
-            for (int g : gcand) {
-                if (!grouped && g != gcand[0]) continue;
-                const float ms = time_best(s, [&] {
-                    gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C,
-                                 fp64 ? RB_WALK_FP64 : RB_WALK_FP32, 0, walk_out(s), false, false,
-                                 s->stream, nullptr, b, learned ? &L : nullptr, g);
+    int wb = s->walk_block, sb = s->search_block, wg = s->walk_group, to = s->tile_order;
+    const bool fp64 = s->cfg.walk == RB_WALK_FP64;
+    const bool learned = s->cfg.walk == RB_WALK_FP32_LEARNED && s->mlp_loaded;
+    const WalkLearn L = learn_args(s);
+    // the plain FP32 walk also chooses its warp shape: the union walk over 32
+    // targets, or the group walk with 4-lane subgroups
+    const bool grouped = !fp64 && !learned;
+    const int gcand[2] = {0, 4};
+    // every tile order is timed with the walk and the search it serves plus
+    // the sort that builds it; the smallest sum wins
+    const int ocand[3] = {kTileMorton, kTileHilbertXY, kTileHilbertXYZ};
+    float best_total = 1e30f;
+    for (int t : ocand) {
+        s->tile_order = t;
+        int wb_t = wb, sb_t = sb, wg_t = wg;
+        float total = 0.f;
+        if (s->cfg.gravity) {
+            rebuild_now(s);
+            if (t != kTileMorton)
+                total += time_best(s, [&] {
+                    build_tile_order(s->T, s->P[s->cur], s->ctl, t, s->box_bits, s->stream);
                 });
-                if (ms < best) { best = ms; wb = b; wg = grouped ? g : wg; }
+            build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, fp64, s->stream, true);
+            float best = 1e30f;
+            for (int b : cand)
+                for (int g : gcand) {
+                    if (!grouped && g != gcand[0]) continue;
+                    const float ms = time_best(s, [&] {
+                        gravity_walk(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C,
+                                     fp64 ? RB_WALK_FP64 : RB_WALK_FP32, 0, walk_out(s), false, false,
+                                     s->stream, nullptr, b, learned ? &L : nullptr, g);
+                    });
+                    if (ms < best) { best = ms; wb_t = b; wg_t = grouped ? g : wg; }
+                }
+            total += best;
+            s->acc_set = -1;   // the tuning walks left no consistent acceleration record
+        }
+        if (s->cfg.collisions == RB_COLL_TREE) {
+            // the records the step uses: boxes on the gravity tree, or Eq. 3's
+            // spheres on a collision tree when gravity is off
+            const bool aabb = s->cfg.gravity != 0;
+            rebuild_now(s);
+            if (!s->cfg.gravity && t != kTileMorton)
+                total += time_best(s, [&] {
+                    build_tile_order(s->T, s->P[s->cur], s->ctl, t, s->box_bits, s->stream);
+                });
+            if (aabb) {
+                build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, false, s->stream);
+                build_collision_aabb(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+            } else {
+                build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
             }
-        s->acc_set = -1;   // the tuning walks left no consistent acceleration record
-    }
-    if (s->cfg.collisions == RB_COLL_TREE) {
-        // the records the step uses: boxes on the gravity tree, or Eq. 3's
-        // spheres on a collision tree when gravity is off
-        const bool aabb = s->cfg.gravity != 0;
-        rebuild_now(s);
-        if (aabb) {
-            build_gravity_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, false, s->stream);
-            build_collision_aabb(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
-        } else {
-            build_collision_records(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->rmax, s->stream);
+            float best = 1e30f;
+            for (int b : cand) {
+                const float ms = time_best(s, [&] {
+                    cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream);
+                    collision_search(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->PR, 0, s->stream, b,
+                                     aabb, s->rmax);
+                });
+                if (ms < best) { best = ms; sb_t = b; }
+            }
+            total += best;
+            cudaMemsetAsync(&s->ctl->pair_n, 0, sizeof(int), s->stream);
         }
-        float best = 1e30f;
-        for (int b : cand) {
-            const float ms = time_best(s, [&] {
-                cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream);
-                collision_search(s->T, s->P[s->cur], s->ctl, s->d_boxes, s->C, s->PR, 0, s->stream, b,
-                                 aabb, s->rmax);
-            });
-            if (ms < best) { best = ms; sb = b; }
+        if (total < best_total) {
+            best_total = total;
+            wb = wb_t; sb = sb_t; wg = wg_t; to = t;
         }
-        cudaMemsetAsync(&s->ctl->pair_n, 0, sizeof(int), s->stream);
     }
     RB_CUDA(s, cudaStreamSynchronize(s->stream));
     RB_CUDA(s, cudaGetLastError());
     s->walk_block = wb;
     s->search_block = sb;
     s->walk_group = wg;
+    s->tile_order = to;
     s->tuned = true;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = {wb, sb, wg};
+        g_tune_cache[key] = {wb, sb, wg, to};
     }
     drop_graphs(s);
     return RB_OK;
 }
 
-int rb_set_launch_shape(rb_sim* s, int walk_block, int search_block, int walk_group) {
+int rb_set_launch_shape(rb_sim* s, int walk_block, int search_block, int walk_group, int tile_order) {
     if (!s) return fail(s, RB_ERR_ARG, "null sim");
     const bool ok = (walk_block == 64 || walk_block == 128 || walk_block == 256) &&
                     (search_block == 64 || search_block == 128 || search_block == 256) &&
-                    (walk_group == 0 || walk_group == 4);
+                    (walk_group == 0 || walk_group == 4) &&
+                    (tile_order == RB_TILE_MORTON || tile_order == RB_TILE_HILBERT_XY ||
+                     tile_order == RB_TILE_HILBERT_XYZ);
     if (!ok)
         return fail(s, RB_ERR_ARG,
-                    "launch shapes: 64, 128 or 256 threads per block; walk group 0 or 4");
+                    "launch shapes: 64, 128 or 256 threads per block; walk group 0 or 4; tile order 0, 1 or 2");
     s->walk_block = walk_block;
     s->search_block = search_block;
     s->walk_group = walk_group;
+    s->tile_order = tile_order;
     s->tuned = true;
     drop_graphs(s);
     return RB_OK;

@@ -132,7 +132,16 @@ struct Tree {
     int32_t* tq;                    // tile queues of the walks (kTileQStride ints each)
     int nq;                         // number of tile queues (one per SM)
     int cap_n, cap_e;
+    // Order in which the walks and the search take their targets, 32 per
+    // tile: nullptr = the Morton order of the slots; otherwise the slots
+    // sorted by a Hilbert key (built by build_tile_order for each tree).
+    uint64_t *tkey, *tkey_alt;
+    uint32_t *tval, *tval_alt;
+    const uint32_t* order = nullptr;
 };
+
+// Target orders of the walk and search tiles (the values of RB_TILE_*).
+enum { kTileMorton = 0, kTileHilbertXY = 1, kTileHilbertXYZ = 2 };
 
 // Pairs and their resolution.
 struct Pairs {
@@ -219,6 +228,11 @@ size_t scan_part_words(int ncap);
 // rb_tree.cu
 void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                     cudaStream_t s);
+// Tile order of the current tree (T.key sorted, P its particles): mode
+// kTileMorton leaves T.order null; kTileHilbertXY sorts the slots by a
+// 10-level 2D Hilbert key of (x, y) (thin sheets), kTileHilbertXYZ by a
+// 7-level 3D Hilbert key, the box id above either; ties keep Morton order.
+void build_tile_order(Tree& T, const PSet& P, Ctl* ctl, int mode, int box_bits, cudaStream_t s);
 // Moments and walk records.  fp64: FP64 records only (FP64 walk, potential);
 // otherwise FP64 and FP32 records, and with f32q the quadrupole is summed in
 // FP32 (the FP64 quadrupole records then hold its FP32 values).

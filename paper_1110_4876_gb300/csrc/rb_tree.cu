@@ -693,6 +693,91 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
     k_box_roots<<<ceil_div(C.nbox, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
 }
 
+namespace {
+
+// Hilbert index of (x, y) on a 2^lv grid (the classic quadrant rotation
+// walk, most significant level first).
+__device__ __forceinline__ uint32_t hilbert2(uint32_t x, uint32_t y, int lv) {
+    const uint32_t n = 1u << lv;
+    uint32_t d = 0;
+    for (uint32_t s = n >> 1; s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = n - 1 - x;
+                y = n - 1 - y;
+            }
+            const uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
+}
+
+// Hilbert index of (x, y, z) on a 2^lv grid: the axes are turned into the
+// curve's "transposed" form (Skilling 2004, AIP Conf. Proc. 707: inverse
+// undo of the excess work, then Gray decoding), whose bits interleaved
+// from the top give the index.
+__device__ __forceinline__ uint32_t hilbert3(uint32_t x, uint32_t y, uint32_t z, int lv) {
+    uint32_t c[3] = {x, y, z};
+    const uint32_t m = 1u << (lv - 1);
+    for (uint32_t q = m; q > 1; q >>= 1) {
+        const uint32_t p = q - 1;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (c[a] & q) {
+                c[0] ^= p;
+            } else {
+                const uint32_t t = (c[0] ^ c[a]) & p;
+                c[0] ^= t;
+                c[a] ^= t;
+            }
+        }
+    }
+    c[1] ^= c[0];
+    c[2] ^= c[1];
+    uint32_t t = 0;
+    for (uint32_t q = m; q > 1; q >>= 1)
+        if (c[2] & q) t ^= q - 1;
+    uint32_t d = 0;
+    for (int b = lv - 1; b >= 0; b--)
+#pragma unroll
+        for (int a = 0; a < 3; a++) d = (d << 1) | (((c[a] ^ t) >> b) & 1u);
+    return d;
+}
+
+// Tile keys of the sorted slots: the box above a Hilbert key of the slot's
+// integer coordinates (read back from its Morton key); value = the slot.
+__global__ void __launch_bounds__(256) k_tile_keys(const uint64_t* __restrict__ key,
+                                                   const int32_t* __restrict__ box,
+                                                   const Ctl* __restrict__ ctl, int ncap, int mode,
+                                                   uint64_t* __restrict__ tkey, uint32_t* __restrict__ tval) {
+    const int n = min(ctl->n_live, ncap);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = key[i];
+    const uint32_t ix = morton_compact3(k >> 2), iy = morton_compact3(k >> 1), iz = morton_compact3(k);
+    const uint32_t h = mode == kTileHilbertXY ? hilbert2(ix >> 11, iy >> 11, 10)
+                                              : hilbert3(ix >> 14, iy >> 14, iz >> 14, 7);
+    tkey[i] = ((uint64_t)(uint32_t)box[i] << 21) | (uint64_t)h;
+    tval[i] = (uint32_t)i;
+}
+
+}  // namespace
+
+void build_tile_order(Tree& T, const PSet& P, Ctl* ctl, int mode, int box_bits, cudaStream_t s) {
+    if (mode == kTileMorton || T.cap_n <= 0) {
+        T.order = nullptr;
+        return;
+    }
+    k_tile_keys<<<ceil_div(T.cap_n, 256), 256, 0, s>>>(T.key, P.box, ctl, T.cap_n, mode, T.tkey, T.tval);
+    const int which = radix_sort(T.tkey, T.tval, T.tkey_alt, T.tval_alt, T.cap_n, &ctl->n_live,
+                                 21 + box_bits, nullptr, 0, T.hist, s);
+    T.order = which ? T.tval_alt : T.tval;
+}
+
 void build_gravity_records(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
                            const SimC& C, bool fp64, cudaStream_t s, bool f32q) {
     const int n = T.cap_n;

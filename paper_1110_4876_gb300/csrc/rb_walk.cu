@@ -34,6 +34,7 @@ struct GravArgs {
     Rec4 ra, rb, rq0, rq1, rc_hi, rc_lo;
     const double4_32a *d_a, *d_q0, *d_q1, *d_c;
     const int32_t *e_skip, *leaf_of, *box_root;
+    const uint32_t* order;      // tile order of the targets (nullptr: Morton order of the slots)
     const int32_t* e_child;     // per cell entry: child entry of each octant (group walk)
     const uint32_t* e_cmask;    // per cell entry: octants holding a child (0: depth-21 group)
     const BoxP* boxes;
@@ -112,6 +113,11 @@ __device__ __forceinline__ int sm_queue(int nq) {
     unsigned sm;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
     return (int)(sm % (unsigned)nq);
+}
+
+// Slot of the k-th target in tile order.
+__device__ __forceinline__ int tile_slot(const uint32_t* order, int k) {
+    return order ? (int)__ldg(&order[k]) : k;
 }
 
 // The warp's next tile, or -1 when every queue is empty: its own SM's queue
@@ -239,9 +245,9 @@ template <bool kQuad, bool kInside, bool kPot, bool kSoft, bool kRecord, bool kL
 __device__ __forceinline__ void walk32(const GravArgs& A, LearnQ* LQ, const mlp::Packed* W, int wbase,
                                        int n) {
     const int lane = threadIdx.x & 31;
-    const int i = wbase + lane;
-    const bool valid = i < n;
-    const int ii = valid ? i : n - 1;
+    const bool valid = wbase + lane < n;
+    const int ii = tile_slot(A.order, valid ? wbase + lane : n - 1);
+    const int i = ii;   // the target's slot
     const int root = A.box_root[A.box[ii]];
     const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
     const int self_leaf = A.leaf_of[ii];
@@ -804,9 +810,9 @@ __device__ __forceinline__ void mixed_walks(const GravArgs& A, const int2* mix, 
 template <bool kQuad, bool kInside, bool kSoft, int kS>
 __device__ __forceinline__ void walk32g(const GravArgs& A, GroupSmem& G, int wbase, int n) {
     const int lane = threadIdx.x & 31;
-    const int i = wbase + lane;
-    const bool valid = i < n;
-    const int ii = valid ? i : n - 1;
+    const bool valid = wbase + lane < n;
+    const int ii = tile_slot(A.order, valid ? wbase + lane : n - 1);
+    const int i = ii;   // the target's slot
     const int box = A.box[ii];
     const int root = A.box_root[box];
     const int self_leaf = A.leaf_of[ii];
@@ -997,8 +1003,8 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 4) k_gwalk32(GravArgs A) {
     const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
     for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile)) {
         if (!kOne) {
-            const int i = (t << 5) + (threadIdx.x & 31);
-            const int b = A.box[i < n ? i : n - 1];
+            const int k = (t << 5) + (threadIdx.x & 31);
+            const int b = A.box[tile_slot(A.order, k < n ? k : n - 1)];
             if (!__all_sync(kFull, b == __shfl_sync(kFull, b, 0))) {
                 walk32<kQuad, kInside, false, kSoft, false, false, false>(A, nullptr, nullptr, t << 5, n);
                 continue;
@@ -1031,9 +1037,9 @@ __global__ void __launch_bounds__(kMaxWalkBlock, 2) k_walk32_learn(GravArgs A) {
 template <bool kQuad, bool kInside, bool kPot>
 __device__ __forceinline__ void walk64(const GravArgs& A, int wbase, int n) {
     const int lane = threadIdx.x & 31;
-    const int i = wbase + lane;
-    const bool valid = i < n;
-    const int ii = valid ? i : n - 1;
+    const bool valid = wbase + lane < n;
+    const int ii = tile_slot(A.order, valid ? wbase + lane : n - 1);
+    const int i = ii;   // the target's slot
     const double px = A.x[ii], py = A.y[ii], pz = A.z[ii];
     const int root = A.box_root[A.box[ii]];
     const int wend = root >= 0 ? A.e_skip[root] : 0;   // end of this box's tree
@@ -1160,6 +1166,7 @@ struct CollArgs {
     int nq;
     float rmaxf;         // largest radius, rounded up (box records)
     const int32_t* e_top;   // sphere records: largest particle slot below each cell
+    const uint32_t* order;  // tile order of the targets (nullptr: Morton order of the slots)
 };
 
 // Overlap test of Sect. 5.1 on the canonical orientation (a = lower id, b
@@ -1196,9 +1203,9 @@ __device__ __forceinline__ bool overlap64(double xa, double ya, double za, doubl
 template <bool kAABB>
 __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
     const int lane = threadIdx.x & 31;
-    const int i = wbase + lane;
-    const bool valid = i < n;
-    const int ii = valid ? i : n - 1;
+    const bool valid = wbase + lane < n;
+    const int ii = tile_slot(A.order, valid ? wbase + lane : n - 1);
+    const int i = ii;   // the target's slot
     const double px = A.x[ii], py = A.y[ii], pz = A.z[ii], pr = A.r[ii];
     const int pid = A.id[ii];
     const int root = A.box_root[A.box[ii]];
@@ -1451,6 +1458,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
     A.d_c = reinterpret_cast<const double4_32a*>(T.d_c);
     A.e_skip = T.e_skip; A.leaf_of = T.leaf_of; A.box_root = T.box_root;
     A.e_child = T.e_child; A.e_cmask = T.e_cmask;
+    A.order = T.order;
     A.boxes = boxes; A.ctl = ctl;
     A.out = out;
     if (!counts) { A.out.ncell = nullptr; A.out.nleaf = nullptr; A.out.nmac = nullptr; }
@@ -1533,6 +1541,7 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.x = P.x; A.y = P.y; A.z = P.z; A.r = P.r; A.id = P.id; A.box = P.box;
     A.ra = T.ra; A.rb = T.rb; A.box_root = T.box_root; A.e_skip = T.e_skip; A.boxes = boxes;
     A.e_top = T.e_top;
+    A.order = T.order;
     A.ctl = ctl;
     A.pair_key = PR.key; A.pair_cap = PR.cap; A.ncap = T.cap_n;
     A.ngx = C.ngx; A.ngy = C.ngy; A.ngz = C.ngz;

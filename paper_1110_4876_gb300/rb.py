@@ -21,6 +21,7 @@ RB_INT_LEAPFROG, RB_INT_SEI = 0, 1
 RB_WALK_FP64, RB_WALK_FP32, RB_WALK_FP32_LEARNED = 0, 1, 2
 RB_COLL_NONE, RB_COLL_TREE, RB_COLL_SWEEP = 0, 1, 2
 RB_EPS_CONSTANT, RB_EPS_POWER = 0, 1
+RB_TILE_MORTON, RB_TILE_HILBERT_XY, RB_TILE_HILBERT_XYZ = 0, 1, 2
 
 EXPORTS = [
     "rb_create", "rb_set_box", "rb_set_particles", "rb_step", "rb_get_particles", "rb_energy",
@@ -62,6 +63,7 @@ class rb_stats_t(C.Structure):
         ("kernels_per_step", C.c_int64), ("walk_block", C.c_int64), ("search_block", C.c_int64),
         ("t", C.c_double), ("ms_last_step", C.c_double), ("ms_stage", C.c_double * 12),
         ("corrections", C.c_int64), ("warp_iterations", C.c_int64), ("walk_group", C.c_int64),
+        ("tile_order", C.c_int64),
     ]
 
 
@@ -103,7 +105,7 @@ def load():
     lib.rb_stats.argtypes = [_P, C.POINTER(rb_stats_t)]
     lib.rb_set_profiling.argtypes = [_P, i32]
     lib.rb_autotune.argtypes = [_P, i32]
-    lib.rb_set_launch_shape.argtypes = [_P, i32, i32, i32]
+    lib.rb_set_launch_shape.argtypes = [_P, i32, i32, i32, i32]
     lib.rb_set_n_active.argtypes = [_P, C.c_int64]
     lib.rb_set_restitution.argtypes = [_P, i32, C.c_double, C.c_double]
     lib.rb_set_pair_capacity.argtypes = [_P, i64]
@@ -317,10 +319,10 @@ def rb_set_profiling(sim, on: bool = True):
 
 def rb_autotune(sim, use_cache: bool = True):
     """Pick the walk/search launch shapes by timing them; returns the choice
-    (walk block, search block, walk group)."""
+    (walk block, search block, walk group, tile order)."""
     _check(load().rb_autotune(sim, 1 if use_cache else 0), sim)
     st = rb_stats(sim)
-    return int(st["walk_block"]), int(st["search_block"]), int(st["walk_group"])
+    return int(st["walk_block"]), int(st["search_block"]), int(st["walk_group"]), int(st["tile_order"])
 
 
 def rb_set_n_active(sim, n_active: int):
@@ -333,10 +335,13 @@ def rb_set_restitution(sim, law: int, v_c: float = 1.0, p: float = 0.0):
     _check(load().rb_set_restitution(sim, int(law), float(v_c), float(p)), sim)
 
 
-def rb_set_launch_shape(sim, walk_block: int, search_block: int, walk_group: int = 0):
+def rb_set_launch_shape(sim, walk_block: int, search_block: int, walk_group: int = 0,
+                        tile_order: int = 0):
     """Threads per block of the walk and of the collision search (64, 128,
-    256) and the FP32 walk's warp shape (0 union walk, 4 group walk)."""
-    _check(load().rb_set_launch_shape(sim, int(walk_block), int(search_block), int(walk_group)), sim)
+    256), the FP32 walk's warp shape (0 union walk, 4 group walk) and the
+    tile order of the targets (RB_TILE_*)."""
+    _check(load().rb_set_launch_shape(sim, int(walk_block), int(search_block), int(walk_group),
+                                      int(tile_order)), sim)
 
 
 def rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z, out,

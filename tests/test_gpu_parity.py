@@ -85,15 +85,16 @@ def test_fp64_walk_matches_oracle_tree(rb, orc, theta):
     np.testing.assert_array_equal(nl, rl)
 
 
-@pytest.mark.parametrize("group", [0, 4])
+@pytest.mark.parametrize("group,order", [(0, 0), (4, 0), (0, 1), (4, 2)])
 @pytest.mark.parametrize("theta,quad", [(0.5, 1), (0.5, 0), (0.3, 1)])
-def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad, group):
-    """Both warp shapes of the FP32 walk: the union walk and the group walk
-    (group decisions, staged interaction list, 4-lane mixed subtrees)."""
+def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad, group, order):
+    """Both warp shapes of the FP32 walk (the union walk and the group walk:
+    group decisions, staged interaction list, 4-lane mixed subtrees) and the
+    tile orders of the targets (Morton, 2D and 3D Hilbert)."""
     L, N = 160.0, 6000
     P = I.sheet(L, N, 7)
     sim = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP32, theta=theta, quadrupole=quad))
-    rb.rb_set_launch_shape(sim.h, 128, 128, group)
+    rb.rb_set_launch_shape(sim.h, 128, 128, group, order)
     sim.set_particles(P)
     a, (nc, nl, nm) = sim.gravity(counts=True)
     p = sheet_params(orc, L, theta, quadrupole=quad)
@@ -109,8 +110,8 @@ def test_fp32_walk_matches_oracle_tree(rb, orc, theta, quad, group):
     assert sim.stats()["fp64_rechecks"] > 0
 
 
-@pytest.mark.parametrize("walk,group", [(0, 0), (1, 0), (1, 4)])
-def test_plummer_open_inside_rule(rb, orc, walk, group):
+@pytest.mark.parametrize("walk,group,order", [(0, 0, 0), (1, 0, 0), (1, 4, 0), (1, 0, 2), (0, 0, 2)])
+def test_plummer_open_inside_rule(rb, orc, walk, group, order):
     """theta = 0.7 > 1/sqrt(3): the target-inside-cell rule is active (the
     group walk must also keep its group decisions clear of the cell cube)."""
     N = 5000
@@ -118,7 +119,7 @@ def test_plummer_open_inside_rule(rb, orc, walk, group):
     cfg = dict(G=1.0, box=(128.0,) * 3, boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG,
                theta=0.7, softening=1e-3, dt=1e-3, gravity=1, collisions=0, walk=walk)
     sim = rb.Sim(**cfg)
-    rb.rb_set_launch_shape(sim.h, 128, 128, group)
+    rb.rb_set_launch_shape(sim.h, 128, 128, group, order)
     sim.set_particles(P)
     a, (nc, nl, nm) = sim.gravity(counts=True)
     p = orc.Params(G=1.0, L=(128.0,) * 3, theta=0.7, soft=1e-3, dt=1e-3, gravity=1)

@@ -1,7 +1,8 @@
 """The autotuner picks the walk/search launch shapes by timing them.  The
 block sizes do not change any result; the FP32 walk's warp shape (union walk
-or group walk with 4-lane subgroups) changes only the order in which
-each target's FP32 terms are summed: its accepted cells and particle terms
+or group walk with 4-lane subgroups) and the tile order of the targets
+(Morton, 2D or 3D Hilbert) change only the order in which each target's
+FP32 terms are summed: its accepted cells and particle terms
 are the same (counts equal), and forces agree to FP32 rounding: each shape is
 within 1e-5 of the FP64 tree (the parity tests), so two shapes are within
 2e-5 of each other (per-particle denominator floored at 1e-3 of the rms)."""
@@ -31,8 +32,8 @@ def test_autotune_keeps_results():
     a.set_particles(P)
     acc0, cnt0 = a.gravity(counts=True)
     pairs0 = a.pairs()
-    wb, sb, wg = rb.rb_autotune(a.h, use_cache=False)
-    assert wb in (64, 128, 256) and sb in (64, 128, 256) and wg in (0, 4)
+    wb, sb, wg, to = rb.rb_autotune(a.h, use_cache=False)
+    assert wb in (64, 128, 256) and sb in (64, 128, 256) and wg in (0, 4) and to in (0, 1, 2)
     acc1, cnt1 = a.gravity(counts=True)
     assert _rel(acc1, acc0) <= 2e-5
     for c0, c1 in zip(cnt0[:2], cnt1[:2]):
@@ -41,7 +42,7 @@ def test_autotune_keeps_results():
     # a second simulation of the same kind takes the cached choice
     b = rb.Sim(**cfg)
     b.set_particles(P)
-    assert rb.rb_autotune(b.h, use_cache=True) == (wb, sb, wg)
+    assert rb.rb_autotune(b.h, use_cache=True) == (wb, sb, wg, to)
     a.step(2)
     b.step(2)
     pa, pb = a.particles(), b.particles()
@@ -63,23 +64,28 @@ def test_every_launch_shape_gives_the_same_forces_and_pairs(theta):
     sim = rb.Sim(**cfg)
     sim.set_particles(P)
     ref_a, ref_c, ref_p = None, None, None
-    for wg in (0, 4):
-        shape_a = None
-        for wb in (64, 128, 256):
-            for sb in (64, 128, 256):
-                rb.rb_set_launch_shape(sim.h, wb, sb, wg)
-                acc, cnt = sim.gravity(counts=True)
-                pairs = rb.pair_keys(*sim.pairs())
-                if ref_a is None:
-                    ref_a, ref_c, ref_p = acc, cnt, pairs
-                if shape_a is None:
-                    shape_a = acc
-                assert np.array_equal(acc, shape_a), (wg, wb, sb)
-                assert _rel(acc, ref_a) <= 2e-5, (wg, wb, sb)
-                for c, r in zip(cnt, ref_c):
-                    np.testing.assert_array_equal(c, r)
-                assert np.array_equal(pairs, ref_p), (wg, wb, sb)
+    for to in (rb.RB_TILE_MORTON, rb.RB_TILE_HILBERT_XY, rb.RB_TILE_HILBERT_XYZ):
+        for wg in (0, 4):
+            shape_a = None
+            for wb in (64, 128, 256):
+                for sb in (64, 128, 256):
+                    rb.rb_set_launch_shape(sim.h, wb, sb, wg, to)
+                    acc, cnt = sim.gravity(counts=True)
+                    pairs = rb.pair_keys(*sim.pairs())
+                    if ref_a is None:
+                        ref_a, ref_c, ref_p = acc, cnt, pairs
+                    if shape_a is None:
+                        shape_a = acc
+                    # block sizes: bit for bit; warp shapes and tile orders:
+                    # the same terms summed in another FP32 order
+                    assert np.array_equal(acc, shape_a), (to, wg, wb, sb)
+                    assert _rel(acc, ref_a) <= 2e-5, (to, wg, wb, sb)
+                    for c, r in zip(cnt, ref_c):
+                        np.testing.assert_array_equal(c, r)
+                    assert np.array_equal(pairs, ref_p), (to, wg, wb, sb)
     with pytest.raises(rb.RbError):
-        rb.rb_set_launch_shape(sim.h, 96, 128, 8)
+        rb.rb_set_launch_shape(sim.h, 96, 128, 0)
     with pytest.raises(rb.RbError):
         rb.rb_set_launch_shape(sim.h, 128, 128, 8)
+    with pytest.raises(rb.RbError):
+        rb.rb_set_launch_shape(sim.h, 128, 128, 0, 3)
