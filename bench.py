@@ -209,7 +209,11 @@ def run_ours(args):
     P = I.sheet(L_SHEET, N_SHEET, SEED + rank)
     sim = make_sim(rb, cfg, stream.cuda_stream)
     sim.set_particles(P)
-    tuned = rb.rb_autotune(sim.h)
+    if args.shape:
+        rb.rb_set_launch_shape(sim.h, *args.shape)
+        tuned = tuple(args.shape)
+    else:
+        tuned = rb.rb_autotune(sim.h)
     rb.rb_set_profiling(sim.h, True)
     clk = Clocks(local).__enter__()   # sampling from before the warm-up
     sim.step(args.warmup)
@@ -263,6 +267,7 @@ def run_ours(args):
         bufs[0][k][:] = a
     sim_e = make_sim(rb, cfg, stream.cuda_stream)
     sim_e.set_particles(tuple(bufs[0][k] for k in fields))
+    rb.rb_set_launch_shape(sim_e.h, *tuned)   # the launch shapes chosen above
     sim_e.step(1)  # capture the step graphs outside the timed region
     sim_e.particles(out=bufs[1])
     barrier()
@@ -331,7 +336,7 @@ def run_ours(args):
                    "pairs_per_step": statistics.mean(pairs),
                    "walk_block, search_block, walk_group, tile_order": list(tuned)},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-        "roofline_build": build_roofline(stage_sum, args.steps, cells, peaks),
+        "roofline_build": build_roofline(stage_sum, args.steps, cells, peaks, tuned[3]),
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
     }
     if args.cpu_baseline and world == 1:
@@ -378,24 +383,30 @@ def profiled_traffic(summary: str, sources, field: str = "dram_bytes_per_launch"
     return float(fields[field]), f"ncu capture in profiles/{summary} (sources {now})"
 
 
-def build_roofline(stage_sum, steps, cells, peaks):
-    """HBM roofline of the tree build (sort + gather, topology, moments) from
-    the event-timed stages: algorithmic bytes per step / stage time."""
+def build_roofline(stage_sum, steps, cells, peaks, tile_order=0):
+    """HBM roofline of the tree build (sort + gather, topology, tile order,
+    moments) from the event-timed stages: algorithmic bytes per step / stage
+    time."""
     n = N_SHEET
     ncells = statistics.mean(cells) if cells else 0.0
     per_particle = BUILD_PASSES * BYTES_PASS + BYTES_GATHER + BYTES_KEYS
+    if tile_order:
+        # Hilbert tile keys: read the Morton key (8 B), write key and slot
+        # (12 B), then 3 radix passes of 24 B
+        per_particle += 20 + 3 * BYTES_PASS
     nbytes = n * per_particle + ncells * BYTES_CELL
     ms = sum(stage_sum.get(k, 0.0) for k in ("sort_gather", "tree", "moments")) / steps
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
     traffic, note = profiled_traffic("tree_build_sheet1m.md", BUILD_SOURCES, "dram_bytes_per_build")
     return {"bound": "hbm", "kernels": "k_rs_up/k_digit_rows/k_rs_down (8 passes), k_permute, topology, "
-                                       "k_moments_level (per depth)",
+                                       "tile order (k_tile_keys + 3 passes), k_moments_level (per depth)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None, "traffic": traffic, "traffic_source": note,
             "bytes_per_step": nbytes, "ms_per_step": ms, "cells_per_particle": ncells / n,
             "bytes_model": f"{BUILD_PASSES} radix passes x {BYTES_PASS} B + gather {BYTES_GATHER} B + "
-                           f"keys {BYTES_KEYS} B per particle + {BYTES_CELL} B per cell",
+                           f"keys {BYTES_KEYS} B per particle + {BYTES_CELL} B per cell"
+                           + (" + tile order 92 B per particle" if tile_order else ""),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
 
 
@@ -1000,6 +1011,9 @@ def main():
     ap.add_argument("--walk", choices=["fp32", "fp64", "learned"], default="fp32",
                     help="fp32 / fp64 walk at theta 0.5, or the learned correction at theta 0.8")
     ap.add_argument("--cpu-samples", type=int, default=16384)
+    ap.add_argument("--shape", type=lambda v: [int(x) for x in v.split(",")], default=None,
+                    help="walk block, search block, walk group, tile order (default: autotuned); "
+                         "fixes the kernels a profiler captures")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--particles", type=int, default=N_SHEET,
                     help="sheet size (default 1M; smaller sizes are for profiling only)")
