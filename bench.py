@@ -568,13 +568,14 @@ def run_ensemble(args):
 
 
 def _timed(sim, stream, steps, warmup):
-    """ms per step (CUDA events on the library's stream) and the gravity walk
-    stage's ms per step, after warm-up and autotuning."""
+    """ms per step (CUDA events on the library's stream), the gravity walk
+    stage's ms per step, after warm-up and autotuning, and the launch shape
+    the autotuner chose (walk block, search block, walk group, tile order)."""
     import torch
 
     from paper_1110_4876_gb300 import rb
 
-    rb.rb_autotune(sim.h)
+    shape = rb.rb_autotune(sim.h)
     rb.rb_set_profiling(sim.h, True)
     sim.step(warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -586,7 +587,7 @@ def _timed(sim, stream, steps, warmup):
         walk += sim.stats()["ms_stage"]["gravity_walk"]
     e1.record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps, walk / steps
+    return e0.elapsed_time(e1) / steps, walk / steps, list(shape)
 
 
 def _errors(a, a_ref):
@@ -628,9 +629,9 @@ def run_compare(args):
         a = sim.gravity()
         err = _errors(a[sel], a_dir)
         sim.set_particles(P)
-        ms, wms = _timed(sim, stream, args.steps, args.warmup)
+        ms, wms, shape = _timed(sim, stream, args.steps, args.warmup)
         rows[name] = {"particle_steps_per_s": N_SHEET / (ms / 1e3), "ms_per_step": ms,
-                      "walk_ms": wms, "force_error_vs_direct": err}
+                      "walk_ms": wms, "force_error_vs_direct": err, "launch_shape": shape}
         del sim
     clk.window(t_clk, time.time())
     clk.__exit__()
@@ -675,9 +676,10 @@ def run_plummer(args):
             a = sim.gravity()
             err = _errors(a[sel], a_dir)
             sim.set_particles(P)
-            ms, wms = _timed(sim, stream, args.steps, args.warmup)
+            ms, wms, shape = _timed(sim, stream, args.steps, args.warmup)
             rows[f"{walk} theta={theta}"] = {"particle_steps_per_s": n / (ms / 1e3), "ms_per_step": ms,
-                                             "walk_ms": wms, "force_error_vs_direct": err}
+                                             "walk_ms": wms, "force_error_vs_direct": err,
+                                             "launch_shape": shape}
             del sim
     clk.window(t_clk, time.time())
     clk.__exit__()
@@ -927,9 +929,10 @@ def run_learned_sweep(args):
             err = _errors(a[sel], a_dir)
             corr = sim.stats()["corrections"]
             sim.set_particles(P)
-            ms, wms = _timed(sim, stream, args.steps, args.warmup)
+            ms, wms, shape = _timed(sim, stream, args.steps, args.warmup)
             forms[form].append({"theta": theta, "particle_steps_per_s": N_SHEET / (ms / 1e3),
                                 "ms_per_step": ms, "walk_ms": wms, "force_error_vs_direct": err,
+                                "launch_shape": shape,
                                 "corrected_cells_per_particle": corr / N_SHEET if form == "learned" else 0})
             del sim
     target = forms["plain"][0]["force_error_vs_direct"]["e_sum"]
