@@ -558,6 +558,8 @@ int collide_with_retry(rb_sim* s, int c, int hs, bool resolve, bool aabb) {
         if (s->hctl.err & kErrSweepLong)
             return fail(s, RB_ERR_CAPACITY, "plane sweep: a trajectory overlaps more than 65536 others in x "
                                             "(use the tree detector)");
+        if (s->hctl.err & kErrSortStall)
+            return fail(s, RB_ERR_TIMEOUT, "radix sort: a bounded look-back wait gave up");
         if (s->hctl.pair_count <= s->PR.cap) {
             if (resolve) {
                 resolve_pairs(s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->T.img, s->stream);
@@ -618,6 +620,8 @@ int gravity_now(rb_sim* s, bool potential) {
     if (int rc = read_ctl(s)) return rc;
     if (s->hctl.err & kErrWalk)
         return fail(s, RB_ERR_STATE, "gravity walk: an entry index outside the tree (malformed tree)");
+    if (s->hctl.err & kErrSortStall)
+        return fail(s, RB_ERR_TIMEOUT, "radix sort: a bounded look-back wait gave up");
     return RB_OK;
 }
 
@@ -753,6 +757,7 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
     }
     s->nsm = walk_prepare();
     resolve_prepare(s->nsm);
+    radix_prepare(s->nsm);
     cudaEventCreate(&s->ev0);
     cudaEventCreate(&s->ev1);
     for (auto& ev : s->ev_stage) cudaEventCreate(&ev);
@@ -863,6 +868,8 @@ int rb_step(rb_sim* s, int64_t nsteps) {
                                             "(use the tree detector)");
         if (s->hctl.err & kErrResolveStall)
             return fail(s, RB_ERR_TIMEOUT, "collision resolution: a bounded wait for the ready queue gave up");
+        if (s->hctl.err & kErrSortStall)
+            return fail(s, RB_ERR_TIMEOUT, "radix sort: a bounded look-back wait gave up");
         if (s->cfg.collisions && s->hctl.pair_count > s->PR.cap) {
             // the step ended before resolution: search again with a larger buffer
             const bool aabb = s->cfg.gravity && s->cfg.collisions == RB_COLL_TREE;

@@ -83,6 +83,7 @@ constexpr int kErrPairOverflow = 2;
 constexpr int kErrSweepLong = 4;    // a plane-sweep item met more than kMaxSweepScan extents
 constexpr int kErrResolveStall = 8; // the resolution queue stopped filling (bounded wait gave up)
 constexpr int kErrWalk = 16;        // a walk met an entry index outside the tree (malformed tree)
+constexpr int kErrSortStall = 32;   // a radix pass's look-back stopped advancing (bounded wait gave up)
 constexpr int kMaxSweepScan = 1 << 16;
 
 // One ghost image of one box at the time of a walk or search (Sect. 2.3):
@@ -216,11 +217,16 @@ int radix_sort_passes(int key_bits, bool box_pass, int box_bits);
 // Sorts (key, val) pairs stably by key bits [0, key_bits) and then, when
 // box_digits is non-null, by box_digits[val] (bits [0, box_bits)).
 // Ping-pongs between the two buffers; returns 0 if the result is in
-// (k0, v0) and 1 if it is in (k1, v1).
+// (k0, v0) and 1 if it is in (k1, v1).  hist holds radix_hist_words(ncap)
+// words; ncap < 2^30.  A look-back wait that gives up sets kErrSortStall in
+// *err (device memory).
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap, const int* d_n,
-               int key_bits, const int32_t* box_digits, int box_bits, uint32_t* hist,
+               int key_bits, const int32_t* box_digits, int box_bits, uint32_t* hist, int* err,
                cudaStream_t s);
 size_t radix_hist_words(int ncap);
+// Queries the resident blocks of a radix pass once (outside any stream
+// capture); a grid that fits needs no tile tickets.
+void radix_prepare(int nsm);
 void exclusive_scan_i32(int32_t* data, int n_cap, const int* d_n, int32_t* part, int32_t* total,
                         cudaStream_t s);
 size_t scan_part_words(int ncap);

@@ -519,7 +519,7 @@ void sort_and_permute(const PSet& src, const PSet& dst, Tree& T, Pairs& PR, Ctl*
                       const SimC& C, int ncap, int box_bits, cudaStream_t s) {
     if (ncap <= 0) return;
     const int which = radix_sort(T.key, T.idx, T.key_alt, T.idx_alt, ncap, nullptr, 64,
-                                 C.nbox > 1 ? T.sbox : nullptr, box_bits, T.hist, s);
+                                 C.nbox > 1 ? T.sbox : nullptr, box_bits, T.hist, &ctl->err, s);
     if (which == 1) {
         // keep the sorted keys in T.key for the topology kernels
         uint64_t* k = T.key; T.key = T.key_alt; T.key_alt = k;
@@ -605,7 +605,7 @@ void sort_pairs(Pairs& PR, Ctl* ctl, cudaStream_t s, int key_bits) {
     // an odd number of passes leaves the keys in key_alt; the buffers are
     // not swapped, so every captured graph finds them in the same place
     PR.sorted_alt = radix_sort(PR.key, PR.val, PR.key_alt, PR.val_alt, PR.cap, &ctl->pair_n,
-                               key_bits, nullptr, 0, PR.hist, s) == 1;
+                               key_bits, nullptr, 0, PR.hist, &ctl->err, s) == 1;
 }
 
 void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pairs& PR,
@@ -622,7 +622,7 @@ void resolve_pairs(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Pa
     k_pair_ends<<<grid, 256, 0, s>>>(A, PR.ekey, PR.eval);
     // particle slots are < 2^24: three 8-bit passes, stable in queue order
     const int which = radix_sort(PR.ekey, PR.eval, PR.ekey_alt, PR.eval_alt, 2 * PR.cap,
-                                 &ctl->pair_ends, 24, nullptr, 0, PR.ehist, s);
+                                 &ctl->pair_ends, 24, nullptr, 0, PR.ehist, &ctl->err, s);
     k_pair_prev<<<2 * grid, 256, 0, s>>>(which ? PR.ekey_alt : PR.ekey,
                                          which ? PR.eval_alt : PR.eval, ctl, PR.prev_a, PR.prev_b,
                                          PR.next_a, PR.next_b);

@@ -257,7 +257,7 @@ void sweep_search(const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C, Swe
     k_sweep_items<<<ceil_div(ncap, 256), 256, 0, s>>>(A);
     const int key_bits = 32 + S.box_bits;
     const int which = radix_sort(S.key, S.val, S.key_alt, S.val_alt, S.cap, &ctl->sweep_items, key_bits,
-                                 nullptr, 0, S.hist, s);
+                                 nullptr, 0, S.hist, &ctl->err, s);
     if (which == 1) {
         A.key = S.key_alt;
         A.val = S.val_alt;

@@ -774,7 +774,7 @@ void build_tile_order(Tree& T, const PSet& P, Ctl* ctl, int mode, int box_bits, 
     }
     k_tile_keys<<<ceil_div(T.cap_n, 256), 256, 0, s>>>(T.key, P.box, ctl, T.cap_n, mode, T.tkey, T.tval);
     const int which = radix_sort(T.tkey, T.tval, T.tkey_alt, T.tval_alt, T.cap_n, &ctl->n_live,
-                                 21 + box_bits, nullptr, 0, T.hist, s);
+                                 21 + box_bits, nullptr, 0, T.hist, &ctl->err, s);
     T.order = which ? T.tval_alt : T.tval;
 }
 
