@@ -45,6 +45,7 @@ FP32_LANES_PER_SM = 128
 # once; each tree cell writes ~160 B of FP64 and FP32 records
 BUILD_PASSES = 8
 BYTES_PASS, BYTES_GATHER, BYTES_KEYS, BYTES_CELL = 24, 148, 8, 160
+BYTES_DIGITS = 8   # one read of the keys counts the digits of every pass
 # algorithmic FP32 flops per interaction (FMA = 2, add/mul = 1, rsqrt = 0)
 FLOP_CELL, FLOP_LEAF, FLOP_MAC = 60, 20, 10
 FLOP_MLP = 2 * (12 * 64 + 2 * 64 * 64 + 64 * 3)
@@ -389,24 +390,24 @@ def build_roofline(stage_sum, steps, cells, peaks, tile_order=0):
     time."""
     n = N_SHEET
     ncells = statistics.mean(cells) if cells else 0.0
-    per_particle = BUILD_PASSES * BYTES_PASS + BYTES_GATHER + BYTES_KEYS
+    per_particle = BYTES_DIGITS + BUILD_PASSES * BYTES_PASS + BYTES_GATHER + BYTES_KEYS
     if tile_order:
         # Hilbert tile keys: read the Morton key (8 B), write key and slot
-        # (12 B), then 3 radix passes of 24 B
-        per_particle += 20 + 3 * BYTES_PASS
+        # (12 B), then the digit counts and 3 radix passes of 24 B
+        per_particle += 20 + BYTES_DIGITS + 3 * BYTES_PASS
     nbytes = n * per_particle + ncells * BYTES_CELL
     ms = sum(stage_sum.get(k, 0.0) for k in ("sort_gather", "tree", "moments")) / steps
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
     traffic, note = profiled_traffic("tree_build_sheet1m.md", BUILD_SOURCES, "dram_bytes_per_build")
-    return {"bound": "hbm", "kernels": "k_rs_up/k_digit_rows/k_rs_down (8 passes), k_permute, topology, "
-                                       "tile order (k_tile_keys + 3 passes), k_moments_level (per depth)",
+    return {"bound": "hbm", "kernels": "k_rs_hist + k_rs_pass (8 passes), k_permute, topology, "
+                                       "tile order (k_tile_keys, k_rs_hist + 3 passes), k_moments_level (per depth)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None, "traffic": traffic, "traffic_source": note,
             "bytes_per_step": nbytes, "ms_per_step": ms, "cells_per_particle": ncells / n,
-            "bytes_model": f"{BUILD_PASSES} radix passes x {BYTES_PASS} B + gather {BYTES_GATHER} B + "
-                           f"keys {BYTES_KEYS} B per particle + {BYTES_CELL} B per cell"
-                           + (" + tile order 92 B per particle" if tile_order else ""),
+            "bytes_model": f"digit counts {BYTES_DIGITS} B + {BUILD_PASSES} radix passes x {BYTES_PASS} B + "
+                           f"gather {BYTES_GATHER} B + keys {BYTES_KEYS} B per particle + {BYTES_CELL} B per cell"
+                           + (" + tile order 100 B per particle" if tile_order else ""),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
 
 
