@@ -331,8 +331,23 @@ int rb_energy_sums_noalloc(int64_t n, const double* m, const double* x, const do
                            const double* vx, const double* vy, const double* vz,
                            const double* phi, int integrator, double omega, double omega_z,
                            double* out, void* cuda_stream);
+/* The sort that puts particles in Morton order before every tree build (it
+ * replaces the tree reconstruction of Sect. 4.2), the collision queue in
+ * canonical pair order (Sect. 5) and the pair ends of the resolution, run on
+ * host arrays: a stable LSD radix sort of (key, value) pairs by key bits
+ * [0, key_bits), 8-bit digits.  keys / vals: host arrays of n entries, sorted
+ * in place (vals may be NULL).  cap >= n sizes the device buffers while the
+ * count n is read on the device, as the step's sorts of pairs run; cap < 2^30.
+ * key_bits in [1, 64].  cuda_stream: the stream to run on (NULL: the default
+ * stream); the call returns when the result is on the host.  It allocates and
+ * frees its own device buffers.  Errors: RB_ERR_ARG (bad sizes or key_bits, a
+ * missing array), RB_ERR_CUDA, RB_ERR_TIMEOUT (a bounded wait between blocks
+ * of a pass gave up), with a message in rb_last_error(NULL). */
+int rb_sort_pairs_u64(int64_t n, int64_t cap, int key_bits, uint64_t* keys, uint32_t* vals,
+                      void* cuda_stream);
 /* Description of the last error of `sim`, or with sim NULL of the last
- * failed rb_create or rb_energy_sums_noalloc on the calling thread (that
+ * failed rb_create, rb_energy_sums_noalloc or rb_sort_pairs_u64 on the
+ * calling thread (that
  * message is kept per host thread, so threads that fail at the same time do
  * not overwrite each other's).  Storage owned by the library, valid until the
  * next failing call of the same simulation or thread. */

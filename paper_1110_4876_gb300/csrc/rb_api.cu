@@ -1636,4 +1636,58 @@ int rb_mlp_train(const float* X, const float* Y, int64_t n, int epochs, int batc
     return RB_OK;
 }
 
+int rb_sort_pairs_u64(int64_t n, int64_t cap, int key_bits, uint64_t* keys, uint32_t* vals,
+                      void* cuda_stream) {
+    if (n < 0 || cap < n || cap >= (int64_t(1) << 30) || key_bits < 1 || key_bits > 64 ||
+        (n > 0 && !keys)) {
+        set_global_error("rb_sort_pairs_u64: bad n, cap or key_bits, or keys missing");
+        return RB_ERR_ARG;
+    }
+    if (cap == 0) return RB_OK;
+    const int nsm = walk_prepare();
+    radix_prepare(nsm);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int ncap = (int)cap;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr;
+    int* dn = nullptr;   // [0]: count, [1]: error bits
+    auto cleanup = [&]() {
+        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(dn);
+    };
+    auto cuda_fail = [&](cudaError_t e) {
+        set_global_error(std::string("rb_sort_pairs_u64: ") + cudaGetErrorString(e));
+        cleanup();
+        return RB_ERR_CUDA;
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&k0, sizeof(uint64_t) * cap)) || (e = cudaMalloc(&k1, sizeof(uint64_t) * cap)) ||
+        (e = cudaMalloc(&v0, sizeof(uint32_t) * cap)) || (e = cudaMalloc(&v1, sizeof(uint32_t) * cap)) ||
+        (e = cudaMalloc(&hist, sizeof(uint32_t) * radix_hist_words(ncap))) ||
+        (e = cudaMalloc(&dn, 2 * sizeof(int))))
+        return cuda_fail(e);
+    const int hn[2] = {(int)n, 0};
+    if ((e = cudaMemcpyAsync(dn, hn, sizeof(hn), cudaMemcpyHostToDevice, st)) ||
+        (n > 0 && (e = cudaMemcpyAsync(k0, keys, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st))))
+        return cuda_fail(e);
+    if (n > 0 && vals && (e = cudaMemcpyAsync(v0, vals, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st)))
+        return cuda_fail(e);
+    cudaGetLastError();
+    const int which = radix_sort(k0, v0, k1, v1, ncap, dn, key_bits, nullptr, 0, hist, dn + 1, st);
+    if ((e = cudaGetLastError())) return cuda_fail(e);
+    int herr[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(herr, dn, sizeof(herr), cudaMemcpyDeviceToHost, st)) ||
+        (n > 0 && (e = cudaMemcpyAsync(keys, which ? k1 : k0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, st))))
+        return cuda_fail(e);
+    if (n > 0 && vals &&
+        (e = cudaMemcpyAsync(vals, which ? v1 : v0, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st)))
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(st))) return cuda_fail(e);
+    cleanup();
+    if (herr[1] & kErrSortStall) {
+        set_global_error("rb_sort_pairs_u64: a bounded look-back wait gave up");
+        return RB_ERR_TIMEOUT;
+    }
+    return RB_OK;
+}
+
 }  // extern "C"

@@ -31,6 +31,7 @@ EXPORTS = [
     "rb_set_profiling", "rb_destroy", "rb_last_error", "rb_energy_sums_noalloc",
     "rb_load_mlp", "rb_mlp_samples", "rb_mlp_train", "rb_mlp_grad", "rb_mlp_grad_fp32", "rb_autotune",
     "rb_set_pair_capacity", "rb_debug_hold_pair", "rb_set_launch_shape", "rb_set_n_active", "rb_set_restitution",
+    "rb_sort_pairs_u64",
 ]
 RB_MLP_PARAMS = 9347
 
@@ -118,6 +119,7 @@ def load():
     lib.rb_mlp_grad_fp32.argtypes = [_VP, _VP, _VP, i64, _VP, _VP, _VP]
     lib.rb_energy_sums_noalloc.argtypes = [i64] + [_VP] * 7 + [i32, C.c_double, C.c_double, _VP,
                                                               _VP]
+    lib.rb_sort_pairs_u64.argtypes = [i64, i64, i32, _VP, _VP, _VP]
     lib.rb_destroy.argtypes = [_P]
     lib.rb_destroy.restype = None
     lib.rb_last_error.argtypes = [_P]
@@ -351,6 +353,21 @@ def rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega
     rc = load().rb_energy_sums_noalloc(n, m, x, z, vx, vy, vz, phi, integrator, omega, omega_z,
                                        out, stream)
     _check(rc, None)
+
+
+def rb_sort_pairs_u64(keys, vals=None, key_bits: int = 64, cap=None, stream=None):
+    """The library's stable radix sort on host arrays: returns (keys, vals)
+    sorted by key bits [0, key_bits) (copies; the inputs are not changed).
+    cap >= len(keys) sizes the device buffers, the count being read on the
+    device as in the step's pair sorts."""
+    k = np.array(keys, dtype=np.uint64, copy=True)
+    v = None if vals is None else np.array(vals, dtype=np.uint32, copy=True)
+    if v is not None and len(v) != len(k):
+        raise ValueError("keys and vals differ in length")
+    n = len(k)
+    _check(load().rb_sort_pairs_u64(n, n if cap is None else int(cap), int(key_bits), _ptr(k),
+                                    None if v is None else _ptr(v), stream), None)
+    return k, v
 
 
 def _f32(a, shape=None):

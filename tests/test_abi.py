@@ -43,3 +43,20 @@ def test_create_rejects_bad_config_without_gpu():
     assert rb.load().rb_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == rb.RB_ERR_ARG
     cfg = rb.make_config(integrator=rb.RB_INT_SEI, omega=0.0)
     assert rb.load().rb_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == rb.RB_ERR_ARG
+
+
+def test_sort_rejects_bad_arguments_without_gpu():
+    """rb_sort_pairs_u64 checks its sizes and key width before any device
+    call; an empty sort is a no-op."""
+    from paper_1110_4876_gb300 import rb
+
+    lib = rb.load()
+    k = (ctypes.c_uint64 * 4)()
+    assert lib.rb_sort_pairs_u64(-1, 4, 64, k, None, None) == rb.RB_ERR_ARG
+    assert lib.rb_sort_pairs_u64(4, 3, 64, k, None, None) == rb.RB_ERR_ARG
+    assert lib.rb_sort_pairs_u64(4, 4, 0, k, None, None) == rb.RB_ERR_ARG
+    assert lib.rb_sort_pairs_u64(4, 4, 65, k, None, None) == rb.RB_ERR_ARG
+    assert lib.rb_sort_pairs_u64(4, 1 << 30, 64, k, None, None) == rb.RB_ERR_ARG
+    assert lib.rb_sort_pairs_u64(4, 4, 64, None, None, None) == rb.RB_ERR_ARG
+    assert b"rb_sort_pairs_u64" in lib.rb_last_error(None)
+    assert lib.rb_sort_pairs_u64(0, 0, 64, None, None, None) == rb.RB_OK
