@@ -757,7 +757,6 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
     }
     s->nsm = walk_prepare();
     resolve_prepare(s->nsm);
-    radix_prepare(s->nsm);
     cudaEventCreate(&s->ev0);
     cudaEventCreate(&s->ev1);
     for (auto& ev : s->ev_stage) cudaEventCreate(&ev);
@@ -1644,8 +1643,6 @@ int rb_sort_pairs_u64(int64_t n, int64_t cap, int key_bits, uint64_t* keys, uint
         return RB_ERR_ARG;
     }
     if (cap == 0) return RB_OK;
-    const int nsm = walk_prepare();
-    radix_prepare(nsm);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int ncap = (int)cap;
     uint64_t *k0 = nullptr, *k1 = nullptr;

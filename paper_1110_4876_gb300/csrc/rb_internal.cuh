@@ -224,9 +224,6 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap,
                int key_bits, const int32_t* box_digits, int box_bits, uint32_t* hist, int* err,
                cudaStream_t s);
 size_t radix_hist_words(int ncap);
-// Queries the resident blocks of a radix pass once (outside any stream
-// capture); a grid that fits needs no tile tickets.
-void radix_prepare(int nsm);
 void exclusive_scan_i32(int32_t* data, int n_cap, const int* d_n, int32_t* part, int32_t* total,
                         cudaStream_t s);
 size_t scan_part_words(int ncap);

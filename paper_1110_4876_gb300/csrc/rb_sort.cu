@@ -157,19 +157,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_block(T* __restrict__ a, 
     if (sum && threadIdx.x == kScanThreads - 1) *sum = run;
 }
 
-// One digit pass, one launch.  The grid is at most the blocks resident at
-// once; block b takes tiles b, b + G, b + 2G, ... in order.  For each tile
-// it ranks the keys with warp ballots, publishes its per-digit counts, finds
+// One digit pass, one launch: block b takes tile b (2048 keys).  It ranks
+// the tile's keys with warp ballots, publishes its per-digit counts, finds
 // the counts of all earlier tiles by looking back over their status words
 // (decoupled look-back: sum aggregates until a prefix is met), and writes
-// the tile in digit order.  A tile waits only on smaller tiles, which
-// publish their aggregate before they wait themselves, and the block that
-// holds the smallest unfinished tile has finished all its earlier ones, so
-// with every block resident the waits end; each is bounded all the same
-// (half a second, or at once when another wait gave up) and reports
-// kErrSortStall when it gives up (say, when another stream's kernel held
-// the SMs that long).  Stable: within a tile keys keep their order, and the
-// tiles are in key order.
+// the tile in digit order.  A tile waits only on smaller tiles, whose blocks
+// the GPU dispatched before it (blocks start in index order) and which
+// publish before they wait themselves, so the waits end whether or not the
+// whole grid is resident, also beside other kernels; each wait is bounded
+// all the same (half a second, or at once when another wait gave up) and
+// reports kErrSortStall when it gives up.  Stable: within a tile keys keep
+// their order, and the tiles are in key order.
 template <bool kBoxDigit>
 __global__ void __launch_bounds__(kThreads, 4) k_rs_pass(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
@@ -187,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rs_pass(const uint64_t* __restr
     __shared__ uint64_t sk[kTile];
     __shared__ uint32_t sv[kTile];
     const int n = read_n(d_n, ncap);
+    if ((long long)blockIdx.x * kTile >= n) return;   // past the keys in use
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = threadIdx.x;   // the digit this thread counts and looks back for
     uint32_t* mine = status + (size_t)(pass & 1) * tiles_cap * kBins;
@@ -208,13 +207,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_rs_pass(const uint64_t* __restr
         digit_base = before + v - tot;
     }
     const unsigned lt = (1u << lane) - 1u;
-    for (int tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
+    const int tile = blockIdx.x;
+    if (tile * kTile < n) {
         const int base = tile * kTile;
         const int tn = min(kTile, n - base);
         // the other bank held the previous pass's words; clear this tile's
         // row of it for the next pass
         other[(size_t)tile * kBins + d] = 0u;
-        __syncthreads();   // shared arrays of the previous tile (and wsum) are free
         for (int q = threadIdx.x; q < (kThreads / 32) * kBins; q += kThreads) (&wcnt[0][0])[q] = 0;
         __syncthreads();
         uint64_t k[kItems];
@@ -420,20 +419,6 @@ int radix_sort_passes(int key_bits, bool box_pass, int box_bits) {
     return ceil_div(key_bits, 8) + (box_pass ? ceil_div(box_bits, 8) : 0);
 }
 
-namespace {
-int g_pass_resident = 0;   // blocks of k_rs_pass resident at once on the whole GPU
-}
-
-void radix_prepare(int nsm) {
-    int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rs_pass<false>, kThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rs_pass<true>, kThreads, 0) != cudaSuccess) {
-        cudaGetLastError();
-        a = b = 1;
-    }
-    g_pass_resident = std::max(nsm, 1) * std::max(std::min(a, b), 1);
-}
-
 int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap, const int* d_n,
                int key_bits, const int32_t* box_digits, int box_bits, uint32_t* hist, int* err,
                cudaStream_t s) {
@@ -452,7 +437,6 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap,
     else
         k_rs_hist<false><<<hgrid, kThreads, 0, s>>>(k0, v0, nullptr, d_n, ncap, passes_key, 0, hist,
                                                     status, tiles_cap);
-    const int pgrid = std::max(1, std::min(tiles_cap, g_pass_resident));
     int cur = 0;
     uint64_t* K[2] = {k0, k1};
     uint32_t* V[2] = {v0, v1};
@@ -460,11 +444,11 @@ int radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int ncap,
         const bool boxp = p >= passes_key;
         const int sh = boxp ? 8 * (p - passes_key) : 8 * p;
         if (boxp)
-            k_rs_pass<true><<<pgrid, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
+            k_rs_pass<true><<<tiles_cap, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
                                                            box_digits, d_n, ncap, sh, p, hist,
                                                            status, tiles_cap, err);
         else
-            k_rs_pass<false><<<pgrid, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
+            k_rs_pass<false><<<tiles_cap, kThreads, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1],
                                                             nullptr, d_n, ncap, sh, p, hist, status,
                                                             tiles_cap, err);
         cur ^= 1;
