@@ -78,6 +78,10 @@ struct rb_sim {
     std::string err;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_stage[13] = {};
+    // a branch of the step graph: the tile order of the targets runs on `side`
+    // beside the moments, which leave most of the GPU idle
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool profiling = false;
     int kernels_per_step = 0;
     float last_ms = 0.f;
@@ -431,9 +435,15 @@ int record_step(rb_sim* s, int p) {
         c = 1 - c;
         mark(s, 2);
         build_topology(s->T, s->P[c], s->ctl, s->d_boxes, s->C, st);
-        build_tile_order(s->T, s->P[c], s->ctl, s->tile_order, s->box_bits, st);
+        // the tile order reads the sorted keys and writes only its own
+        // arrays: it runs on the side stream while the moments run here
+        cudaEventRecord(s->ev_fork, st);
+        cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+        build_tile_order(s->T, s->P[c], s->ctl, s->tile_order, s->box_bits, s->side);
+        cudaEventRecord(s->ev_join, s->side);
         mark(s, 3);
         build_gravity_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->cfg.walk == RB_WALK_FP64, st, true);
+        cudaStreamWaitEvent(st, s->ev_join, 0);
         mark(s, 4);
         if (s->cfg.walk == RB_WALK_FP32_LEARNED) {
             // walk at theta; accepted cells with w/R > theta_fb get the
@@ -757,6 +767,16 @@ int rb_create(const rb_config* cfg, int nbox, void* cuda_stream, rb_sim** out) {
     }
     s->nsm = walk_prepare();
     resolve_prepare(s->nsm);
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+        if (s->side) cudaStreamDestroy(s->side);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return fail(nullptr, RB_ERR_CUDA, "cudaStreamCreate / cudaEventCreate failed");
+    }
     cudaEventCreate(&s->ev0);
     cudaEventCreate(&s->ev1);
     for (auto& ev : s->ev_stage) cudaEventCreate(&ev);
@@ -1318,6 +1338,12 @@ void rb_destroy(rb_sim* s) {
     if (s->ev1) cudaEventDestroy(s->ev1);
     for (auto& ev : s->ev_stage)
         if (ev) cudaEventDestroy(ev);
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
