@@ -367,12 +367,39 @@ __device__ __forceinline__ void mom_add(const GravRecArgs& A, int c, double ox, 
     }
 }
 
+// Levels shared by two Morton keys (3 bits a level below the unused top bit).
+__device__ __forceinline__ int common_levels(uint64_t a, uint64_t b) {
+    const uint64_t x = a ^ b;
+    return x ? (__clzll((long long)x) - 1) / 3 : kMaxDepth;
+}
+
+// A depth-21 leaf group (members first..last share their key) stands in the
+// insertion tree below a run of one-child cells that reaches depth 20 unless
+// its parent cell, the deepest one holding another particle of the box, is
+// at depth 20 itself.  Those one-child cells hold the group's members and
+// are opened or accepted like any cell; of them the depth-20 one accepts
+// first (narrowest, and the smallest for the inside rule), so the group's
+// record carries that cell's width and corner.  Without such a cell the group
+// is never accepted.
+__device__ __forceinline__ bool group_has_chain(const GravRecArgs& A, int first, int last) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const uint64_t kf = A.key[first];
+    const int b = A.box[first];
+    int d = -1;   // depth of the group's parent cell
+    if (first > 0 && A.box[first - 1] == b) d = max(d, common_levels(A.key[first - 1], kf));
+    if (last + 1 < n && A.box[last + 1] == b) d = max(d, common_levels(kf, A.key[last + 1]));
+    return d < kMaxDepth - 1;
+}
+
 // The cell's centre of mass, its quadrupole moved there, and its records.
 template <bool kF32Q>
 __device__ __forceinline__ void mom_finish(const GravRecArgs& A, int k, int depth, int end, double ox,
                                            double oy, double oz, MomSums& S) {
-    const int v = depth;
     const int first = A.e_first[k];
+    // a leaf group's members are the entries k + 1 .. end - 1
+    const bool group = depth == kMaxDepth;
+    const bool chain = group && group_has_chain(A, first, first + (end - k - 2));
+    const int v = chain ? kMaxDepth - 1 : depth;   // the depth whose cell the record describes
     const BoxP bp = A.boxes[A.box[first]];
     const double w = ldexp(bp.L, -v);
     const double lo = -0.5 * bp.L;
@@ -408,9 +435,9 @@ __device__ __forceinline__ void mom_finish(const GravRecArgs& A, int k, int dept
         S.q[4] -= S.M * (3.0 * ux * uz);
         S.q[5] -= S.M * (3.0 * uy * uz);
     }
-    const bool group = v == kMaxDepth;   // leaf group: never used as a multipole
+    const bool never = group && !chain;   // a leaf group with no one-child cell above it
     const double ww = w * w;
-    A.d_a[k] = make_double4_32a(cx, cy, cz, group ? __longlong_as_double(0x7ff0000000000000ll) : ww);
+    A.d_a[k] = make_double4_32a(cx, cy, cz, never ? __longlong_as_double(0x7ff0000000000000ll) : ww);
     A.d_q0[k] = make_double4_32a(S.M, S.q[0], S.q[1], S.q[2]);
     A.d_q1[k] = make_double4_32a(S.q[3], S.q[4], S.q[5], w);
     double c0x = 0.0, c0y = 0.0, c0z = 0.0;
@@ -426,7 +453,7 @@ __device__ __forceinline__ void mom_finish(const GravRecArgs& A, int k, int dept
         split_hilo(cx, hx, lx);
         split_hilo(cy, hy, ly);
         split_hilo(cz, hz, lz);
-        const float crit = group ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
+        const float crit = never ? __int_as_float(0x7f800000) : (float)(ww * A.crit_scale);
         A.ra[k] = make_float4(hx, hy, hz, lz);
         A.rb[k] = make_float4(lx, ly, crit, __int_as_float(end));
         if (kF32Q) {

@@ -285,3 +285,34 @@ def test_step_pairs_on_the_gravity_tree(rb, orc, walk):
                                 got["id"])
         assert len(ref) > 50
         assert np.array_equal(keys, ref), k
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_coincident_particles_leaf_groups(rb, orc, walk):
+    """Particles that share a Morton key (exactly coincident, or one ulp
+    apart) end in depth-21 leaf groups whose members are interacted one by
+    one, softened, as in the oracle's insertion tree (Sect. 4.2): the cells,
+    the forces and the per-target interaction counts equal the oracle's."""
+    g = np.random.default_rng(21)
+    n, L = 3000, 4.0
+    x, y, z = g.uniform(-1.5, 1.5, (3, n))
+    groups = [list(range(10, 12)), list(range(100, 103)), list(range(1000, 1005))]
+    for mem in groups:
+        x[mem] = x[mem[0]]; y[mem] = y[mem[0]]; z[mem] = z[mem[0]]
+    x[2001], y[2001], z[2001] = np.nextafter(x[2000], np.inf), y[2000], z[2000]
+    groups.append([2000, 2001])
+    m = g.uniform(0.5, 1.5, n)
+    zero = np.zeros(n)
+    sim = rb.Sim(G=1.0, box=(L, L, L), boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG, theta=0.5,
+                 softening=0.01, dt=1e-3, gravity=1, collisions=0, walk=walk)
+    sim.set_particles((x, y, z, zero, zero, zero, m, zero))
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    p = orc.Params(G=1.0, L=(L,) * 3, theta=0.5, soft=0.01, quadrupole=1)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, x, y, z, m, counts=True)
+    assert orc.force_errors(a, a_ref)[2] <= (FP64_TOL if walk == rb.RB_WALK_FP64 else FP32_TOL)
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
+    got = {(d, frozenset(mm.tolist())) for d, mm, *_ in rb.rb_get_tree(sim.h)}
+    ref = {(d, frozenset(mm.tolist())) for d, mm, *_ in orc.Tree(x, y, z, m, L).cells()}
+    assert got == ref
+    assert {mm for d, mm in got if d == 21} == {frozenset(mem) for mem in groups}
