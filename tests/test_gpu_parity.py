@@ -316,3 +316,30 @@ def test_coincident_particles_leaf_groups(rb, orc, walk):
     ref = {(d, frozenset(mm.tolist())) for d, mm, *_ in orc.Tree(x, y, z, m, L).cells()}
     assert got == ref
     assert {mm for d, mm in got if d == 21} == {frozenset(mem) for mem in groups}
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_ensemble_with_empty_and_tiny_boxes(rb, orc, walk):
+    """Boxes with no particle, one or two particles beside ordinary boxes in
+    one batched simulation: each box advances as it does alone (the FP32
+    walk's compensated sums are grouped by warp iterations, so there the
+    match is to rounding), and an empty box stays empty."""
+    boxes = [(60.0, 900, 31), (40.0, 0, 0), (35.0, 1, 32), (50.0, 2, 33), (80.0, 1200, 34), (45.0, 0, 0)]
+    ens = rb.Sim(nbox=len(boxes), **sheet_cfg(rb, 60.0, walk))
+    for b, (L, N, seed) in enumerate(boxes):
+        ens.set_box(b, (L, L, L))
+        if N:
+            ens.set_particles(I.sheet(L, N, seed), box=b)
+    ens.step(3)
+    tol = 1e-12 if walk == rb.RB_WALK_FP64 else 1e-9
+    for b, (L, N, seed) in enumerate(boxes):
+        ge = ens.particles(b)
+        if N == 0:
+            assert len(ge["id"]) == 0
+            continue
+        one = rb.Sim(**sheet_cfg(rb, L, walk))
+        one.set_particles(I.sheet(L, N, seed))
+        one.step(3)
+        go = one.particles()
+        assert ge["id"].tolist() == go["id"].tolist()
+        assert np.max(np.abs(arrays(ge) - arrays(go))) <= tol * L
