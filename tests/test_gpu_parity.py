@@ -343,3 +343,34 @@ def test_ensemble_with_empty_and_tiny_boxes(rb, orc, walk):
         go = one.particles()
         assert ge["id"].tolist() == go["id"].tolist()
         assert np.max(np.abs(arrays(ge) - arrays(go))) <= tol * L
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("theta,quad", [(0.9, 1), (1.2, 1), (0.9, 0), (0.5, 0)])
+def test_wide_opening_angles_and_monopole(rb, orc, walk, theta, quad):
+    """Wide opening angles (most cells accepted, the inside rule deciding
+    many of them) and the monopole-only walk, on a Plummer sphere and on a
+    sheet with its ghost images: forces and per-target counts equal the
+    oracle's tree at the same theta."""
+    N = 4000
+    P = I.plummer(N, 5)
+    sim = rb.Sim(G=1.0, box=(128.0,) * 3, boundary=rb.RB_BC_OPEN, integrator=rb.RB_INT_LEAPFROG,
+                 theta=theta, quadrupole=quad, softening=1e-3, dt=1e-3, gravity=1, collisions=0, walk=walk)
+    sim.set_particles(P)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    p = orc.Params(G=1.0, L=(128.0,) * 3, theta=theta, quadrupole=quad, soft=1e-3, dt=1e-3, gravity=1)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, P.x, P.y, P.z, P.m, counts=True)
+    tol = FP64_TOL if walk == rb.RB_WALK_FP64 else FP32_TOL
+    assert orc.force_errors(a, a_ref)[2] <= tol
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
+    L = 100.0
+    S = I.sheet(L, 2400, 9)
+    sim = rb.Sim(**sheet_cfg(rb, L, walk, theta=theta, quadrupole=quad))
+    sim.set_particles(S)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(sheet_params(orc, L, theta, quadrupole=quad), 0.0, S.x, S.y,
+                                           S.z, S.m, counts=True)
+    assert orc.force_errors(a, a_ref)[2] <= tol
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
