@@ -204,6 +204,25 @@ def test_correction_equals_oracle_sum_over_band_cells(rb, orc):
         assert np.linalg.norm(got - expect) <= 2e-2 * np.linalg.norm(expect) + 1e-3 * np.linalg.norm(a0[i])
 
 
+def test_zero_network_is_the_plain_walk(rb):
+    """With every weight zero the network outputs zero, so the learned walk
+    (band cells queued through the network inside the walk) gives the plain
+    FP32 walk's forces bit for bit, with the same accepted sets."""
+    L, N = 100.0, 2400
+    P = I.sheet(L, N, 1)
+    plain = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP32, 0.8))
+    plain.set_particles(P)
+    a0, c0 = plain.gravity(counts=True)
+    learned = rb.Sim(**sheet_cfg(rb, L, rb.RB_WALK_FP32_LEARNED, 0.8))
+    learned.set_particles(P)
+    rb.rb_load_mlp(learned.h, np.zeros(rb.RB_MLP_PARAMS, np.float32), 0.5)
+    a1, c1 = learned.gravity(counts=True)
+    assert learned.stats()["corrections"] > 0
+    np.testing.assert_array_equal(a1, a0)
+    for x, y in zip(c0, c1):
+        np.testing.assert_array_equal(x, y)
+
+
 @pytest.fixture(scope="module")
 def trained(rb):
     """Weights trained on residuals of the small and mid sheets."""
