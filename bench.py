@@ -365,9 +365,12 @@ def source_hash(paths) -> str:
 
 
 def profiled_traffic(summary: str, sources, field: str = "dram_bytes_per_launch"):
-    """DRAM bytes (per launch, or per build) from a committed ncu summary, if
-    it was taken on the current kernel sources (its `source_sha256:` line
-    equals the hash of `sources`); else None.  Returns (bytes or None, note)."""
+    """DRAM bytes (per launch, or per build) of the 1M sheet from a committed
+    ncu summary, if it was taken on the current kernel sources (its
+    `source_sha256:` line equals the hash of `sources`) and the run is that
+    workload; else None.  Returns (bytes or None, note)."""
+    if (N_SHEET, L_SHEET) != (1_000_000, 2050.0):
+        return None, f"profiles/{summary} holds the 1M sheet's traffic; this run is another workload: null"
     path = os.path.join(ROOT, "profiles", summary)
     fields = {}
     try:
