@@ -374,3 +374,24 @@ def test_wide_opening_angles_and_monopole(rb, orc, walk, theta, quad):
     assert orc.force_errors(a, a_ref)[2] <= tol
     np.testing.assert_array_equal(nc, rc)
     np.testing.assert_array_equal(nl, rl)
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_late_time_shear_offset(rb, orc, walk):
+    """Far into a run (t = 3.1e7 s, about 650 orbits) the shear offset
+    s = fmod(1.5 Omega Lx t, Ly) of Sect. 2.3 has wrapped thousands of times:
+    the ghost images, and so the forces, the per-target counts and three
+    steps from there (pair sets, positions, velocities), equal the oracle's."""
+    L, N, t0 = 100.0, 2400, 3.1e7
+    P = I.sheet(L, N, 4)
+    p = sheet_params(orc, L, t0=t0)
+    sim = rb.Sim(**sheet_cfg(rb, L, walk, t0=t0))
+    sim.set_particles(P)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, t0, P.x, P.y, P.z, P.m, counts=True)
+    assert orc.force_errors(a, a_ref)[2] <= (FP64_TOL if walk == rb.RB_WALK_FP64 else FP32_TOL)
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
+    sim.set_particles(P)
+    vtol = 1e-12 if walk == rb.RB_WALK_FP64 else 1e-5
+    assert stepwise(rb, orc, sim, p, 3, vtol=vtol, xtol=1e-9 * L, brute_pairs=True) > 100
