@@ -114,3 +114,40 @@ def test_positions_on_the_box_faces(rb, orc, boundary):
         assert np.array_equal(got[key], getattr(st, key)), key
     if boundary:
         assert np.any(got["x"] == -h) and not np.any(got["x"] >= h)
+
+
+@pytest.mark.parametrize("boundary", [1, 2])
+def test_fast_particles_wrap_several_boxes(rb, orc, boundary):
+    """Particles whose drift half carries them up to 7.3 box lengths in x and
+    y, either way, over three drift-only steps: the periodic and the
+    shear-periodic wrap of Sect. 2.3 (an x crossing shifts y by the shear
+    offset and v_y by 1.5 Omega Lx) give the oracle's positions and
+    velocities bit for bit.  By reading R6 x is wrapped once per drift half
+    and y one box length at a time until it is inside, so y always ends in
+    the box and x need not."""
+    L = 16.0
+    g = np.random.default_rng(41)
+    n = 200
+    x, y = g.uniform(-L / 2, L / 2, (2, n))
+    z = g.uniform(-1, 1, n)
+    dt = 0.5
+    # |v| dt / 2 up to 7.3 L, both signs, in x and in y
+    vx = g.uniform(-7.3, 7.3, n) * L / (dt / 2)
+    vy = g.uniform(-7.3, 7.3, n) * L / (dt / 2)
+    vz = np.zeros(n)
+    zero = np.zeros(n)
+    bc = (rb.RB_BC_OPEN, rb.RB_BC_PERIODIC, rb.RB_BC_SHEAR)[boundary]
+    sim = rb.Sim(G=1.0, omega=1e-2, box=(L, L, L), nghost=(1, 1, 0), boundary=bc,
+                 integrator=rb.RB_INT_LEAPFROG, dt=dt, gravity=0, collisions=0)
+    sim.set_particles((x, y, z, vx, vy, vz, np.ones(n), zero))
+    p = orc.Params(omega=1e-2, L=(L, L, L), nghost=(1, 1, 0), boundary=boundary, integrator=0, dt=dt,
+                   gravity=0, collisions=0)
+    st = orc.State(p, x, y, z, vx, vy, vz, np.ones(n), zero)
+    for k in range(3):
+        sim.step(1)
+        st.step(1)
+        got = sim.particles()
+        assert got["id"].tolist() == st.id.tolist(), k
+        for key in ("x", "y", "z", "vx", "vy"):
+            assert np.array_equal(got[key], getattr(st, key)), (k, key)
+        assert np.all(np.abs(got["y"]) <= L / 2)
