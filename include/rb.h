@@ -149,7 +149,12 @@ int rb_set_particles(rb_sim* sim, int box, int64_t n, const double* x, const dou
  * stream, replaying a captured CUDA graph per step; returns once the steps
  * are done and the device error word was checked.  A pair-buffer overflow is
  * repaired inside the step (buffer grown, the search re-run before any
- * velocity changes); RB_ERR_CAPACITY only if that fails. */
+ * velocity changes); RB_ERR_CAPACITY only if that fails.  Other errors:
+ * RB_ERR_NONFINITE (a position became non-finite or left the box by more
+ * than 4096 box lengths in one drift half), RB_ERR_STATE (a malformed tree
+ * met by a walk; the learned walk without weights), RB_ERR_TIMEOUT (a
+ * bounded device wait gave up: the resolution queue's or a radix pass's
+ * look-back), RB_ERR_CUDA. */
 int rb_step(rb_sim* sim, int64_t nsteps);
 
 /* Copy the live particles of box `box`, in ascending id order, into host
