@@ -648,6 +648,47 @@ def run_compare(args):
     return line
 
 
+def run_extensions(args):
+    """The 1M sheet's step (FP32 walk, theta 0.5) with the velocity-dependent
+    restitution and the test particles the paper allows (Sect. 5 and
+    Sect. 4): the constant eps = 0.5 as in the default run, an illustrative
+    power law eps = min(1, (|v_n| / v_c)^-p) with v_c = 7.7e-5 m/s and
+    p = 0.234 (about 0.75 at the sheet's impact speeds), and the ids above
+    N/2 as test particles.  Their parity with the oracle is tested in
+    tests/test_gpu_extensions.py.  One JSON line."""
+    import torch
+
+    from paper_1110_4876_gb300 import inputs as I
+    from paper_1110_4876_gb300 import rb
+
+    rb.load()
+    stream = torch.cuda.Stream()
+    clk = Clocks(torch.cuda.current_device()).__enter__()
+    t_clk = time.time()
+    P = I.sheet(L_SHEET, N_SHEET, SEED)
+    rows = {}
+    for name in ("constant eps=0.5", "power-law eps (v_c=7.7e-5 m/s, p=0.234)", "test particles (n_active=N/2)"):
+        sim = make_sim(rb, sheet_config(rb, "fp32"), stream.cuda_stream)
+        if name.startswith("power"):
+            rb.rb_set_restitution(sim.h, rb.RB_EPS_POWER, 7.7e-5, 0.234)
+        if name.startswith("test"):
+            rb.rb_set_n_active(sim.h, N_SHEET // 2)
+        sim.set_particles(P)
+        ms, wms, shape = _timed(sim, stream, args.steps, args.warmup)
+        st = sim.stats()
+        rows[name] = {"particle_steps_per_s": N_SHEET / (ms / 1e3), "ms_per_step": ms, "walk_ms": wms,
+                      "pairs_last_step": st["pairs_found"], "launch_shape": shape}
+        del sim
+    clk.window(t_clk, time.time())
+    clk.__exit__()
+    line = {"metric": "particle-steps/s with the restitution law and test particles (1M sheet)",
+            "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "forms": rows,
+            "data": "synthetic", "config": {"workload": workload_name("fp32")}}
+    line["clocks (whole run)"] = clk.summary()
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_plummer(args):
     """Plummer sphere, N = 2^20 (G = M = a = 1, open, leap-frog, dt = 1e-3,
     softening 1e-3): the FP32 and FP64 walks at theta 0.3 / 0.5 / 0.7,
@@ -1029,6 +1070,8 @@ def main():
                     help="measure the 256-box ensemble (batched vs looped) instead")
     ap.add_argument("--compare", action="store_true",
                     help="each walk form on the 1M sheet with its force error vs direct sum")
+    ap.add_argument("--extensions", action="store_true",
+                    help="the 1M sheet with the power-law restitution and with test particles")
     ap.add_argument("--plummer", action="store_true",
                     help="FP32 and FP64 walks on the 2^20 Plummer sphere at theta 0.3/0.5/0.7")
     ap.add_argument("--sweep", action="store_true",
@@ -1051,6 +1094,8 @@ def main():
         run_ensemble(args)
     elif args.compare:
         run_compare(args)
+    elif args.extensions:
+        run_extensions(args)
     elif args.plummer:
         run_plummer(args)
     elif args.sweep:
