@@ -36,9 +36,9 @@ def _sheet(rb, orc, L, walk):
     return cfg, p
 
 
-def _check_terms(orc, sim, p, t):
-    g = sim.particles()
-    K, U, W, P = sim.energy_terms()
+def _check_terms(orc, sim, p, t, box=0):
+    g = sim.particles(box)
+    K, U, W, P = sim.energy_terms(box)
     rK, rU, rW, rP = orc.energy_terms(p, t, g["x"], g["y"], g["z"], g["vx"], g["vy"], g["vz"], g["m"])
     m = g["m"]
     v2 = g["vx"] ** 2 + g["vy"] ** 2 + g["vz"] ** 2
@@ -50,7 +50,7 @@ def _check_terms(orc, sim, p, t):
         assert abs(P[k] - rP[k]) <= 1e-12 * np.sum(m * np.abs(g[v])), k
     assert rW < 0.0
     assert abs(W - rW) <= 1e-12 * abs(rW)
-    E, PP = sim.energy()
+    E, PP = sim.energy(box)
     assert E == K + U + W
     np.testing.assert_array_equal(PP, P)
     return K, U, W
@@ -86,3 +86,20 @@ def test_open_leapfrog_energy_terms_match_oracle(rb, orc):
     # a Plummer sphere sampled from its distribution function is in virial
     # equilibrium: 2K + W ~ 0 within the sampling noise of 4000 particles
     assert abs(2 * K + W) < 0.1 * abs(W)
+
+
+def test_batched_boxes_energy_terms_match_oracle(rb, orc):
+    """Each box of a batched simulation (different sizes and particle
+    counts) has the energy terms of that box alone, with its own ghost
+    images and tree, after two steps."""
+    boxes = [(60.0, 900, 41), (35.0, 300, 42), (80.0, 1500, 43)]
+    cfg, _ = _sheet(rb, orc, 60.0, 1)
+    ens = rb.Sim(nbox=len(boxes), **cfg)
+    for b, (L, N, seed) in enumerate(boxes):
+        ens.set_box(b, (L, L, L))
+        ens.set_particles(I.sheet(L, N, seed), box=b)
+    ens.step(2)
+    for b, (L, N, seed) in enumerate(boxes):
+        _, p = _sheet(rb, orc, L, 1)
+        K, U, W = _check_terms(orc, ens, p, orc.time_at(p, 4), box=b)
+        assert U < 0.0 < K
