@@ -179,3 +179,29 @@ def test_degenerate_sweep_is_reported(rb):
     with pytest.raises(rb.RbError) as e:
         sim.step(1)
     assert e.value.code == rb.RB_ERR_CAPACITY
+
+
+def test_batched_sweep_boxes_equal_single_boxes(rb):
+    """The plane sweep in a batched simulation: elongated boxes of different
+    lengths and particle counts (the sweep's items sorted by box, then by
+    lower end) advance exactly as each box does alone."""
+    Ly = 20.0
+    boxes = []
+    for n, seed in ((1500, 51), (600, 52), (2500, 53)):
+        Lx = I.long_sheet_size(n, Ly)
+        P = I.sheet_xy(Lx, Ly, n, seed)
+        P.vx += np.random.default_rng(seed + 100).normal(0, 0.02, n)
+        boxes.append((Lx, P))
+    Lmax = max(Lx for Lx, _ in boxes)
+    ens = rb.Sim(nbox=len(boxes), **_long_cfg(rb, Lmax, Ly))
+    for b, (Lx, P) in enumerate(boxes):
+        ens.set_box(b, (Lx, Ly, Lx))
+        ens.set_particles(P, box=b)
+    ens.step(5)
+    for b, (Lx, P) in enumerate(boxes):
+        one = rb.Sim(**_long_cfg(rb, Lx, Ly))
+        one.set_particles(P)
+        one.step(5)
+        ge, go = ens.particles(b), one.particles()
+        assert ge["id"].tolist() == go["id"].tolist()
+        np.testing.assert_array_equal(arrays(ge), arrays(go))
