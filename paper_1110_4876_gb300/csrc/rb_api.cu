@@ -541,6 +541,12 @@ int capture_graphs(rb_sim* s) {
     return RB_OK;
 }
 
+__global__ void k_ctl_fresh(Ctl* ctl, int n) {
+    Ctl c{};
+    c.n_live = n;
+    *ctl = c;
+}
+
 int read_ctl(rb_sim* s) {
     RB_CUDA(s, cudaMemcpyAsync(&s->hctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
     RB_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -666,8 +672,13 @@ int read_box(rb_sim* s, int box, int64_t cap, int64_t* n_out, double* const dst[
     int32_t* flags = s->T.start;   // scratch: ncap + 1 ints, free between steps
     particles_by_id(s->P[s->cur], out, box, (int)s->base[box], s->ncap, flags, nb, &s->ctl->out_live,
                     s->stream);
-    if (read_ctl(s)) return RB_ERR_CUDA;
-    const int live = s->hctl.out_live;
+    // only an open boundary removes particles; otherwise every id of the box
+    // is live and the copies need not wait for the count
+    int live = nb;
+    if (s->cfg.boundary == RB_BC_OPEN) {
+        if (read_ctl(s)) return RB_ERR_CUDA;
+        live = s->hctl.out_live;
+    }
     if (n_out) *n_out = live;
     bool want = id != nullptr;
     for (int f = 0; f < 8; f++) want = want || dst[f] != nullptr;
@@ -826,10 +837,10 @@ int rb_set_particles(rb_sim* s, int box, int64_t n, const double* x, const doubl
         if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN && 2.0 * rm >= std::min(h.L[0], h.L[1]))
             return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
         reset_slots(P, s->PR.slot_of_id, (int)n, s->ncap, s->nbox, s->stream);
-        Ctl cc{};
-        cc.n_live = (int)n;
-        RB_CUDA(s, cudaMemcpyAsync(s->ctl, &cc, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
-        RB_CUDA(s, cudaStreamSynchronize(s->stream));
+        // the counters of a fresh state, written on the stream (no host wait:
+        // the next call's work follows on the same stream)
+        k_ctl_fresh<<<1, 1, 0, s->stream>>>(s->ctl, (int)n);
+        RB_CUDA(s, cudaGetLastError());
         if (rm != s->rmax) drop_graphs(s);   // R_max is a launch argument of the graphs
         s->rmax = rm;
         s->cur = c;
