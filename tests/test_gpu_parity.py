@@ -395,3 +395,18 @@ def test_late_time_shear_offset(rb, orc, walk):
     sim.set_particles(P)
     vtol = 1e-12 if walk == rb.RB_WALK_FP64 else 1e-5
     assert stepwise(rb, orc, sim, p, 3, vtol=vtol, xtol=1e-9 * L, brute_pairs=True) > 100
+
+
+def test_sei_with_a_distinct_vertical_frequency(rb, orc):
+    """SEI (Sect. 3.3) with a vertical epicyclic frequency Omega_z = 1.7
+    Omega, as self-gravity raises it in a dense ring: collisions only, each
+    step from the same state gives the oracle's positions and pair sets
+    exactly and its velocities to 1e-12."""
+    L, N = 100.0, 2400
+    P = I.sheet(L, N, 6)
+    Oz = 1.7 * I.OMEGA
+    cfg = sheet_cfg(rb, L, rb.RB_WALK_FP64, gravity=0, omega_z=Oz)
+    p = sheet_params(orc, L, gravity=0, omega_z=Oz)
+    sim = rb.Sim(**cfg)
+    sim.set_particles(P)
+    assert stepwise(rb, orc, sim, p, 5) > 50
