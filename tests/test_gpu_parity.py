@@ -410,3 +410,22 @@ def test_sei_with_a_distinct_vertical_frequency(rb, orc):
     sim = rb.Sim(**cfg)
     sim.set_particles(P)
     assert stepwise(rb, orc, sim, p, 5) > 50
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("nghost,zper", [((2, 2, 0), 0), ((1, 1, 1), 1)])
+def test_more_ghost_images(rb, orc, walk, nghost, zper):
+    """Two rings of ghost boxes in x and y (25 images), and one ring with a
+    periodic z (27 images), Sect. 2.3: forces and per-target counts equal the
+    oracle's tree over the same images."""
+    L, N = 60.0, 2000
+    P = I.sheet(L, N, 8)
+    cfg = sheet_cfg(rb, L, walk, nghost=nghost, z_periodic=zper)
+    p = sheet_params(orc, L, nghost=nghost, z_periodic=zper)
+    sim = rb.Sim(**cfg)
+    sim.set_particles(P)
+    a, (nc, nl, nm) = sim.gravity(counts=True)
+    a_ref, (rc, rl, rm) = orc.tree_gravity(p, 0.0, P.x, P.y, P.z, P.m, counts=True)
+    assert orc.force_errors(a, a_ref)[2] <= (FP64_TOL if walk == rb.RB_WALK_FP64 else FP32_TOL)
+    np.testing.assert_array_equal(nc, rc)
+    np.testing.assert_array_equal(nl, rl)
