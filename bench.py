@@ -520,7 +520,11 @@ def run_ensemble(args):
     for b, (Lb, P) in enumerate(parts):
         ens.set_box(b, (Lb, Lb, Lb))
         ens.set_particles(P, box=b)
-    tuned = rb.rb_autotune(ens.h)
+    if args.shape:
+        rb.rb_set_launch_shape(ens.h, *args.shape)   # fixed shapes (profiling runs)
+        tuned = tuple(args.shape)
+    else:
+        tuned = rb.rb_autotune(ens.h)
     clk = Clocks(torch.cuda.current_device()).__enter__()
     ens.step(args.warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
