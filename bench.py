@@ -179,6 +179,23 @@ def max_over_ranks(t_ms: float, dist, device) -> float:
     return float(t.item())
 
 
+def search_rate(visits, iters, ms, ms_counted):
+    """Tree collision search: tree entries tested by the targets (nodes
+    visited, all images) per launch, counted by the search's counting
+    variant in one step after the timed ones, over the event-timed search
+    stage of the timed steps (which run the plain variant).  The search is
+    bound by L1/L2 latency, so it is reported as a rate, with no roofline."""
+    if not (visits > 0 and ms > 0):
+        return None
+    return {"bound": "latency (L1/L2 round trips)", "kernel": "k_collide (tree collision search)",
+            "nodes_visited_per_launch": visits, "nodes_visited_per_particle": visits / N_SHEET,
+            "nodes_visited_per_s": visits / (ms / 1e3), "ms_per_launch": ms,
+            "warp_iterations_per_launch": iters,
+            "lane_utilisation": visits / (32.0 * iters) if iters > 0 else None,
+            "counted": "in one step after the timed steps, by the counting variant "
+                       f"({ms_counted:.4f} ms); the timed steps run the plain search"}
+
+
 def whole_job_value(world: int, n_per_rank: int, steps: int, t_ms: float) -> float:
     """Particle-steps/s of all ranks together (each rank advances its own
     n_per_rank particles for `steps` steps; t_ms is the slowest rank)."""
@@ -228,7 +245,7 @@ def run_ours(args):
     # ---- device-resident throughput (inputs already in HBM) ----
     walk_ms, walk_flops, stage_sum = [], [], {}
     launches = 0
-    pairs, corr, counts, cells = [], [], [], []
+    pairs, corr, counts, cells, search_ms = [], [], [], [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -248,6 +265,7 @@ def run_ours(args):
         counts.append((st["cell_interactions"], st["leaf_interactions"], st["mac_tests"],
                        st["warp_iterations"]))
         cells.append(st["cells"])
+        search_ms.append(st["ms_stage"]["collision_search"])
     e1.record(stream)
     barrier()
     clk.window(tw0, time.time())
@@ -255,6 +273,13 @@ def run_ours(args):
     t_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     clocks = clk.summary()
     value = whole_job_value(world, N_SHEET, args.steps, t_ms)
+    # one more step, untimed, with the counting variant of the collision search
+    rb.rb_set_profiling(sim.h, 2)
+    sim.step(1)
+    st = sim.stats()
+    search = search_rate(st["search_visits"], st["search_iterations"],
+                         statistics.mean(search_ms), st["ms_stage"]["collision_search"])
+    rb.rb_set_profiling(sim.h, 1)
 
     # ---- end to end through the C ABI with host buffers ----
     ke = max(3, min(args.steps, 10))
@@ -338,6 +363,7 @@ def run_ours(args):
                    "walk_block, search_block, walk_group, tile_order": list(tuned)},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
         "roofline_build": build_roofline(stage_sum, args.steps, cells, peaks, tuned[3]),
+        "collision_search": search,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
     }
     if args.cpu_baseline and world == 1:

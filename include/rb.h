@@ -117,6 +117,10 @@ typedef struct rb_stats_t {
     int64_t walk_group;       /* FP32 walk shape: 0 union walk, 4 group walk (4-lane subgroups
                                  for the mixed subtrees) */
     int64_t tile_order;       /* order in which walks and search take their targets (RB_TILE_*) */
+    int64_t search_visits;    /* tree search: entries (cells and leaves) tested by the targets of
+                                 the last collision search, all images; counted only at
+                                 rb_set_profiling level 2 (else 0; 0 for the plane sweep) */
+    int64_t search_iterations;/* tree search: warp iterations of that search (32 targets each) */
 } rb_stats_t;
 
 typedef struct rb_sim rb_sim; /* opaque, owned by the library */
@@ -222,7 +226,11 @@ int rb_get_time(rb_sim* sim, double* t);
 /* Counters of the last step (host struct). */
 int rb_stats(rb_sim* sim, rb_stats_t* out);
 /* on = 1: record CUDA events between the stages of every step (event nodes
- * inside the step graph) so rb_stats reports per-stage device times. */
+ * inside the step graph) so rb_stats reports per-stage device times.
+ * on = 2: also run the tree collision search in its counting variant, so
+ * rb_stats reports search_visits and search_iterations (that variant is
+ * about 9% slower; at 0 and 1 both counters read 0).  on = 0 turns both off.
+ * Errors: RB_ERR_ARG (on outside 0..2). */
 int rb_set_profiling(rb_sim* sim, int on);
 /* Time the gravity walk and the tree collision search on the current
  * positions at 64, 128 and 256 threads per block, for the plain FP32 walk at

@@ -82,7 +82,7 @@ struct rb_sim {
     // beside the moments, which leave most of the GPU idle
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    bool profiling = false;
+    int profiling = 0;   // 1: stage events; 2: also the counting collision search
     int kernels_per_step = 0;
     float last_ms = 0.f;
     float stage_ms[12] = {};
@@ -483,7 +483,7 @@ int record_step(rb_sim* s, int p) {
         build_collision_aabb(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
         mark(s, 9);
         collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block, true,
-                         s->rmax);
+                         s->rmax, s->profiling == 2);
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
@@ -497,7 +497,8 @@ int record_step(rb_sim* s, int p) {
         mark(s, 8);
         build_collision_records(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->rmax, st);
         mark(s, 9);
-        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block);
+        collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, 2, st, s->search_block, false,
+                         0.0, s->profiling == 2);
         mark(s, 10);
         sort_pairs(s->PR, s->ctl, st, pair_key_bits(s));
         mark(s, 11);
@@ -563,12 +564,13 @@ int clear_err(rb_sim* s) {
 int collide_with_retry(rb_sim* s, int c, int hs, bool resolve, bool aabb) {
     for (int attempt = 0; attempt < 2; attempt++) {
         RB_CUDA(s, cudaMemsetAsync(&s->ctl->pair_count, 0, sizeof(int), s->stream));
+        clear_search_stats(s->ctl, s->stream);
         if (clear_err(s)) return RB_ERR_CUDA;
         if (s->cfg.collisions == RB_COLL_SWEEP)
             sweep_search(s->P[c], s->ctl, s->d_boxes, s->C, s->SW, s->PR, hs, s->ncap, s->stream);
         else
             collision_search(s->T, s->P[c], s->ctl, s->d_boxes, s->C, s->PR, hs, s->stream,
-                             s->search_block, aabb, s->rmax);
+                             s->search_block, aabb, s->rmax, s->profiling == 2);
         sort_pairs(s->PR, s->ctl, s->stream, pair_key_bits(s));
         if (read_ctl(s)) return RB_ERR_CUDA;
         if (s->hctl.err & kErrSweepLong)
@@ -1132,6 +1134,8 @@ int rb_stats(rb_sim* s, rb_stats_t* out) {
     for (int q = 0; q < 12; q++) out->ms_stage[q] = s->stage_ms[q];
     out->corrections = s->cfg.walk == RB_WALK_FP32_LEARNED ? c.req_count : 0;
     out->warp_iterations = (int64_t)c.n_iter;
+    out->search_visits = (int64_t)c.n_visit;
+    out->search_iterations = (int64_t)c.n_siter;
     return RB_OK;
 }
 
@@ -1331,8 +1335,9 @@ int rb_set_restitution(rb_sim* s, int law, double v_c, double p) {
 
 int rb_set_profiling(rb_sim* s, int on) {
     if (!s) return fail(s, RB_ERR_ARG, "null sim");
-    if ((on != 0) != s->profiling) {
-        s->profiling = on != 0;
+    if (on < 0 || on > 2) return fail(s, RB_ERR_ARG, "profiling level must be 0, 1 or 2");
+    if (on != s->profiling) {
+        s->profiling = on;
         drop_graphs(s);
     }
     return RB_OK;

@@ -76,6 +76,8 @@ struct Ctl {
     int pad_;
     unsigned long long n_cell, n_leaf, n_mac, n_recheck;
     unsigned long long n_iter;        // warp iterations of the last FP32 walk (entries visited)
+    unsigned long long n_visit;       // tree entries tested by the targets of the last collision search
+    unsigned long long n_siter;       // warp iterations of the last collision search
     unsigned long long sweep_wbits;   // plane sweep: largest half extent (double bits)
 };
 constexpr int kErrNonFinite = 1;
@@ -299,9 +301,11 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
                   bool counts, cudaStream_t s, const WalkRecord* rec = nullptr, int block = 128,
                   const WalkLearn* learn = nullptr, int group = 0);
 // aabb: the records of build_collision_aabb, with rmax the largest radius.
+// count: the variant that adds the entries its targets test and its warp
+// iterations to ctl->n_visit and ctl->n_siter.
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                       const Pairs& PR, int half_step_offset, cudaStream_t s, int block = 128,
-                      bool aabb = false, double rmax = 0.0);
+                      bool aabb = false, double rmax = 0.0, bool count = false);
 
 // rb_sweep.cu: plane-sweep search on set P at half-step offset hs; the
 // canonical pair keys are appended to PR like the tree search's.
@@ -373,5 +377,6 @@ void to_bf16_async(const float* w, void* wbf, cudaStream_t s);
 void label_async(const ReqArgs& A, float* X, float* Y, int64_t* meta, int max_req, cudaStream_t s);
 }  // namespace mlp
 void clear_walk_stats(Ctl* ctl, cudaStream_t s);
+void clear_search_stats(Ctl* ctl, cudaStream_t s);
 
 }  // namespace rb

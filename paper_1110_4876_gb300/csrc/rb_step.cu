@@ -642,8 +642,13 @@ void energy_terms(const PSet& P, Ctl* ctl, const SimC& C, const double* phi, int
 
 void step_advance(Ctl* ctl, cudaStream_t s) { k_step_advance<<<1, 1, 0, s>>>(ctl); }
 
+// The walk's counters (n_cell .. n_iter) and the search's (n_visit, n_siter).
 void clear_walk_stats(Ctl* ctl, cudaStream_t s) {
-    cudaMemsetAsync(&ctl->n_cell, 0, 5 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(&ctl->n_cell, 0, 7 * sizeof(unsigned long long), s);
+}
+
+void clear_search_stats(Ctl* ctl, cudaStream_t s) {
+    cudaMemsetAsync(&ctl->n_visit, 0, 2 * sizeof(unsigned long long), s);
 }
 
 }  // namespace rb

@@ -1200,7 +1200,10 @@ __device__ __forceinline__ bool overlap64(double xa, double ya, double za, doubl
 // id a, image of b as seen from a).  On GB300 an FP64 instruction occupies
 // the SM's FP64 pipe 16 cycles per warp, so the exact test on every overlap
 // kept that pipe busy for most of the search.
-template <bool kAABB>
+// kCount: also count the entries the targets test (nodes visited) and the
+// warp iterations; a separate variant, since the counters cost the
+// 32-register search about 9% of its time in spilled registers.
+template <bool kAABB, bool kCount>
 __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
     const int lane = threadIdx.x & 31;
     const bool valid = wbase + lane < n;
@@ -1217,6 +1220,9 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
     split_d(pz, phz, plz);
     const ImgTab* itab = A.img + (size_t)A.box[ii] * A.nimg;
     int gi = 0;
+    // kCount: entries the warp's targets tested and warp iterations
+    // (both warp-uniform)
+    unsigned nvis = 0, siter = 0;
     for (int gx = -A.ngx; gx <= A.ngx; gx++)
         for (int gy = -A.ngy; gy <= A.ngy; gy++)
             for (int gz = -A.ngz; gz <= A.ngz; gz++, gi++) {
@@ -1236,6 +1242,10 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                     if (e == kEnd) break;
                     const float4 ra = __ldg(&A.ra[e]);
                     const bool act = next == e;
+                    if (kCount) {
+                        nvis += __popc(__ballot_sync(kFull, act));
+                        siter++;
+                    }
                     bool hit = false;
                     uint64_t key = 0;
                     if (__float_as_int(ra.w) < 0) {
@@ -1317,18 +1327,22 @@ __device__ __forceinline__ void collide(const CollArgs& A, int wbase, int n) {
                     }
                 }
             }
+    if (kCount && lane == 0) {
+        atomicAdd(&A.ctl->n_visit, (unsigned long long)nvis);
+        atomicAdd(&A.ctl->n_siter, (unsigned long long)siter);
+    }
 }
 
 // At most 32 registers (8 blocks of 256 threads per SM, every warp slot
 // resident): the search is latency-bound, and going from 40 resident warps
 // per SM (48 registers) to 48 (40) and 64 (32, with a few spilled values)
 // took 4% and another 2% off it.
-template <bool kAABB>
+template <bool kAABB, bool kCount = false>
 __global__ void __launch_bounds__(kMaxWalkBlock, 8) k_collide(CollArgs A) {
     const int n = min(A.ctl->n_live, A.ncap);
     const int ntile = (n + 31) >> 5, q = sm_queue(A.nq);
     for (int t = next_tile(A.tq, A.nq, q, ntile); t >= 0; t = next_tile(A.tq, A.nq, q, ntile))
-        collide<kAABB>(A, t << 5, n);
+        collide<kAABB, kCount>(A, t << 5, n);
 }
 
 }  // namespace
@@ -1430,6 +1444,8 @@ int walk_prepare() {
 #undef RB_PREP_G
     prepare_one(k_collide<true>);
     prepare_one(k_collide<false>);
+    prepare_one(k_collide<true, true>);
+    prepare_one(k_collide<false, true>);
     return g_nsm;
 }
 
@@ -1532,7 +1548,7 @@ void gravity_walk(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, con
 
 void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, const SimC& C,
                       const Pairs& PR, int half_step_offset, cudaStream_t s, int block, bool aabb,
-                      double rmax) {
+                      double rmax, bool count) {
     if (T.cap_n <= 0) return;
     block = (block == 64 || block == 256) ? block : 128;
     CollArgs A;
@@ -1550,8 +1566,14 @@ void collision_search(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes,
     A.tq = T.tq;
     A.nq = T.nq;
     A.nimg = build_image_table(boxes, ctl, C, half_step_offset, T.img, s, T.tq, T.nq);
-    if (aabb) RB_LAUNCH(k_collide<true>);
-    else RB_LAUNCH(k_collide<false>);
+    if (count) {
+        if (aabb) RB_LAUNCH(k_collide<true, true>);
+        else RB_LAUNCH(k_collide<false, true>);
+    } else if (aabb) {
+        RB_LAUNCH(k_collide<true>);
+    } else {
+        RB_LAUNCH(k_collide<false>);
+    }
 #undef RB_LAUNCH
 }
 

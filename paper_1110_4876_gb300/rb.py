@@ -64,7 +64,7 @@ class rb_stats_t(C.Structure):
         ("kernels_per_step", C.c_int64), ("walk_block", C.c_int64), ("search_block", C.c_int64),
         ("t", C.c_double), ("ms_last_step", C.c_double), ("ms_stage", C.c_double * 12),
         ("corrections", C.c_int64), ("warp_iterations", C.c_int64), ("walk_group", C.c_int64),
-        ("tile_order", C.c_int64),
+        ("tile_order", C.c_int64), ("search_visits", C.c_int64), ("search_iterations", C.c_int64),
     ]
 
 
@@ -315,8 +315,10 @@ def rb_stats(sim) -> dict:
     return out
 
 
-def rb_set_profiling(sim, on: bool = True):
-    _check(load().rb_set_profiling(sim, 1 if on else 0), sim)
+def rb_set_profiling(sim, on=True):
+    """on: False/0 off, True/1 stage times, 2 stage times and the counting
+    collision search (search_visits, search_iterations in rb_stats)."""
+    _check(load().rb_set_profiling(sim, int(on)), sim)
 
 
 def rb_autotune(sim, use_cache: bool = True):

@@ -63,7 +63,8 @@ def test_every_launch_shape_gives_the_same_forces_and_pairs(theta):
                integrator=rb.RB_INT_SEI, theta=theta, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
     sim = rb.Sim(**cfg)
     sim.set_particles(P)
-    ref_a, ref_c, ref_p = None, None, None
+    rb.rb_set_profiling(sim.h, 2)   # the counting search
+    ref_a, ref_c, ref_p, ref_v = None, None, None, None
     for to in (rb.RB_TILE_MORTON, rb.RB_TILE_HILBERT_XY, rb.RB_TILE_HILBERT_XYZ):
         for wg in (0, 4):
             shape_a = None
@@ -72,8 +73,10 @@ def test_every_launch_shape_gives_the_same_forces_and_pairs(theta):
                     rb.rb_set_launch_shape(sim.h, wb, sb, wg, to)
                     acc, cnt = sim.gravity(counts=True)
                     pairs = rb.pair_keys(*sim.pairs())
+                    st = sim.stats()
+                    visits, iters = st["search_visits"], st["search_iterations"]
                     if ref_a is None:
-                        ref_a, ref_c, ref_p = acc, cnt, pairs
+                        ref_a, ref_c, ref_p, ref_v = acc, cnt, pairs, visits
                     if shape_a is None:
                         shape_a = acc
                     # block sizes: bit for bit; warp shapes and tile orders:
@@ -83,9 +86,44 @@ def test_every_launch_shape_gives_the_same_forces_and_pairs(theta):
                     for c, r in zip(cnt, ref_c):
                         np.testing.assert_array_equal(c, r)
                     assert np.array_equal(pairs, ref_p), (to, wg, wb, sb)
+                    # each target's search is its own walk, whichever warp
+                    # carries it: the entries it tests do not depend on the
+                    # shape; every target tests the root of each of the 9
+                    # images, and a warp iteration serves at most 32 lanes
+                    assert visits == ref_v, (to, wg, wb, sb)
+                    assert 9 * N <= visits <= 32 * iters
     with pytest.raises(rb.RbError):
         rb.rb_set_launch_shape(sim.h, 96, 128, 0)
     with pytest.raises(rb.RbError):
         rb.rb_set_launch_shape(sim.h, 128, 128, 8)
     with pytest.raises(rb.RbError):
         rb.rb_set_launch_shape(sim.h, 128, 128, 0, 3)
+
+
+def test_search_visits_of_a_step_do_not_depend_on_the_search_block():
+    """The step's search (cell boxes on the gravity tree) counts the entries
+    its targets test; block sizes give bit-identical steps, so equal counts."""
+    from paper_1110_4876_gb300 import build, rb
+
+    build.build()
+    L, N = 160.0, 6000
+    P = I.sheet(L, N, 8)
+    cfg = dict(G=I.G_SI, omega=I.OMEGA, box=(L, L, L), nghost=(1, 1, 0), boundary=rb.RB_BC_SHEAR,
+               integrator=rb.RB_INT_SEI, theta=0.5, eps=0.5, dt=I.DT_SHEET, gravity=1, collisions=1)
+    sim = rb.Sim(**cfg)
+    got = []
+    sim.set_particles(P)
+    sim.step(1)
+    assert sim.stats()["search_visits"] == 0   # not counted below level 2
+    rb.rb_set_profiling(sim.h, 2)
+    for sb in (64, 128, 256):
+        sim.set_particles(P)
+        rb.rb_set_launch_shape(sim.h, 128, sb, 0, rb.RB_TILE_HILBERT_XY)
+        sim.step(1)
+        st = sim.stats()
+        assert st["pairs_found"] > 0
+        assert 9 * N <= st["search_visits"] <= 32 * st["search_iterations"]
+        got.append((st["search_visits"], st["pairs_found"]))
+    assert got[0] == got[1] == got[2]
+    with pytest.raises(rb.RbError):
+        rb.rb_set_profiling(sim.h, 3)
