@@ -289,6 +289,7 @@ int upload(rb_sim* s) {
             rc |= dalloc(s, &rab, 2 * (size_t)ecap, L);
             rc |= dalloc(s, &rq, 2 * (size_t)ecap, L);
             rc |= dalloc(s, &rcc, 2 * (size_t)ecap, L);
+            rc |= dalloc(s, &T.pbox, 2 * (size_t)box_items(cap), L);
             T.ra.p = rab; T.rb.p = rab ? rab + 1 : nullptr;
             T.rq0.p = rq; T.rq1.p = rq ? rq + 1 : nullptr;
             T.rc_hi.p = rcc; T.rc_lo.p = rcc ? rcc + 1 : nullptr;

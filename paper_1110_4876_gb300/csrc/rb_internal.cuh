@@ -95,6 +95,12 @@ struct ImgTab {
     float4 hi, lo;   // w unused
 };
 
+// Box items of the collision records on the gravity tree: one per slot and
+// per run of 32, 256 and 8192 slots.
+inline long long box_items(int cap_n) {
+    return (long long)cap_n + (cap_n + 31) / 32 + (cap_n + 255) / 256 + (cap_n + 8191) / 8192;
+}
+
 // Tree and scratch buffers of one build (sized for capacity n).
 // One of two float4 records that an entry keeps side by side, so that the
 // pair read together (e.g. centre of mass hi and lo) is one 32-byte sector:
@@ -128,6 +134,7 @@ struct Tree {
     // records written over them later in the step have their own layout.
     Rec4 ra, rb, rq0, rq1;
     Rec4 rc_hi, rc_lo;              // FP32 cell corner (hi/lo) + width, inside test
+    float4* pbox;                   // collision boxes of slots and slot runs (box_items(cap_n) pairs)
     double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
     int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
     int32_t* lvl;                   // per-depth cell counts / offsets / cursors (96)

@@ -562,6 +562,7 @@ struct CollRecArgs {
     const Ctl* ctl;
     int ecap, ncap, nbox;
     double rmax;
+    float4* pbox = nullptr;   // box items (pairs lo, hi): slots, then runs of 32, then runs of 256
 };
 
 // Collision-search records (Sect. 5.2): per cell its geometric centre
@@ -608,92 +609,216 @@ __global__ void __launch_bounds__(256) k_coll_records(CollRecArgs A) {
 // with i are examined from the other particle.  Leaves as in
 // k_coll_records; a removed particle's leaf sits at +infinity and is never
 // close.
-__global__ void __launch_bounds__(256) k_aabb_leaves(CollRecArgs A) {
-    const int n = min(A.ctl->n_live, A.ncap);
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int e = A.leaf_of[p];
-    if (A.box[p] >= A.nbox) {
-        const float inf = __int_as_float(0x7f800000);
-        A.ra[e] = make_float4(inf, inf, inf, __int_as_float(~p));
-        A.rb[e] = make_float4(0.f, 0.f, 0.f, (float)A.r[p]);
-        return;
-    }
-    float hx, lx, hy, ly, hz, lz;
-    split_hilo(A.x[p], hx, lx);
-    split_hilo(A.y[p], hy, ly);
-    split_hilo(A.z[p], hz, lz);
-    A.ra[e] = make_float4(hx, hy, hz, __int_as_float(~p));
-    A.rb[e] = make_float4(lx, ly, lz, (float)A.r[p]);
-}
+// Boxes from particle ranges: a cell of the gravity tree holds the
+// consecutive slots [first, first + count), so its box is the union of its
+// particles' boxes, taken here from the fewest aligned runs that tile the
+// range (single slots at its ends, runs of 32, 256 and 8192 slots).
+// Minima and maxima are exact in any order, so the records equal those of a
+// bottom-up merge over the children, in three launches instead of one per
+// depth.  A box item is the pair (lo, hi): lo = lower corner and the largest
+// live slot (int bits, -1 none), hi = upper corner; an item with no live
+// particle is (+inf, -inf).
+constexpr int kRunA = 32, kRunB = 256, kRunC = 8192;
+constexpr int kRunsInB = kRunB / kRunA, kRunsInC = kRunC / kRunB;
+static_assert(kRunsInC == 32, "a warp per run of 8192 slots");
 
-// One child's contribution to a cell's box and largest slot.
 struct BoxAcc {
     float lox, loy, loz, hix, hiy, hiz;
     int top;
 };
 
-__device__ __forceinline__ void box_add(const CollRecArgs& A, int c, BoxAcc& B) {
+__device__ __forceinline__ BoxAcc box_empty() {
     const float inf = __int_as_float(0x7f800000);
-    const float4 a = A.ra[c], b = A.rb[c];
-    if (__float_as_int(a.w) < 0) {
-        // particle leaf: hi/lo floats of its position (hi = x rounded to
-        // nearest, lo the sign of x - hi), so x lies in [hi, next float up]
-        // or [next float down, hi]
-        if (a.x == inf) return;   // removed particle
-        B.top = max(B.top, ~__float_as_int(a.w));
-        B.lox = fminf(B.lox, b.x < 0.f ? nextafterf(a.x, -inf) : a.x);
-        B.hix = fmaxf(B.hix, b.x > 0.f ? nextafterf(a.x, inf) : a.x);
-        B.loy = fminf(B.loy, b.y < 0.f ? nextafterf(a.y, -inf) : a.y);
-        B.hiy = fmaxf(B.hiy, b.y > 0.f ? nextafterf(a.y, inf) : a.y);
-        B.loz = fminf(B.loz, b.z < 0.f ? nextafterf(a.z, -inf) : a.z);
-        B.hiz = fmaxf(B.hiz, b.z > 0.f ? nextafterf(a.z, inf) : a.z);
-    } else {
-        B.lox = fminf(B.lox, a.x); B.loy = fminf(B.loy, a.y); B.loz = fminf(B.loz, a.z);
-        B.hix = fmaxf(B.hix, b.x); B.hiy = fmaxf(B.hiy, b.y); B.hiz = fmaxf(B.hiz, b.z);
-        B.top = max(B.top, __float_as_int(a.w));
+    return BoxAcc{inf, inf, inf, -inf, -inf, -inf, -1};
+}
+
+__device__ __forceinline__ void box_fold(BoxAcc& B, const BoxAcc& o) {
+    B.lox = fminf(B.lox, o.lox); B.loy = fminf(B.loy, o.loy); B.loz = fminf(B.loz, o.loz);
+    B.hix = fmaxf(B.hix, o.hix); B.hiy = fmaxf(B.hiy, o.hiy); B.hiz = fmaxf(B.hiz, o.hiz);
+    B.top = max(B.top, o.top);
+}
+
+// Fold of the boxes of the lanes l with (l & ~(width - 1)) equal, width a
+// power of two up to 32.
+__device__ __forceinline__ void box_reduce(BoxAcc& B, int width) {
+    for (int x = 1; x < width; x <<= 1) {
+        BoxAcc o;
+        o.lox = __shfl_xor_sync(0xffffffffu, B.lox, x);
+        o.loy = __shfl_xor_sync(0xffffffffu, B.loy, x);
+        o.loz = __shfl_xor_sync(0xffffffffu, B.loz, x);
+        o.hix = __shfl_xor_sync(0xffffffffu, B.hix, x);
+        o.hiy = __shfl_xor_sync(0xffffffffu, B.hiy, x);
+        o.hiz = __shfl_xor_sync(0xffffffffu, B.hiz, x);
+        o.top = __shfl_xor_sync(0xffffffffu, B.top, x);
+        box_fold(B, o);
     }
 }
 
-// The cells of one depth (same split between eight lanes per cell and one
-// thread per cell as the moments; minima and maxima do not depend on order).
-__global__ void __launch_bounds__(256) k_aabb_level(CollRecArgs A, const int32_t* __restrict__ lvl,
-                                                    const int32_t* __restrict__ list, int depth) {
-    const int cnt = lvl[depth], off = lvl[32 + depth];
-    const float inf = __int_as_float(0x7f800000);
-    if (cnt <= kWarpCells && depth < kMaxDepth) {
-        const int lane = threadIdx.x & 31, o = lane & 7;
-        const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwg = (gridDim.x * blockDim.x) >> 5;
-        for (int base = 4 * wg; base < cnt; base += 4 * nwg) {
-            const int g = base + (lane >> 3);
-            const bool live = g < cnt;
-            const int k = live ? list[off + g] : 0;
-            BoxAcc B{inf, inf, inf, -inf, -inf, -inf, -1};
-            if (live && ((A.e_cmask[k] >> o) & 1u)) box_add(A, A.e_child[8 * (size_t)k + o], B);
-#pragma unroll
-            for (int x = 1; x < 8; x <<= 1) {
-                B.lox = fminf(B.lox, __shfl_xor_sync(0xffffffffu, B.lox, x));
-                B.loy = fminf(B.loy, __shfl_xor_sync(0xffffffffu, B.loy, x));
-                B.loz = fminf(B.loz, __shfl_xor_sync(0xffffffffu, B.loz, x));
-                B.hix = fmaxf(B.hix, __shfl_xor_sync(0xffffffffu, B.hix, x));
-                B.hiy = fmaxf(B.hiy, __shfl_xor_sync(0xffffffffu, B.hiy, x));
-                B.hiz = fmaxf(B.hiz, __shfl_xor_sync(0xffffffffu, B.hiz, x));
-                B.top = max(B.top, __shfl_xor_sync(0xffffffffu, B.top, x));
-            }
-            if (live && o == 0) {
-                A.ra[k] = make_float4(B.lox, B.loy, B.loz, __int_as_float(B.top));
-                A.rb[k] = make_float4(B.hix, B.hiy, B.hiz, __int_as_float(A.e_skip[k]));
-            }
+__device__ __forceinline__ void item_put(float4* pbox, long long i, const BoxAcc& B) {
+    pbox[2 * i] = make_float4(B.lox, B.loy, B.loz, __int_as_float(B.top));
+    pbox[2 * i + 1] = make_float4(B.hix, B.hiy, B.hiz, 0.f);
+}
+
+__device__ __forceinline__ void item_fold(const float4* pbox, long long i, BoxAcc& B) {
+    const float4 lo = pbox[2 * i], hi = pbox[2 * i + 1];
+    B.lox = fminf(B.lox, lo.x); B.loy = fminf(B.loy, lo.y); B.loz = fminf(B.loz, lo.z);
+    B.hix = fmaxf(B.hix, hi.x); B.hiy = fmaxf(B.hiy, hi.y); B.hiz = fmaxf(B.hiz, hi.z);
+    B.top = max(B.top, __float_as_int(lo.w));
+}
+
+__device__ __forceinline__ void cell_put(const CollRecArgs& A, int k, const BoxAcc& B) {
+    A.ra[k] = make_float4(B.lox, B.loy, B.loz, __int_as_float(B.top));
+    A.rb[k] = make_float4(B.hix, B.hiy, B.hiz, __int_as_float(A.e_skip[k]));
+}
+
+// Collision records on the gravity tree, at the positions after the second
+// drift (Sect. 5.2, with a tighter pruning volume than Eq. 3's sphere): the
+// tree's cells still hold the same particles, and a cell records the
+// axis-aligned box of its particles' current positions (lower corner rounded
+// down, upper corner rounded up to FP32), so the search stays exact without a
+// second sort and build.  A cell's record also holds the largest particle
+// slot below it (ra.w), so a search from slot i skips subtrees whose pairs
+// with i are examined from the other particle.  Leaves as in
+// k_coll_records; a removed particle's leaf sits at +infinity and is never
+// close.  This launch also writes the box items of every slot and of the
+// runs of 32 and 256 slots (kRunB threads per block).
+__global__ void __launch_bounds__(kRunB) k_aabb_leaves(CollRecArgs A) {
+    __shared__ BoxAcc wbox[kRunsInB];
+    const int n = min(A.ctl->n_live, A.ncap);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    BoxAcc B = box_empty();
+    if (p < n) {
+        const int e = A.leaf_of[p];
+        if (A.box[p] >= A.nbox) {
+            const float inf = __int_as_float(0x7f800000);
+            A.ra[e] = make_float4(inf, inf, inf, __int_as_float(~p));
+            A.rb[e] = make_float4(0.f, 0.f, 0.f, (float)A.r[p]);
+        } else {
+            float hx, lx, hy, ly, hz, lz;
+            split_hilo(A.x[p], hx, lx);
+            split_hilo(A.y[p], hy, ly);
+            split_hilo(A.z[p], hz, lz);
+            A.ra[e] = make_float4(hx, hy, hz, __int_as_float(~p));
+            A.rb[e] = make_float4(lx, ly, lz, (float)A.r[p]);
+            // hi = x rounded to nearest, lo the sign of x - hi: x lies in
+            // [hi, next float up] or [next float down, hi]
+            const float inf = __int_as_float(0x7f800000);
+            B.lox = lx < 0.f ? nextafterf(hx, -inf) : hx;
+            B.hix = lx > 0.f ? nextafterf(hx, inf) : hx;
+            B.loy = ly < 0.f ? nextafterf(hy, -inf) : hy;
+            B.hiy = ly > 0.f ? nextafterf(hy, inf) : hy;
+            B.loz = lz < 0.f ? nextafterf(hz, -inf) : hz;
+            B.hiz = lz > 0.f ? nextafterf(hz, inf) : hz;
+            B.top = p;
         }
-        return;
+        item_put(A.pbox, p, B);
     }
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
-        const int k = list[off + t];
-        const int end = A.e_skip[k];
-        BoxAcc B{inf, inf, inf, -inf, -inf, -inf, -1};
-        for (int c = k + 1; c < end; c = A.e_skip[c]) box_add(A, c, B);
-        A.ra[k] = make_float4(B.lox, B.loy, B.loz, __int_as_float(B.top));
-        A.rb[k] = make_float4(B.hix, B.hiy, B.hiz, __int_as_float(end));
+    box_reduce(B, kRunA);
+    const int w = threadIdx.x / kRunA;
+    if (threadIdx.x % kRunA == 0) {
+        if (p < n) item_put(A.pbox, (long long)A.ncap + p / kRunA, B);
+        wbox[w] = B;
+    }
+    __syncthreads();
+    if (w == 0) {
+        BoxAcc C = (threadIdx.x < kRunsInB) ? wbox[threadIdx.x] : box_empty();
+        box_reduce(C, kRunsInB);
+        const int nruns = (A.ncap + kRunA - 1) / kRunA;
+        if (threadIdx.x == 0 && blockIdx.x * kRunB < n)
+            item_put(A.pbox, (long long)A.ncap + nruns + blockIdx.x, C);
+    }
+}
+
+// The aligned pieces of [lo, hi) (units of the finer run) at a coarser run
+// of `ratio` finer ones: the finer runs before the first coarse boundary,
+// the coarse runs [c0, c1), the finer runs from c1 * ratio on.
+struct Split {
+    int head_end, c0, c1, tail_begin;
+};
+__device__ __forceinline__ Split split_runs(int lo, int hi, int ratio) {
+    Split S;
+    S.head_end = min(hi, (lo + ratio - 1) / ratio * ratio);
+    S.tail_begin = max(S.head_end, hi / ratio * ratio);
+    S.c0 = S.head_end / ratio;
+    S.c1 = S.tail_begin / ratio;
+    return S;
+}
+
+// Box items of the runs of 8192 slots, from their 32 runs of 256 (a warp per
+// run).
+__global__ void __launch_bounds__(256) k_aabb_runs(CollRecArgs A) {
+    const int n = min(A.ctl->n_live, A.ncap);
+    const long long nA = (A.ncap + kRunA - 1) / kRunA, nB = (A.ncap + kRunB - 1) / kRunB;
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = w; (long long)c * kRunC < n; c += nw) {
+        BoxAcc B = box_empty();
+        const int q = c * kRunsInC + lane;   // its run of 256
+        if ((long long)q * kRunB < n) item_fold(A.pbox, A.ncap + nA + q, B);
+        box_reduce(B, 32);
+        if (lane == 0) item_put(A.pbox, A.ncap + nA + nB + c, B);
+    }
+}
+
+// Folds the items that tile slots [a, e), lane `lane` of 32 taking every
+// 32nd one: slots and runs of 32 and 256 at both ends, runs of 8192 between.
+// A cell of c slots needs at most 138 + c / 8192 items.
+__device__ __forceinline__ void range_fold(const CollRecArgs& A, int a, int e, int lane, BoxAcc& B) {
+    const long long nA = (A.ncap + kRunA - 1) / kRunA, nB = (A.ncap + kRunB - 1) / kRunB;
+    const long long baseA = A.ncap, baseB = baseA + nA, baseC = baseB + nB;
+    const Split s1 = split_runs(a, e, kRunA);                // slots | runs of 32
+    const Split s2 = split_runs(s1.c0, s1.c1, kRunsInB);     // runs of 32 | runs of 256
+    const Split s3 = split_runs(s2.c0, s2.c1, kRunsInC);     // runs of 256 | runs of 8192
+    // seven pieces in turn, each (first item index, count); `off` carries
+    // this lane's position from one piece into the next
+    int off = lane;
+    auto piece = [&](long long first, int count) {
+#pragma unroll 1
+        for (; off < count; off += 32) item_fold(A.pbox, first + off, B);
+        off -= count;
+    };
+    piece(a, s1.head_end - a);
+    piece(baseA + s1.c0, s2.head_end - s1.c0);
+    piece(baseB + s2.c0, s3.head_end - s2.c0);
+    piece(baseC + s3.c0, s3.c1 - s3.c0);
+    piece(baseB + s3.tail_begin, s2.c1 - s3.tail_begin);
+    piece(baseA + s2.tail_begin, s1.c1 - s2.tail_begin);
+    piece(s1.tail_begin, e - s1.tail_begin);
+}
+
+// Every cell of the gravity build, in entry order (consecutive entries: the
+// counts and first slots are read coalesced; particle leaves are skipped).
+// A lane takes a cell of at most eight slots alone; larger cells are taken
+// afterwards by the whole warp, one at a time.
+__global__ void __launch_bounds__(256) k_aabb_cells(CollRecArgs A) {
+    const int E = min(A.ctl->n_entries, A.ecap);
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int e0 = 32 * w; e0 < E; e0 += 32 * nw) {
+        const int k = e0 + lane;
+        const bool cell = k < E && A.e_level[k] < 22;   // 22 marks a particle leaf
+        int a = 0, c = 0;
+        if (cell) {
+            a = A.e_first[k];
+            c = A.e_count[k];
+        }
+        if (cell && c <= 8) {
+            BoxAcc B = box_empty();
+#pragma unroll 4
+            for (int j = 0; j < c; j++) item_fold(A.pbox, a + j, B);
+            cell_put(A, k, B);
+        }
+        unsigned big = __ballot_sync(0xffffffffu, cell && c > 8);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int ab = __shfl_sync(0xffffffffu, a, src);
+            const int cb = __shfl_sync(0xffffffffu, c, src);
+            BoxAcc W = box_empty();
+            range_fold(A, ab, ab + cb, lane, W);
+            box_reduce(W, 32);
+            if (lane == 0) cell_put(A, e0 + src, W);
+        }
     }
 }
 
@@ -858,10 +983,12 @@ void build_collision_aabb(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* bo
     A.e_count = T.e_count; A.e_top = T.e_top; A.e_child = T.e_child; A.e_cmask = T.e_cmask;
     A.ra = T.ra; A.rb = T.rb; A.ctl = ctl; A.ecap = T.cap_e; A.rmax = rmax;
     A.ncap = T.cap_n; A.nbox = C.nbox;
-    k_aabb_leaves<<<ceil_div(T.cap_n, 256), 256, 0, s>>>(A);
-    // the cell lists per depth of the gravity build (same tree) are reused
-    const int grid = std::min(ceil_div(T.cap_n, 256), 4 * 152);
-    for (int d = kMaxDepth; d >= 0; d--) k_aabb_level<<<grid, 256, 0, s>>>(A, T.lvl, T.e_arrive, d);
+    A.pbox = T.pbox;
+    k_aabb_leaves<<<ceil_div(T.cap_n, kRunB), kRunB, 0, s>>>(A);
+    k_aabb_runs<<<ceil_div(ceil_div(T.cap_n, kRunC), 8), 256, 0, s>>>(A);
+    // a warp per 32 entries; the resident blocks (48 registers: 5 of 256 per SM)
+    const int grid = std::min(ceil_div(T.cap_e, 256), 5 * 152);
+    k_aabb_cells<<<grid, 256, 0, s>>>(A);
 }
 
 }  // namespace rb
