@@ -297,11 +297,11 @@ int upload(rb_sim* s) {
         rc |= dalloc(s, &T.d_a, ecap, L); rc |= dalloc(s, &T.d_q0, ecap, L);
         rc |= dalloc(s, &T.d_q1, ecap, L); rc |= dalloc(s, &T.d_c, ecap, L);
         rc |= dalloc(s, &T.box_first, s->nbox + 1, L);
-        rc |= dalloc(s, &T.box_root, s->nbox, L);
+        rc |= dalloc(s, &T.box_root, s->nbox + 1, L);
         rc |= dalloc(s, &T.lvl, 96, L);
         rc |= dalloc(s, &T.tq, kMaxTileQueues * kTileQStride, L);
         T.nq = s->nsm > 0 ? min(s->nsm, kMaxTileQueues) : 1;
-        rc |= dalloc(s, &T.img, (size_t)s->nbox * (2 * s->cfg.nghost[0] + 1) * (2 * s->cfg.nghost[1] + 1) *
+        rc |= dalloc(s, &T.img, (size_t)(s->nbox + 1) * (2 * s->cfg.nghost[0] + 1) * (2 * s->cfg.nghost[1] + 1) *
                                     (2 * s->cfg.nghost[2] + 1), L);
         rc |= dalloc(s, &s->PR.slot_of_id, cap, L);
         rc |= dalloc(s, &s->acc_x, cap, L); rc |= dalloc(s, &s->acc_y, cap, L);
@@ -675,38 +675,61 @@ int read_box(rb_sim* s, int box, int64_t cap, int64_t* n_out, double* const dst[
     int32_t* flags = s->T.start;   // scratch: ncap + 1 ints, free between steps
     particles_by_id(s->P[s->cur], out, box, (int)s->base[box], s->ncap, flags, nb, &s->ctl->out_live,
                     s->stream);
-    // only an open boundary removes particles; otherwise every id of the box
-    // is live and the copies need not wait for the count
-    int live = nb;
-    if (s->cfg.boundary == RB_BC_OPEN) {
-        if (read_ctl(s)) return RB_ERR_CUDA;
-        live = s->hctl.out_live;
-    }
-    if (n_out) *n_out = live;
+    // an open face (an open box, or the open z of a periodic or shearing box)
+    // may have removed ids; otherwise every id of the box is live
+    const bool may_remove = s->cfg.boundary == RB_BC_OPEN || !s->cfg.z_periodic;
     bool want = id != nullptr;
     for (int f = 0; f < 8; f++) want = want || dst[f] != nullptr;
-    if (!want) return RB_OK;   // a count query
+    int live = nb;
+    if (!want || (may_remove && cap < nb)) {
+        if (may_remove) {
+            if (read_ctl(s)) return RB_ERR_CUDA;
+            live = s->hctl.out_live;
+        }
+        if (n_out) *n_out = live;
+        if (!want) return RB_OK;   // a count query
+    }
     if (live > cap) return fail(s, RB_ERR_ARG, "capacity too small");
     const double* src[8] = {out.x, out.y, out.z, out.vx, out.vy, out.vz, out.m, out.r};
-    if (live == nb) {
+    std::vector<int32_t> fl;
+    if (cap >= nb) {
+        // every id's entry straight into the caller's arrays; with removals
+        // possible, the count read waits for these copies as well
         for (int f = 0; f < 8; f++)
             if (dst[f])
-                RB_CUDA(s, cudaMemcpyAsync(dst[f], src[f], sizeof(double) * live, cudaMemcpyDeviceToHost,
+                RB_CUDA(s, cudaMemcpyAsync(dst[f], src[f], sizeof(double) * nb, cudaMemcpyDeviceToHost,
                                            s->stream));
-        RB_CUDA(s, cudaStreamSynchronize(s->stream));
-        if (id)
-            for (int k = 0; k < live; k++) id[k] = k;
-        return RB_OK;
-    }
-    std::vector<int32_t> fl;
-    if (d2h(s, fl, flags, nb)) return RB_ERR_CUDA;
-    std::vector<double> buf;
-    for (int f = 0; f < 8; f++) {
-        if (!dst[f]) continue;
-        if (d2h(s, buf, src[f], nb)) return RB_ERR_CUDA;
-        int64_t k = 0;
-        for (int j = 0; j < nb; j++)
-            if (fl[j]) dst[f][k++] = buf[j];
+        if (may_remove) {
+            if (read_ctl(s)) return RB_ERR_CUDA;
+            live = s->hctl.out_live;
+        } else {
+            RB_CUDA(s, cudaStreamSynchronize(s->stream));
+        }
+        if (n_out) *n_out = live;
+        if (live == nb) {
+            if (id)
+                for (int k = 0; k < live; k++) id[k] = k;
+            return RB_OK;
+        }
+        // removed ids leave gaps: keep the live entries, in id order
+        if (d2h(s, fl, flags, nb)) return RB_ERR_CUDA;
+        for (int f = 0; f < 8; f++) {
+            if (!dst[f]) continue;
+            int64_t k = 0;
+            for (int j = 0; j < nb; j++)
+                if (fl[j]) dst[f][k++] = dst[f][j];
+        }
+    } else {
+        // fewer places than ids: through host buffers
+        if (d2h(s, fl, flags, nb)) return RB_ERR_CUDA;
+        std::vector<double> buf;
+        for (int f = 0; f < 8; f++) {
+            if (!dst[f]) continue;
+            if (d2h(s, buf, src[f], nb)) return RB_ERR_CUDA;
+            int64_t k = 0;
+            for (int j = 0; j < nb; j++)
+                if (fl[j]) dst[f][k++] = buf[j];
+        }
     }
     if (id) {
         int64_t k = 0;

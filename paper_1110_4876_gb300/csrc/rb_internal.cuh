@@ -136,9 +136,9 @@ struct Tree {
     Rec4 rc_hi, rc_lo;              // FP32 cell corner (hi/lo) + width, inside test
     float4* pbox;                   // collision boxes of slots and slot runs (box_items(cap_n) pairs)
     double4_32a *d_a, *d_q0, *d_q1, *d_c;  // FP64 walk records (d_c: cell corner + width)
-    int32_t *box_first, *box_root;  // per box (nbox + 1 / nbox)
+    int32_t *box_first, *box_root;  // per box, nbox + 1 each (box_root[nbox] = -1: removed particles)
     int32_t* lvl;                   // per-depth cell counts / offsets / cursors (96)
-    ImgTab* img;                    // [box][image] offsets of the current walk or search
+    ImgTab* img;                    // [box][image] offsets of the current walk or search (nbox + 1 rows)
     int32_t* tq;                    // tile queues of the walks (kTileQStride ints each)
     int nq;                         // number of tile queues (one per SM)
     int cap_n, cap_e;

@@ -173,12 +173,16 @@ __global__ void __launch_bounds__(256) k_box_ranges(const int32_t* __restrict__ 
         for (int q = b + 1; q <= nbox; q++) box_first[q] = n;
 }
 
+// Root entry of each box's tree, -1 for an empty box; entry nbox, -1, is the
+// root of the box that particles removed by an open boundary carry (nbox):
+// those still hold slots of the gravity tree when the step's collision
+// search runs on it, and search nothing.
 __global__ void k_box_roots(const int32_t* __restrict__ box_first,
                             const int32_t* __restrict__ start, int nbox,
                             int32_t* __restrict__ box_root) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    box_root[b] = box_first[b] < box_first[b + 1] ? start[box_first[b]] : -1;
+    if (b > nbox) return;
+    box_root[b] = b < nbox && box_first[b] < box_first[b + 1] ? start[box_first[b]] : -1;
 }
 
 
@@ -842,7 +846,7 @@ void build_topology(const Tree& T, const PSet& P, Ctl* ctl, const BoxP* boxes, c
                               T.e_count, T.e_skip, T.e_level, T.leaf_of, T.key, T.e_child, T.e_cmask);
     k_box_ranges<<<ceil_div(n > C.nbox + 1 ? n : C.nbox + 1, 256), 256, 0, s>>>(
         P.box, ctl, n, C.nbox, T.box_first);
-    k_box_roots<<<ceil_div(C.nbox, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
+    k_box_roots<<<ceil_div(C.nbox + 1, 256), 256, 0, s>>>(T.box_first, T.start, C.nbox, T.box_root);
 }
 
 namespace {

@@ -158,8 +158,10 @@ __device__ __noinline__ int next_tile(int32_t* tq, int nq, int q, int ntile) {
 }
 
 // Ghost-image table of the walk or search time: one thread per (box, image),
-// images in the kernels' loop order (gx outermost, gz innermost).  Threads
-// below nq * kTileQStride also empty the tile queues.
+// images in the kernels' loop order (gx outermost, gz innermost), for boxes
+// 0 .. nbox (row nbox, a copy of box 0's, is read by removed particles, which
+// search nothing).  Threads below nq * kTileQStride also empty the tile
+// queues.
 __global__ void k_img_table(const BoxP* __restrict__ boxes, const Ctl* __restrict__ ctl, double t0,
                             double half_dt, int hs, int nbox, int ngx, int ngy, int ngz,
                             ImgTab* __restrict__ tab, int32_t* __restrict__ tq, int nqw) {
@@ -167,10 +169,10 @@ __global__ void k_img_table(const BoxP* __restrict__ boxes, const Ctl* __restric
     const int nimg = (2 * ngx + 1) * ny * nz;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nqw) tq[k] = 0;
-    if (k >= nbox * nimg) return;
+    if (k >= (nbox + 1) * nimg) return;
     const int b = k / nimg, g = k % nimg;
     const int gz = g % nz - ngz, gy = (g / nz) % ny - ngy, gx = g / (ny * nz) - ngx;
-    const BoxP bp = boxes[b];
+    const BoxP bp = boxes[b < nbox ? b : 0];
     const double s = shear_offset(bp, time_of(ctl, t0, half_dt, hs));
     ImgTab T;
     image_offset(bp, s, gx, gy, gz, T.ox, T.oy, T.oz);
@@ -1351,7 +1353,7 @@ int build_image_table(const BoxP* boxes, const Ctl* ctl, const SimC& C, int half
                       cudaStream_t s, int32_t* tq, int nq) {
     const int nimg = (2 * C.ngx + 1) * (2 * C.ngy + 1) * (2 * C.ngz + 1);
     const int nqw = tq ? nq * kTileQStride : 0;
-    const int nt = max(C.nbox * nimg, nqw);
+    const int nt = max((C.nbox + 1) * nimg, nqw);
     k_img_table<<<ceil_div(nt, 128), 128, 0, s>>>(boxes, ctl, C.t0, C.half_dt, half_step_offset, C.nbox,
                                                    C.ngx, C.ngy, C.ngz, tab, tq, nqw);
     return nimg;

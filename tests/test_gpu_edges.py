@@ -151,3 +151,38 @@ def test_fast_particles_wrap_several_boxes(rb, orc, boundary):
         for key in ("x", "y", "z", "vx", "vy"):
             assert np.array_equal(got[key], getattr(st, key)), (k, key)
         assert np.all(np.abs(got["y"]) <= L / 2)
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_particles_leaving_in_the_second_drift(rb, orc, walk):
+    """Particles that leave through the open z faces in a step's second drift
+    half: they still sit in that step's gravity tree when its cells get the
+    boxes of the end-of-step positions, as particles with no box.  The pair
+    set of every step equals brute force on the positions the GPU returns,
+    and the removed ids equal the oracle's."""
+    L, n = 12.0, 300
+    x, y, z, vx, vy, vz, m, r = (np.array(a) for a in _dense(n, 5))
+    r[:] = 0.3                         # a few hundred pairs, not thousands
+    g = np.random.default_rng(6)
+    k = g.choice(n, 40, replace=False)
+    side = np.where(np.arange(40) % 2 == 0, 1.0, -1.0)
+    z[k] = side * 5.9                  # inside after dt/2, outside after dt
+    vz[k] = side * 3e-3
+    P = (x, y, z, vx, vy, vz, m, r)
+    sim = rb.Sim(**_cfg(rb, L, walk))
+    sim.set_particles(P)
+    p = _params(orc, L)
+    st = orc.State(p, *P)
+    for s in range(2):
+        sim.step(1)
+        st.step(1)
+        got = sim.particles()
+        keys = rb.pair_keys(*sim.pairs(detect=False))
+        ref = orc.collide_brute(p, orc.time_at(p, 2 * (s + 1)), got["x"], got["y"], got["z"], got["r"],
+                                got["id"])
+        assert np.array_equal(keys, ref), s
+        assert len(ref) > 0
+        assert got["id"].tolist() == st.id.tolist(), s
+    assert len(got["id"]) <= n - 40
+    if walk == 0:
+        assert np.max(np.abs(got["x"] - st.x)) <= 1e-9 * L
