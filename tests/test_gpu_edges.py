@@ -153,22 +153,29 @@ def test_fast_particles_wrap_several_boxes(rb, orc, boundary):
         assert np.all(np.abs(got["y"]) <= L / 2)
 
 
+def _leaving(n, seed):
+    """_dense particles of radius 0.3 m (a few hundred pairs) of which 40 sit
+    at z = +-5.9 m moving outward at 3 mm/s: inside the 12 m box after the
+    first drift half of a step, outside it after the second."""
+    x, y, z, vx, vy, vz, m, r = (np.array(a) for a in _dense(n, seed))
+    r[:] = 0.3
+    g = np.random.default_rng(seed + 1)
+    k = g.choice(n, 40, replace=False)
+    side = np.where(np.arange(40) % 2 == 0, 1.0, -1.0)
+    z[k] = side * 5.9
+    vz[k] = side * 3e-3
+    return (x, y, z, vx, vy, vz, m, r)
+
+
 @pytest.mark.parametrize("walk", [0, 1])
 def test_particles_leaving_in_the_second_drift(rb, orc, walk):
     """Particles that leave through the open z faces in a step's second drift
     half: they still sit in that step's gravity tree when its cells get the
-    boxes of the end-of-step positions, as particles with no box.  The pair
-    set of every step equals brute force on the positions the GPU returns,
-    and the removed ids equal the oracle's."""
+    boxes of the end-of-step positions and the collision search runs.  The
+    pair set of every step equals brute force on the positions the GPU
+    returns, the removed ids equal the oracle's, and reads skip them."""
     L, n = 12.0, 300
-    x, y, z, vx, vy, vz, m, r = (np.array(a) for a in _dense(n, 5))
-    r[:] = 0.3                         # a few hundred pairs, not thousands
-    g = np.random.default_rng(6)
-    k = g.choice(n, 40, replace=False)
-    side = np.where(np.arange(40) % 2 == 0, 1.0, -1.0)
-    z[k] = side * 5.9                  # inside after dt/2, outside after dt
-    vz[k] = side * 3e-3
-    P = (x, y, z, vx, vy, vz, m, r)
+    P = _leaving(n, 5)
     sim = rb.Sim(**_cfg(rb, L, walk))
     sim.set_particles(P)
     p = _params(orc, L)
@@ -183,6 +190,33 @@ def test_particles_leaving_in_the_second_drift(rb, orc, walk):
         assert np.array_equal(keys, ref), s
         assert len(ref) > 0
         assert got["id"].tolist() == st.id.tolist(), s
+        assert np.all(np.abs(got["z"]) < L / 2)
     assert len(got["id"]) <= n - 40
     if walk == 0:
         assert np.max(np.abs(got["x"] - st.x)) <= 1e-9 * L
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_ensemble_with_particles_leaving(rb, orc, walk):
+    """The same in a batched simulation of three boxes: each box advances as
+    it does alone, and each box's pairs equal brute force on its positions."""
+    L, n = 12.0, 300
+    seeds = (5, 15, 25)
+    ens = rb.Sim(nbox=len(seeds), **_cfg(rb, L, walk))
+    for b, seed in enumerate(seeds):
+        ens.set_particles(_leaving(n, seed), box=b)
+    ens.step(2)
+    p = _params(orc, L)
+    tol = 1e-12 if walk == 0 else 1e-9
+    for b, seed in enumerate(seeds):
+        one = rb.Sim(**_cfg(rb, L, walk))
+        one.set_particles(_leaving(n, seed))
+        one.step(2)
+        ge, go = ens.particles(b), one.particles()
+        assert len(ge["id"]) <= n - 40
+        assert ge["id"].tolist() == go["id"].tolist()
+        for f in ("x", "y", "z", "vx", "vy", "vz"):
+            assert np.max(np.abs(ge[f] - go[f])) <= tol * max(L, np.max(np.abs(go[f]))), (b, f)
+        keys = rb.pair_keys(*ens.pairs(box=b, detect=False))
+        ref = orc.collide_brute(p, orc.time_at(p, 4), ge["x"], ge["y"], ge["z"], ge["r"], ge["id"])
+        assert np.array_equal(keys, ref), b
