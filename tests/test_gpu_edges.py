@@ -220,3 +220,39 @@ def test_ensemble_with_particles_leaving(rb, orc, walk):
         keys = rb.pair_keys(*ens.pairs(box=b, detect=False))
         ref = orc.collide_brute(p, orc.time_at(p, 4), ge["x"], ge["y"], ge["z"], ge["r"], ge["id"])
         assert np.array_equal(keys, ref), b
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_boxes_that_empty_and_empty_simulations(rb, orc, walk):
+    """Every particle of a box leaves through the open z faces in the first
+    step: the following steps run on an empty box (alone, and beside a box
+    that keeps its particles), and a simulation with no particles steps."""
+    L, n = 12.0, 64
+    g = np.random.default_rng(9)
+    x, y = g.uniform(-L / 2, L / 2, (2, n))
+    side = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    z = side * 5.9
+    vz = side * 3e-3
+    zero = np.zeros(n)
+    P = (x, y, z, zero, -1.5 * I.OMEGA * x, vz, np.full(n, 1675.516), np.full(n, 0.3))
+    sim = rb.Sim(**_cfg(rb, L, walk))
+    sim.set_particles(P)
+    sim.step(3)
+    assert len(sim.particles()["id"]) == 0
+    ens = rb.Sim(nbox=2, **_cfg(rb, L, walk))
+    ens.set_particles(P, box=0)
+    Q = _leaving(200, 41)
+    ens.set_particles(Q, box=1)
+    ens.step(3)
+    one = rb.Sim(**_cfg(rb, L, walk))
+    one.set_particles(Q)
+    one.step(3)
+    assert len(ens.particles(0)["id"]) == 0
+    ge, go = ens.particles(1), one.particles()
+    assert ge["id"].tolist() == go["id"].tolist()
+    tol = 1e-12 if walk == 0 else 1e-9
+    assert np.max(np.abs(ge["x"] - go["x"])) <= tol * L
+    empty = rb.Sim(**_cfg(rb, L, walk))
+    empty.set_particles(tuple(np.zeros(0) for _ in range(8)))
+    empty.step(2)
+    assert len(empty.particles()["id"]) == 0
