@@ -281,3 +281,30 @@ def test_sweep_detector_with_particles_leaving(rb, orc):
     for f in ("vx", "vy", "vz"):
         ref = getattr(st, f)
         assert np.max(np.abs(got[f] - ref)) <= 1e-9 * np.max(np.abs(ref)), f
+
+
+def test_set_box_after_particles_left(rb, orc):
+    """rb_set_box after some ids left through the open z faces keeps the live
+    particles, renumbered 0 .. n_live - 1 in id order, and the simulation
+    then steps exactly as a fresh one given those particles."""
+    L, n = 12.0, 300
+    P = _leaving(n, 61)
+    fields = ("x", "y", "z", "vx", "vy", "vz", "m", "r")
+    sim = rb.Sim(**_cfg(rb, L, rb.RB_WALK_FP64))
+    sim.set_particles(P)
+    sim.step(1)
+    a = sim.particles()
+    assert len(a["id"]) <= n - 40
+    sim.set_box(0, (L, L, L))
+    b = sim.particles()
+    assert b["id"].tolist() == list(range(len(a["id"])))
+    for f in fields:
+        assert np.array_equal(b[f], a[f]), f
+    sim.step(2)
+    fresh = rb.Sim(**_cfg(rb, L, rb.RB_WALK_FP64))
+    fresh.set_particles(tuple(a[f] for f in fields))
+    fresh.step(2)
+    c, d = sim.particles(), fresh.particles()
+    assert c["id"].tolist() == d["id"].tolist()
+    for f in fields:
+        assert np.max(np.abs(c[f] - d[f])) <= 1e-12 * max(L, np.max(np.abs(d[f]))), f
