@@ -308,3 +308,27 @@ def test_set_box_after_particles_left(rb, orc):
     assert c["id"].tolist() == d["id"].tolist()
     for f in fields:
         assert np.max(np.abs(c[f] - d[f])) <= 1e-12 * max(L, np.max(np.abs(d[f]))), f
+
+
+@pytest.mark.parametrize("walk", [0, 1])
+def test_setting_fewer_then_more_particles(rb, orc, walk):
+    """rb_set_particles on a simulation already on the device with fewer
+    particles than before (copied into the existing buffers), then with more
+    than its capacity (new buffers): each time the simulation steps exactly
+    as a fresh one given the same particles."""
+    L = 12.0
+    fields = ("x", "y", "z", "vx", "vy", "vz", "m", "r")
+    sim = rb.Sim(**_cfg(rb, L, walk))
+    for n, seed in ((200, 71), (90, 72), (350, 73)):
+        P = _dense(n, seed)
+        P = P[:7] + (np.full(n, 0.3),)
+        sim.set_particles(P)
+        sim.step(2)
+        fresh = rb.Sim(**_cfg(rb, L, walk))
+        fresh.set_particles(P)
+        fresh.step(2)
+        c, d = sim.particles(), fresh.particles()
+        assert c["id"].tolist() == d["id"].tolist() == list(range(n))
+        for f in fields:
+            assert np.max(np.abs(c[f] - d[f])) <= 1e-12 * max(L, np.max(np.abs(d[f]))), (n, f)
+        assert np.array_equal(rb.pair_keys(*sim.pairs(detect=False)), rb.pair_keys(*fresh.pairs(detect=False)))
