@@ -143,6 +143,8 @@ int rb_set_box(rb_sim* sim, int box, const double L[3]);
 /* Copy n particles (host arrays: positions, velocities, masses, radii) into
  * box `box`, replacing what it held; ids become 0..n-1 in this order and
  * the step counter restarts at 0 (time cfg->t0 or the last rb_set_time).
+ * The other boxes keep their current particles (ids renumbered over the
+ * live ones if an open face removed some, as rb_set_box does).
  * Errors: RB_ERR_ARG (n < 0, box out of range, a particle outside the root
  * box, r < 0, m < 0, total particles above 2^24), RB_ERR_NONFINITE. */
 int rb_set_particles(rb_sim* sim, int box, int64_t n, const double* x, const double* y,

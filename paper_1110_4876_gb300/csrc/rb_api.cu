@@ -887,6 +887,12 @@ int rb_set_particles(rb_sim* s, int box, int64_t n, const double* x, const doubl
     for (int64_t i = 0; i < n; i++) rm = std::max(rm, r[i]);
     if (s->cfg.collisions && s->cfg.boundary != RB_BC_OPEN && 2.0 * rm >= std::min(h.L[0], h.L[1]))
         return fail(s, RB_ERR_ARG, "box side must exceed 2 max R");
+    if (s->nbox > 1 && !s->dirty && s->ctl) {
+        // the other boxes keep their current state (read back from the
+        // device; ids that left through an open face are dropped)
+        int rc = pull_to_host(s);
+        if (rc) return rc;
+    }
     h.x.assign(x, x + n); h.y.assign(y, y + n); h.z.assign(z, z + n);
     h.vx.assign(vx, vx + n); h.vy.assign(vy, vy + n); h.vz.assign(vz, vz + n);
     h.m.assign(m, m + n); h.r.assign(r, r + n);

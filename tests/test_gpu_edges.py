@@ -332,3 +332,36 @@ def test_setting_fewer_then_more_particles(rb, orc, walk):
         for f in fields:
             assert np.max(np.abs(c[f] - d[f])) <= 1e-12 * max(L, np.max(np.abs(d[f]))), (n, f)
         assert np.array_equal(rb.pair_keys(*sim.pairs(detect=False)), rb.pair_keys(*fresh.pairs(detect=False)))
+
+
+def test_ensemble_box_replaced_after_others_lost_particles(rb, orc):
+    """In a batched simulation, replacing one box's particles keeps the other
+    box's live particles (renumbered over the ids that left through the open
+    z faces); both boxes then step as fresh single boxes with those states.
+    FP64 walk: the FP32 walk groups a box's terms by the warps that hold its
+    targets, and in these dense boxes the collisions carry that rounding
+    into the trajectories."""
+    L, walk = 12.0, 0
+    fields = ("x", "y", "z", "vx", "vy", "vz", "m", "r")
+    A, B, Cp = _leaving(300, 81), _leaving(200, 82), _leaving(250, 83)
+    ens = rb.Sim(nbox=2, **_cfg(rb, L, walk))
+    ens.set_particles(A, box=0)
+    ens.set_particles(B, box=1)
+    ens.step(2)
+    a0 = ens.particles(0)
+    assert len(a0["id"]) <= 300 - 40
+    ens.set_particles(Cp, box=1)
+    b0 = ens.particles(0)
+    assert b0["id"].tolist() == list(range(len(a0["id"])))
+    for f in fields:
+        assert np.array_equal(b0[f], a0[f]), f
+    ens.step(2)
+    tol = 1e-12
+    for box, state in ((0, tuple(a0[f] for f in fields)), (1, Cp)):
+        one = rb.Sim(**_cfg(rb, L, walk))
+        one.set_particles(state)
+        one.step(2)
+        ge, go = ens.particles(box), one.particles()
+        assert ge["id"].tolist() == go["id"].tolist(), box
+        for f in fields:
+            assert np.max(np.abs(ge[f] - go[f])) <= tol * max(L, np.max(np.abs(go[f]))), (box, f)
