@@ -142,3 +142,22 @@ def test_open_boundary_removes_escapers(orc):
     z = np.zeros(5); one = np.ones(5)
     out = orc.boundary(p, 0.0, x, y, z, z, z, z, one, one, np.arange(5))
     assert out[-1].tolist() == [0, 2, 3]
+
+
+def test_shearing_and_periodic_boxes_remove_through_open_z(orc):
+    """Sect. 2.3 with reading R6: periodic and shearing boxes wrap x and y
+    but keep z open unless z is periodic; the box is [-L/2, L/2) on each
+    axis, so z = L/2 leaves and z = -L/2 stays."""
+    L = 4.0
+    x = np.array([0.0, 2.5, 0.0, 0.0, 0.0, 0.0]); y = np.array([0.0, 0.0, 0.0, 0.0, 0.0, -2.5])
+    z = np.array([0.0, 0.0, 2.0, -2.0, 1.999, -2.2])
+    zero, one = np.zeros(6), np.ones(6)
+    for bc in (1, 2):
+        p = orc.Params(L=(L,) * 3, boundary=bc, omega=1e-3, nghost=(1, 1, 0))
+        out = orc.boundary(p, 0.0, x, y, z, zero, zero, zero, one, one, np.arange(6))
+        assert out[-1].tolist() == [0, 1, 3, 4], bc
+        assert abs(out[0][1] - (2.5 - L)) < 1e-15      # wrapped in x
+        p = orc.Params(L=(L,) * 3, boundary=bc, omega=1e-3, nghost=(1, 1, 1), z_periodic=1)
+        out = orc.boundary(p, 0.0, x, y, z, zero, zero, zero, one, one, np.arange(6))
+        assert out[-1].tolist() == [0, 1, 2, 3, 4, 5], bc
+        assert abs(out[2][2] - (2.0 - L)) < 1e-15 and abs(out[2][5] - (-2.2 + L)) < 1e-15
